@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Benchmark: nonzero-branch updates/s of the sparse-state hot path on GB300.
+
+Workload (one step): the large sparse random circuit -- 64 qubits as four
+16-bit registers in one uint64 key, 24 seeded branching gates (16 H, 8 RY)
+interleaved with 500 permutation / diagonal-phase gates (CNOT, Toffoli, X,
+add-mod-2^16, phase), then 8 re-applied H on the cancel qubits; peak 2^24
+branches; prune threshold 1e-14; then the FP64 marginal probabilities of one
+register and the norm.  The state starts from |0...0> each step.
+
+value    = sum over gates of the branches each gate processed, divided by the
+           device time of the step (CUDA events on the state's stream)
+e2e      = the same units over the host wall time of the step through the C
+           ABI, including the device->host read of the probabilities
+roofline = the dominant kernel's algorithmic bytes / its event-timed duration
+           against the measured HBM copy bandwidth
+cpu_baseline / --impl reference = the CPU oracle (std::map, FP64, one core) on
+           a bounded sample of the same gate list
+
+Multi-GPU: the path does not shard; N ranks run N independent replicas
+("replicas only") and value is the sum of their units over the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2503_15118_gb300 import workloads as W  # noqa: E402
+
+METRIC = "nonzero-branch updates/s"
+UNIT = "updates/s"
+WORKLOAD = ("large sparse random circuit: 64 qubits (4 x 16-bit registers, uint64 keys), "
+            "24 branching H/RY + 500 CNOT/Toffoli/X/add-mod-2^16/phase + 8 cancelling H, "
+            "peak 2^24 branches, prune eps 1e-14, FP64 marginals of one 16-bit register")
+PROB_REG = 0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1].split()[0]))
+                    mx = float(f[2].split()[0])
+                except ValueError:
+                    continue
+                names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                         "sw_power_cap"]
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(circ, budget_nnz=1 << 16):
+    """Times the oracle (as it stands, one core) on the gate-list prefix whose
+    inputs stay at or below budget_nnz branches."""
+    import oracle
+    st = oracle.OracleState(circ["widths"], circ["eps"])
+    units, n_gates = 0, 0
+    t0 = time.perf_counter()
+    for g in circ["gates"]:
+        n_in = st.nnz()
+        if n_in > budget_nnz:
+            break
+        st.apply(g, circ["tables"])
+        units += n_in
+        n_gates += 1
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n_gates} of {len(circ['gates'])} gates of the same circuit "
+                      f"(inputs <= {budget_nnz} branches), {units} updates in {dt:.2f} s"}, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    circ = W.config2(seed=2)
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        cpu_baseline(circ, budget_nnz=1 << 12)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        cb, dt = cpu_baseline(circ, budget_nnz=1 << 14)
+        vals.append(cb["value"])
+        secs.append(dt)
+    v = statistics.median(vals)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (bounded prefix on the CPU oracle)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--amp32", action="store_true", help="FP32 amplitude storage")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2503_15118_gb300 import sqs
+    sqs.load()
+    circ = W.config2(seed=2)
+    widths = circ["widths"]
+    stream = torch.cuda.Stream()
+    st = sqs.State(widths, amp32=args.amp32, capacity_hint=1 << 25, stream=stream.cuda_stream,
+                   eps=circ["eps"])
+    probs = torch.empty(2 ** widths[PROB_REG], dtype=torch.float64, device="cuda")
+    norm = torch.empty(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step():
+        st.reset()
+        st.run(circ)
+        st.probabilities_device(PROB_REG, probs.data_ptr(), norm.data_ptr())
+
+    for _ in range(args.warmup):
+        step()
+    st.sync()
+
+    # Units: the branch count entering each gate (one untimed instrumented pass).
+    st.reset()
+    n_in, units = [], 0
+    for g in circ["gates"]:
+        n = st.nnz()
+        n_in.append(n)
+        units += n
+        st.apply(g, circ["tables"])
+    n_final = st.nnz()
+    peak = st.peak_nnz()
+    units += n_final  # the probability reduction reads every branch once
+
+    # Timed region: per-step events on the state's stream; L2 flushed between steps.
+    st.trace_enable(64 * (args.steps + 1) * 8)
+    st.trace_read()
+    launches0 = st.launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i)
+                evs[i][0].record(stream)
+            step()
+            with torch.cuda.stream(stream):
+                evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = st.launch_count() - launches0
+    recs, nrec = st.trace_read(cap=1 << 20)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = statistics.mean(step_ms)
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * units * args.steps / (total_ms / 1e3)
+
+    # Dominant kernel and its roofline from the traced launches.
+    per = {}
+    for name, call, kms in recs:
+        d = per.setdefault(name, [0, 0.0, []])
+        d[0] += 1
+        d[1] += kms
+        d[2].append(call)
+    dom = max(per, key=lambda k: per[k][1])
+    rb = 8 * (2 if sum(widths) > 64 else 1) + (8 if args.amp32 else 16)
+    # Algorithmic bytes of the dominant kernel: per launch, the branches it
+    # reads and writes.  API call c (1-based since the reset) is gate c - 2.
+    gates = circ["gates"]
+    alg = 0.0
+    for call in per[dom][2]:
+        gi = call - 2
+        if 0 <= gi < len(gates):
+            nin = n_in[gi]
+            nout = n_in[gi + 1] if gi + 1 < len(gates) else n_final
+            if dom == "k_pair":
+                alg += (nin + nout) * rb
+            elif dom == "k_partition":
+                alg += 2 * nin * rb
+            else:
+                alg += 2 * nin * rb
+    dom_ms = per[dom][1]
+    hbm, peak_kind = peaks()
+    achieved = alg / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
+    clocks = clk.summary()
+
+    # End to end through the C ABI with a host result buffer.
+    e2e_times = []
+    for _ in range(max(3, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st.reset()
+        st.run(circ)
+        p_host, n2 = st.probabilities(PROB_REG)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_times)
+    d2h = 8 * (2 ** widths[PROB_REG]) + 8
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-storage/f64-math" if args.amp32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": f"replicas{world}",
+                   "l2": "L2 flushed (512 MB write) between steps; peak state 402 MB",
+                   "units_per_step": units, "peak_nnz": peak, "final_nnz": n_final,
+                   "gates": len(gates)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "kernel": dom,
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "kernel_ms_per_step": dom_ms / args.steps,
+                     "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in per.items()}},
+        "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, _ = cpu_baseline(circ)
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    st.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

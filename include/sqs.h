@@ -1,0 +1,269 @@
+/*
+ * sqs.h -- C ABI of the GB300 sparse register-level quantum-state library.
+ *
+ * The library applies quantum operations to a state held only as its nonzero
+ * branches, the representation of SparQSim (arXiv 2503.15118, Sec. II.C):
+ *
+ *     |psi> = sum_i a_i |v_i^0> |v_i^1> ... |v_i^{K-1}>          (Eq. 5)
+ *
+ * Each branch is a packed basis key -- register j occupies key bits
+ * [off_j, off_j + w_j), off_0 = 0, off_j = sum_{i<j} w_i, so register 0 holds
+ * the low bits and key bit q is qubit q of Eq. 4 -- plus one complex
+ * amplitude.  Keys are one 64-bit word when sum(w_j) <= 64 and two words
+ * (bits 64..127 in the second) up to 128 qubits.  A register is 1..64 bits
+ * wide, the size of one StateStorage value (Table S2).
+ *
+ * Execution model.  All device memory belongs to the state; calls enqueue work
+ * on the state's CUDA stream and return without waiting.  Runs of
+ * non-interference operations (permutations, phases, QRAM, diagonal and
+ * anti-diagonal single-qubit matrices) are queued and fused into the kernel
+ * that next touches the state.  Only sqs_nnz, sqs_export, sqs_probabilities,
+ * sqs_sync and sqs_state_destroy wait for the device.  Device-side failures
+ * (capacity overflow, a bounded wait that ran out) are sticky: the next
+ * waiting call returns them, and sqs_last_error() describes them.
+ *
+ * Threading: a state may be used by one host thread at a time.
+ * Errors: every call checks its arguments on the host before enqueueing and
+ * returns SQS_ERR_ARG without side effects when they are invalid.
+ */
+#ifndef SQS_H_
+#define SQS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sqs_state sqs_state;
+typedef struct sqs_table sqs_table;
+
+typedef enum {
+  SQS_OK = 0,
+  SQS_ERR_ARG = -1,      /* invalid argument; nothing was enqueued          */
+  SQS_ERR_OOM = -2,      /* device allocation failed                         */
+  SQS_ERR_CAPACITY = -3, /* state would exceed the largest allowed capacity  */
+  SQS_ERR_CUDA = -4,     /* a CUDA call failed (message in sqs_last_error)   */
+  SQS_ERR_TIMEOUT = -5,  /* a bounded device-side wait ran out               */
+  SQS_ERR_STATE = -6     /* the state is unusable after an earlier error     */
+} sqs_status;
+
+/* State-creation flags. */
+#define SQS_AMP_FP64 0u           /* amplitudes stored as complex<double>       */
+#define SQS_AMP_FP32 1u           /* stored as complex<float>; merge, norm and
+                                     probability arithmetic stays FP64          */
+#define SQS_SIZING_EXACT 0u       /* output buffers sized from exact bounds     */
+#define SQS_SIZING_LEARNED 2u     /* sized by the learned capacity predictor;
+                                     an overflow is detected on the device and
+                                     the operation re-run at the exact size     */
+#define SQS_MERGE_AUTO 0u         /* merge path chosen per step by measurement  */
+#define SQS_MERGE_HASH 4u         /* force the bucketed hash merge              */
+#define SQS_MERGE_SORT 8u         /* force the radix-sort merge                 */
+
+/*
+ * One control (or predicate) qubit: bit `bit` of register `reg` must equal
+ * `value` (1 for the textbook control of Sec. II.A, CU = |0><0| (x) I +
+ * |1><1| (x) U; 0 is accepted as an extension).
+ */
+typedef struct {
+  uint32_t reg, bit, value;
+} sqs_ctrl;
+
+#define SQS_MAX_CTRL 8
+
+/*
+ * Optional device allocator.  alloc(ctx, bytes, stream) returns device memory
+ * usable on `stream` (or NULL on failure); free(ctx, ptr, stream) releases it.
+ * When no allocator is given the library uses cudaMallocAsync/cudaFreeAsync.
+ */
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* stream);
+  void (*free)(void* ctx, void* ptr, void* stream);
+} sqs_allocator;
+
+/* Permutation operations (non-interference, Sec. II.D.1).  Each maps every
+ * basis key to one key, bijectively, under its controls:
+ *   SQS_PERM_X          flip bit `bit` of `reg` (X, CNOT, Toffoli: FlipBool of
+ *                       Supp. B, controls attached as in ClassControllable)
+ *   SQS_PERM_ADD_REG    reg := (reg + src_reg) mod 2^{w_reg}
+ *   SQS_PERM_SUB_REG    reg := (reg - src_reg) mod 2^{w_reg}
+ *   SQS_PERM_ADD_CONST  reg := (reg + constant) mod 2^{w_reg}
+ *   SQS_PERM_SUB_CONST  reg := (reg - constant) mod 2^{w_reg}
+ *   SQS_PERM_SWAP       exchange reg and src_reg (equal widths)
+ * Quantum arithmetic as oracles is stated in Sec. II.D.1 ("addition,
+ * multiplication, and division ... implemented by the same method"). */
+typedef enum {
+  SQS_PERM_X = 0,
+  SQS_PERM_ADD_REG = 1,
+  SQS_PERM_SUB_REG = 2,
+  SQS_PERM_ADD_CONST = 3,
+  SQS_PERM_SUB_CONST = 4,
+  SQS_PERM_SWAP = 5
+} sqs_perm_kind;
+
+typedef struct {
+  uint32_t kind;     /* sqs_perm_kind                                     */
+  uint32_t reg;      /* target / destination register                     */
+  uint32_t bit;      /* SQS_PERM_X: bit within reg                        */
+  uint32_t src_reg;  /* *_REG and SWAP: source register (!= reg)          */
+  uint64_t constant; /* *_CONST: added / subtracted value                 */
+  uint32_t n_ctrl;   /* number of valid entries of ctrl (<= SQS_MAX_CTRL) */
+  sqs_ctrl ctrl[SQS_MAX_CTRL];
+} sqs_perm_op;
+
+/* ---- state lifetime --------------------------------------------------- */
+
+/* Creates a state over n_regs registers of the given widths (each 1..64, sum
+ * 1..128) in |0...0> with amplitude 1 (one branch).  capacity_hint is the
+ * branch count to pre-allocate for (0: small default; the state grows on
+ * demand).  cuda_stream (a cudaStream_t, NULL = the legacy default stream)
+ * orders every operation.  Errors: SQS_ERR_ARG (bad widths/flags),
+ * SQS_ERR_OOM, SQS_ERR_CUDA.  *out is written only on SQS_OK. */
+sqs_status sqs_state_create(const uint32_t* reg_widths, uint32_t n_regs, uint32_t flags,
+                            uint64_t capacity_hint, const sqs_allocator* allocator,
+                            void* cuda_stream, sqs_state** out);
+
+/* Waits for the state's pending work, then releases its device memory. */
+void sqs_state_destroy(sqs_state* st);
+
+/* Resets to |0...0> (one branch, amplitude 1) keeping allocations and any
+ * sticky error cleared.  Enqueued; does not wait. */
+sqs_status sqs_state_reset(sqs_state* st);
+
+/* Threshold of the pruning step that ends every interference operation
+ * (Sec. II.D.2: branches left at zero amplitude are removed).  A branch is
+ * removed when |a| < eps (strict).  Default 1e-14; eps >= 0. */
+sqs_status sqs_set_prune_eps(sqs_state* st, double eps);
+
+/* ---- interference operations (Sec. II.D.2, rotation listing of Supp. B) --
+ * Single-qubit matrix U on qubit `bit` of `reg`, on the branches whose
+ * controls hold:   psi'(x) = sum_s U[x_t][s] psi(x with bit t := s),
+ * U indexed [row = output bit][column = input bit].  Branches are split into
+ * their two children, equal keys merged (amplitudes summed), and branches with
+ * |a| < eps removed.  A control on the target qubit itself is SQS_ERR_ARG.
+ * Diagonal and anti-diagonal U (the _operate_diagonal / _operate_off_diagonal
+ * strategies of Supp. B) take the non-branching fused path; the result is the
+ * same.  m is row-major {re00, im00, re01, im01, re10, im10, re11, im11}. */
+sqs_status sqs_apply_u1q(sqs_state* st, uint32_t reg, uint32_t bit, const double m[8],
+                         const sqs_ctrl* ctrl, uint32_t n_ctrl);
+/* H = 2^{-1/2} [[1, 1], [1, -1]] (Sec. II.A). */
+sqs_status sqs_apply_h(sqs_state* st, uint32_t reg, uint32_t bit, const sqs_ctrl* ctrl,
+                       uint32_t n_ctrl);
+/* RY(theta) = [[cos theta/2, -sin theta/2], [sin theta/2, cos theta/2]]. */
+sqs_status sqs_apply_ry(sqs_state* st, uint32_t reg, uint32_t bit, double theta,
+                        const sqs_ctrl* ctrl, uint32_t n_ctrl);
+/* Register-valued rotation (angle_function_t of the rotation listing, Supp.
+ * B): per branch, RY(scale * value(angle_reg) + offset) on (reg, bit).
+ * angle_reg must not be reg. */
+sqs_status sqs_apply_ry_reg(sqs_state* st, uint32_t reg, uint32_t bit, uint32_t angle_reg,
+                            double scale, double offset, const sqs_ctrl* ctrl,
+                            uint32_t n_ctrl);
+
+/* ---- non-interference operations (Sec. II.D.1) --------------------------
+ * Never change the number of branches and never prune. */
+sqs_status sqs_apply_perm(sqs_state* st, const sqs_perm_op* ops, uint32_t n_ops);
+/* a := a * e^{i phi} on every branch where all n_pred predicates hold (Z, S,
+ * T and controlled phases; n_pred = 0 is a global phase). */
+sqs_status sqs_apply_phase(sqs_state* st, const sqs_ctrl* pred, uint32_t n_pred, double phi);
+
+/* ---- QRAM (Supp. C, Eq. S1) ----------------------------------------------
+ * A table of n_entries little-endian unsigned entries of entry_bytes (1, 2, 4
+ * or 8) copied from host memory to the device (the table is owned by the
+ * state and freed with it).  Load maps |i>_A |j>_D -> |i>_A |j XOR d_i>_D with
+ * d_i truncated to the data register's width (the word length); addresses at
+ * or past n_entries read d = 0.  Unload applies the same map (it is its own
+ * inverse). */
+sqs_status sqs_table_create(sqs_state* st, const void* host_entries, uint64_t n_entries,
+                            uint32_t entry_bytes, sqs_table** out);
+sqs_status sqs_qram_load(sqs_state* st, uint32_t addr_reg, uint32_t data_reg,
+                         const sqs_table* table);
+sqs_status sqs_qram_unload(sqs_state* st, uint32_t addr_reg, uint32_t data_reg,
+                           const sqs_table* table);
+
+/* ---- pruning, readout ---------------------------------------------------- */
+
+/* Removes every branch with |a| < eps (ClearZero, Sec. II.D.2).  When nnz_out
+ * is non-NULL the call waits and writes the remaining count. */
+sqs_status sqs_prune(sqs_state* st, double eps, uint64_t* nnz_out);
+
+/* Marginal probabilities of register `reg`: probs[v] = sum over branches with
+ * reg = v of |a|^2, accumulated in FP64, for v in [0, 2^{w_reg}) (w_reg <= 26;
+ * probs has 2^{w_reg} entries; NULL skips them).  norm2 (nullable) receives
+ * sum |a|^2 over the whole state.  Waits. */
+sqs_status sqs_probabilities(sqs_state* st, uint32_t reg, double* probs, double* norm2);
+
+/* Same, written to device memory (probs_dev: 2^{w_reg} doubles, norm2_dev: 1
+ * double, either nullable).  Enqueued; does not wait. */
+sqs_status sqs_probabilities_device(sqs_state* st, uint32_t reg, double* probs_dev,
+                                    double* norm2_dev);
+
+/* Current branch count.  Waits. */
+sqs_status sqs_nnz(sqs_state* st, uint64_t* out);
+
+/* Largest branch count reached since creation or reset (max_system_size,
+ * Table S1).  Waits. */
+sqs_status sqs_peak_nnz(sqs_state* st, uint64_t* out);
+
+/* Copies the branches to host memory in the library's storage order (a set:
+ * the order carries no meaning).  keys receives kw words per branch (kw = 1
+ * when sum(w) <= 64, else 2: low word first); amps receives (re, im) FP64
+ * pairs.  cap is the capacity of the arrays in branches; *n receives the
+ * branch count (when it exceeds cap nothing is copied and SQS_ERR_ARG is
+ * returned).  Waits. */
+sqs_status sqs_export(sqs_state* st, uint64_t* keys, double* amps, uint64_t cap, uint64_t* n);
+
+/* Replaces the state with n branches from host memory (same layout as
+ * sqs_export; keys must be distinct and fit the register widths). */
+sqs_status sqs_import(sqs_state* st, const uint64_t* keys, const double* amps, uint64_t n);
+
+/* Executes everything queued and waits; returns any sticky device error. */
+sqs_status sqs_sync(sqs_state* st);
+
+/* Executes everything queued without waiting. */
+sqs_status sqs_flush(sqs_state* st);
+
+/* Number of key words per branch (1 or 2). */
+uint32_t sqs_key_words(const sqs_state* st);
+
+/* Kernel launches issued by this state since creation (host-side count). */
+uint64_t sqs_launch_count(const sqs_state* st);
+
+/* ---- tracing (profiling aid; replaces the per-operation wall-clock timer of
+ * the paper's profiler helper, Supp. B, with CUDA events) ------------------
+ * When enabled, every kernel launch is bracketed by two CUDA events on the
+ * state's stream.  A record names the kernel, the index of the API call that
+ * issued it (counted from the last sqs_trace_enable) and its device time. */
+#define SQS_K_INIT 0u
+#define SQS_K_APPLY 1u      /* fused non-interference run, in place        */
+#define SQS_K_COMPACT 2u    /* fused run that may drop branches             */
+#define SQS_K_PARTITION 3u  /* fused run + scatter into merge buckets       */
+#define SQS_K_PAIR 4u       /* pair, 2x2, prune, compact (one CTA / bucket) */
+#define SQS_K_PROB 5u       /* probabilities / norm                         */
+#define SQS_K_CONVERT 6u    /* FP32 <-> FP64 staging for export / import    */
+typedef struct {
+  uint32_t kernel; /* SQS_K_*                          */
+  uint32_t call;   /* API call index since enabling     */
+  float ms;        /* device time between the events    */
+  uint32_t pad;
+} sqs_trace_record;
+
+/* Enables tracing for up to max_records launches (0 disables).  Allocates
+ * events; call outside stream capture. */
+sqs_status sqs_trace_enable(sqs_state* st, uint32_t max_records);
+/* Waits, writes up to cap records, returns the count in *n, and starts a new
+ * trace (records past max_records are dropped and counted in *n). */
+sqs_status sqs_trace_read(sqs_state* st, sqs_trace_record* out, uint32_t cap, uint32_t* n);
+
+/* Human-readable description of the last error on this state (never NULL). */
+const char* sqs_last_error(const sqs_state* st);
+
+/* Library version string. */
+const char* sqs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SQS_H_ */

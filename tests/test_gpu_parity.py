@@ -1,0 +1,306 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+FP64 storage: keys bit-exact except branches whose |a| lies within 1e-12 of
+the pruning threshold, amplitudes within 1e-12 absolute, fidelity >= 1-1e-10.
+FP32 storage (FP64 arithmetic): fidelity >= 1-1e-6 and amplitudes within
+2e-6 absolute (a float keeps 24 bits: |a| <= 1 rounds to within 6e-8 per
+stored value, and a step re-rounds once).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_15118_gb300 import workloads as W
+from tests.helpers import build_config1, compare_states
+
+pytestmark = pytest.mark.gpu
+
+ATOL64 = 1e-12
+ATOL32 = 2e-6
+
+
+@pytest.fixture(scope="module")
+def sqs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_15118_gb300 import sqs as S
+    S.load()
+    return S
+
+
+def _pair(sqs, widths, lo, hi, amps, amp32=False, eps=1e-14):
+    g = sqs.State(widths, amp32=amp32, eps=eps)
+    g.import_(lo, hi, amps)
+    o = oracle.OracleState(widths, eps=eps)
+    o.import_(lo, hi, amps)
+    return g, o
+
+
+def _check(g, o, amp32=False, fid=None):
+    got, ref = g.to_dict(), o.to_dict()
+    # FP32 storage: an exact FP64 cancellation of rounded inputs leaves a residue
+    # of about 2^-24 |a|, so keys are compared outside that noise floor.
+    f = compare_states(got, ref, eps=o.eps, atol=ATOL32 if amp32 else ATOL64,
+                       band=ATOL32 if amp32 else 1e-12)
+    assert f >= (fid if fid is not None else (1 - 1e-6 if amp32 else 1 - 1e-10))
+    return got, ref
+
+
+W64 = [16, 16, 16, 16]
+W128 = [20, 32, 32]
+
+GATES_64 = [
+    ("h", 2, 5, ()),
+    ("h", 1, 3, ((0, 1, 1), (3, 7, 0))),
+    ("ry", 3, 15, 1.234, ()),
+    ("ry", 0, 0, -2.5, ((2, 2, 1),)),
+    ("u1q", 1, 9, np.array([[0.6, -0.8j], [0.8, 0.6j]]), ()),
+    ("u1q", 2, 1, np.array([[np.exp(0.3j), 0], [0, np.exp(-1.1j)]]), ((0, 0, 1),)),
+    ("u1q", 2, 1, np.array([[0, np.exp(0.7j)], [np.exp(2.1j), 0]]), ()),
+    ("ry_reg", 3, 4, 0, 0.0123, 0.4, ()),
+    ("x", 0, 7, ()),
+    ("x", 3, 63 - 48, ((0, 2, 1), (1, 5, 1))),
+    ("add", 1, 2, 0, ()),
+    ("sub", 0, -1, 12345, ((3, 0, 1),)),
+    ("swap", 0, 3, ()),
+    ("phase", ((1, 4, 1), (2, 8, 0)), 0.77),
+]
+
+
+@pytest.mark.parametrize("n", [1, 33, 2049, 70001])
+@pytest.mark.parametrize("gi", range(len(GATES_64)))
+def test_single_gate_64bit_keys(sqs, n, gi):
+    g = GATES_64[gi]
+    target = (g[1], g[2]) if g[0] in ("h", "ry", "u1q", "ry_reg") else None
+    lo, hi, amps = W.random_state(W64, n, seed=100 + n + gi, pair_fraction=0.5, target=target)
+    gs, os_ = _pair(sqs, W64, lo, hi, amps)
+    gs.apply(g)
+    os_.apply(g)
+    _check(gs, os_)
+
+
+@pytest.mark.parametrize("pair_fraction", [0.0, 1.0])
+@pytest.mark.parametrize("n", [5, 4096, 30000])
+def test_h_pairing_extremes(sqs, n, pair_fraction):
+    lo, hi, amps = W.random_state(W64, n, seed=7 * n, pair_fraction=pair_fraction, target=(1, 6))
+    gs, os_ = _pair(sqs, W64, lo, hi, amps)
+    gs.h_gate(1, 6)
+    os_.h_gate(1, 6)
+    _check(gs, os_)
+    assert gs.nnz() == os_.nnz()
+
+
+GATES_128 = [
+    ("h", 1, 31, ()),
+    ("h", 2, 10, ((0, 19, 1),)),
+    ("ry", 2, 31, 0.9, ()),
+    ("ry_reg", 1, 2, 0, 2 * math.pi / 2 ** 20, 0.0, ()),
+    ("u1q", 0, 19, np.array([[0, 1j], [1j, 0]]), ()),
+    ("add", 2, 1, 0, ()),
+    ("add", 2, -1, 0xFFFFFFFF, ((0, 3, 0),)),
+    ("x", 2, 31, ((1, 0, 1),)),
+    ("swap", 1, 2, ()),
+    ("phase", ((2, 30, 1),), -1.3),
+]
+
+
+@pytest.mark.parametrize("amp32", [False, True])
+@pytest.mark.parametrize("n", [3, 2049, 40000])
+@pytest.mark.parametrize("gi", range(len(GATES_128)))
+def test_single_gate_128bit_keys(sqs, n, gi, amp32):
+    g = GATES_128[gi]
+    target = (g[1], g[2]) if g[0] in ("h", "ry", "u1q", "ry_reg") else None
+    lo, hi, amps = W.random_state(W128, n, seed=300 + n + gi, pair_fraction=0.5, target=target)
+    if amp32:
+        amps = amps.astype(np.complex64).astype(np.complex128)  # representable input
+    gs, os_ = _pair(sqs, W128, lo, hi, amps, amp32=amp32)
+    gs.apply(g)
+    os_.apply(g)
+    _check(gs, os_, amp32=amp32)
+
+
+def test_qram_load_unload(sqs):
+    rng = np.random.default_rng(9)
+    table8 = rng.integers(0, 256, size=300).astype(np.uint8)      # longer than 2^8: ignored tail
+    table32 = rng.integers(0, 2 ** 32, size=2 ** 10, dtype=np.uint64).astype(np.uint32)
+    short = rng.integers(0, 2 ** 16, size=100).astype(np.uint16)  # addresses >= 100 read 0
+    for widths, tab, areg, dreg in [([8, 8, 4], table8, 0, 1), ([10, 32, 32], table32, 0, 1),
+                                    ([10, 12], short, 0, 1)]:
+        lo, hi, amps = W.random_state(widths, 3000, seed=len(tab))
+        gs, os_ = _pair(sqs, widths, lo, hi, amps)
+        for st in (gs, os_):
+            st.apply(("qload", areg, dreg, 0), [tab])
+        _check(gs, os_)
+        for st in (gs, os_):
+            st.apply(("qunload", areg, dreg, 0), [tab])
+        got = gs.to_dict()
+        assert got == {(int(h) << 64) | int(l): complex(a) for l, h, a in zip(lo, hi, amps)}
+
+
+def _kinds_all():
+    return ("x", "cx", "ccx", "ry", "cry", "phase", "cphase", "h", "ch", "u1q", "cu1q", "diag",
+            "adiag", "add", "sub", "swap", "qram")
+
+
+# Wide registers use a mix where branching gates are rare, so the state stays small.
+SPARSE_KINDS = ("x", "cx", "ccx", "add", "sub", "swap", "phase", "cphase", "qram") * 3 + (
+    "h", "ry", "cu1q")
+
+
+@pytest.mark.parametrize("seed,widths,kinds", [(1, [4, 4, 4], "all"), (2, [6, 6, 4], "all"),
+                                               (3, [5, 5, 6], "all"),
+                                               (4, [16, 16, 16, 16], "sparse"),
+                                               (5, [20, 32, 32], "sparse")])
+@pytest.mark.parametrize("amp32", [False, True])
+def test_random_circuits(sqs, seed, widths, kinds, amp32):
+    rng = np.random.default_rng(seed)
+    table = rng.integers(0, 2 ** 16, size=2 ** min(widths[0], 12)).astype(np.uint16)
+    n_gates = 150 if kinds == "all" else 90
+    circ = W.random_circuit(widths, n_gates, seed,
+                            kinds=_kinds_all() if kinds == "all" else SPARSE_KINDS,
+                            tables=[table])
+    o = oracle.run_circuit(circ)
+    g = sqs.run_circuit(circ, amp32=amp32)
+    f = compare_states(g.to_dict(), o.to_dict(), atol=1e-5 if amp32 else ATOL64,
+                       band=1e-5 if amp32 else 1e-12)
+    assert f >= (1 - 1e-6 if amp32 else 1 - 1e-10)
+    assert g.peak_nnz() == o.peak() or amp32
+
+
+def test_config1_full(sqs):
+    circ = build_config1(seed=1)
+    o = oracle.run_circuit(circ)
+    g = sqs.run_circuit(circ)
+    got, ref = g.to_dict(), o.to_dict()
+    assert compare_states(got, ref) >= 1 - 1e-10
+    assert set(got) == set(ref)
+    err = max(abs(got[k] - ref[k]) for k in ref)
+    assert err <= ATOL64
+    assert g.nnz() <= 4096 and g.peak_nnz() == o.peak()
+
+
+def test_config1_fp32(sqs):
+    circ = build_config1(seed=1)
+    o = oracle.run_circuit(circ)
+    g = sqs.run_circuit(circ, amp32=True)
+    assert compare_states(g.to_dict(), o.to_dict(), atol=1e-5, band=1e-5) >= 1 - 1e-6
+
+
+def test_config2_reduced(sqs):
+    circ = W.config2(seed=2, n_branch=16, n_perm=300, n_cancel=6)
+    n_main = len(circ["gates"]) - 6
+    o = oracle.run_circuit(circ, upto=n_main)
+    g = sqs.run_circuit(circ, upto=n_main)
+    assert g.nnz() == o.nnz() == 2 ** 16
+    _check(g, o)
+    for i, gate in enumerate(circ["gates"][n_main:]):
+        g.apply(gate)
+        o.apply(gate)
+        assert g.nnz() == o.nnz() == 2 ** 16 >> (i + 1)
+    _check(g, o)
+
+
+@pytest.mark.parametrize("amp32", [False, True])
+def test_config3_reduced(sqs, amp32):
+    circ = W.config3(seed=3, addr_bits=10, rounds=4)
+    o = oracle.run_circuit(circ)
+    g = sqs.run_circuit(circ, amp32=amp32)
+    got, ref = g.to_dict(), o.to_dict()
+    assert compare_states(got, ref, atol=1e-5 if amp32 else ATOL64,
+                          band=1e-5 if amp32 else 1e-12) >= (1 - 1e-6 if amp32 else 1 - 1e-10)
+    assert g.peak_nnz() == o.peak() or amp32
+
+
+def test_probabilities(sqs):
+    circ = build_config1(seed=1)
+    o = oracle.run_circuit(circ)
+    g = sqs.run_circuit(circ)
+    for reg in range(3):
+        p, n2 = g.probabilities(reg)
+        v, pr = o.probabilities(reg)
+        want = np.zeros_like(p)
+        want[v.astype(np.int64)] = pr
+        assert np.max(np.abs(p - want)) < 1e-13
+        assert abs(n2 - o.norm2()) < 1e-13
+
+
+def test_probabilities_wide_register_128(sqs):
+    circ = W.config3(seed=3, addr_bits=8, rounds=2)
+    o = oracle.run_circuit(circ)
+    g = sqs.run_circuit(circ)
+    p, n2 = g.probabilities(0)
+    v, pr = o.probabilities(0)
+    want = np.zeros_like(p)
+    want[v.astype(np.int64)] = pr
+    assert np.max(np.abs(p - want)) < 1e-13
+    _, n2b = g.probabilities(2, with_probs=False)
+    assert abs(n2b - o.norm2()) < 1e-13
+
+
+# ---- edge cases ---------------------------------------------------------------
+def test_empty_state_stays_empty(sqs):
+    g = sqs.State([8, 8])
+    g.h_gate(0, 0)
+    assert g.prune(10.0, wait=True) == 0
+    g.h_gate(0, 1)
+    g.x(1, 3)
+    g.ry(1, 2, 0.3)
+    assert g.nnz() == 0
+    p, n2 = g.probabilities(0)
+    assert n2 == 0.0 and not p.any()
+
+
+def test_full_cancellation(sqs):
+    g = sqs.State([4, 4])
+    for b in range(4):
+        g.h_gate(0, b)
+    for b in range(4):
+        g.h_gate(0, b)
+    assert g.to_dict().keys() == {0}
+    assert abs(g.to_dict()[0] - 1) < 1e-15
+
+
+def test_controls_never_hold(sqs):
+    lo, hi, amps = W.random_state(W64, 5000, seed=11)
+    lo &= ~np.uint64(1 << 3)  # control bit forced to 0 everywhere
+    lo = np.unique(lo)
+    amps = amps[: lo.shape[0]]
+    gs, os_ = _pair(sqs, W64, lo, np.zeros_like(lo), amps)
+    for st in (gs, os_):
+        st.h_gate(1, 0, ((0, 3, 1),))
+    got, _ = _check(gs, os_)
+    assert len(got) == lo.shape[0]
+
+
+def test_exact_capacity_growth(sqs):
+    """Capacity hint far below the final size: buffers grow on demand."""
+    g = sqs.State([24], capacity_hint=1)
+    for b in range(20):
+        g.h_gate(0, b)
+    assert g.nnz() == 2 ** 20
+    p, n2 = g.probabilities(0, with_probs=False)
+    assert abs(n2 - 1) < 1e-12
+
+
+def test_bad_arguments_leave_state_usable(sqs):
+    g = sqs.State([4, 4])
+    with pytest.raises(sqs.SqsError):
+        g.h_gate(2, 0)
+    with pytest.raises(sqs.SqsError):
+        g.h_gate(0, 4)
+    with pytest.raises(sqs.SqsError):
+        g.h_gate(0, 1, ((0, 1, 1),))   # control on the target
+    with pytest.raises(sqs.SqsError):
+        g.perm([(sqs.PERM_SWAP, 0, 0, 0, 0, ())])
+    g.h_gate(0, 1)
+    assert g.nnz() == 2
+
+
+def test_deterministic_as_a_set(sqs):
+    circ = W.config2(seed=5, n_branch=14, n_perm=150, n_cancel=4)
+    a = sqs.run_circuit(circ).to_dict()
+    b = sqs.run_circuit(circ).to_dict()
+    assert a == b  # bitwise: each output is a sum of at most two products
