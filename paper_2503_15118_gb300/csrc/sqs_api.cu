@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -20,7 +21,6 @@
 #include "sqs_internal.h"
 
 using sqs::Arr;
-using sqs::Buckets;
 using sqs::Ctl;
 using sqs::DevOp;
 using sqs::Gate1;
@@ -31,6 +31,58 @@ struct sqs_table {
   uint64_t n;
   uint32_t bytes;
 };
+
+namespace {
+
+constexpr uint32_t kBucketLog2 = 11;  // branches per merge bucket (shared-memory tile)
+constexpr uint32_t kSegLog2 = 12;     // branches per output segment (2 x bucket)
+
+// One branch buffer and its current layout.
+struct Store {
+  uint64_t* k0 = nullptr;
+  uint64_t* k1 = nullptr;
+  void* amp = nullptr;
+  uint64_t cap = 0;
+  unsigned int* segs = nullptr;  // per-segment counts (cap >> kBucketLog2 + 1 entries)
+  bool segmented = false;
+  uint32_t seg_log2 = 0;
+  uint32_t n_seg = 0;
+
+  Arr view() const {
+    Arr a;
+    a.k0 = k0;
+    a.k1 = k1;
+    a.amp = amp;
+    a.cap = cap;
+    a.seg_cnt = segmented ? segs : nullptr;
+    a.seg_log2 = seg_log2;
+    a.n_seg = n_seg;
+    return a;
+  }
+  // Slots a kernel must visit: the segments, or the dense count bound.
+  uint64_t slots(uint64_t count_ub) const {
+    return segmented ? ((uint64_t)n_seg << seg_log2) : count_ub;
+  }
+  void set_dense() {
+    segmented = false;
+    seg_log2 = 0;
+    n_seg = 0;
+  }
+  void set_segments(uint32_t log2, uint32_t n) {
+    segmented = true;
+    seg_log2 = log2;
+    n_seg = n;
+  }
+};
+
+// A queued non-interference operation; factors c0/c1 of amplitude operations
+// stay on the host and are folded into the launch's factor table.
+struct HostOp {
+  DevOp d;
+  std::complex<double> c0, c1;
+};
+
+}  // namespace
 
 struct sqs_state {
   std::vector<uint32_t> width, offset;
@@ -46,17 +98,14 @@ struct sqs_state {
   sqs_allocator alloc{};
   bool has_alloc = false;
 
-  Arr cur{}, alt{};
+  Store cur, alt, bk;
   int cur_slot = 0;
-  Buckets bk{};
-  uint64_t bk_slots = 0;  // allocated branches in the bucket arrays
-  uint32_t bk_counters = 0;
   Ctl* ctl = nullptr;
-  Ctl* ctl_host = nullptr;  // pinned mirror
-  double* scratch = nullptr;  // probabilities / format conversion
+  Ctl* ctl_host = nullptr;    // pinned mirror
+  double* scratch = nullptr;  // probabilities / format conversion / offsets
   size_t scratch_bytes = 0;
 
-  std::vector<DevOp> pending;
+  std::vector<HostOp> pending;
   OpList ops_buf;   // staging for one launch's fused operations
   uint64_t ub = 1;  // upper bound of the current branch count
   uint32_t seq = 0;
@@ -74,7 +123,7 @@ struct sqs_state {
 
 namespace {
 
-const char* kVersion = "sqs 0.1 (sm_103a)";
+const char* kVersion = "sqs 0.2 (sm_103a)";
 
 sqs_status fail(sqs_state* st, sqs_status s, const char* fmt, ...) {
   char buf[512];
@@ -113,33 +162,41 @@ void dfree(sqs_state* st, void* p) {
 
 size_t amp_bytes(const sqs_state* st) { return st->amp32 ? 8 : 16; }
 
-void free_arr(sqs_state* st, Arr& a) {
-  dfree(st, a.k0);
-  dfree(st, a.k1);
-  dfree(st, a.amp);
-  a = Arr{};
-}
-
-bool alloc_arr(sqs_state* st, Arr& a, uint64_t cap) {
-  a.k0 = (uint64_t*)dalloc(st, cap * 8);
-  a.k1 = st->kw == 2 ? (uint64_t*)dalloc(st, cap * 8) : nullptr;
-  a.amp = dalloc(st, cap * amp_bytes(st));
-  a.cap = cap;
-  if (!a.k0 || (st->kw == 2 && !a.k1) || !a.amp) {
-    free_arr(st, a);
-    return false;
-  }
-  return true;
+void free_store(sqs_state* st, Store& s) {
+  dfree(st, s.k0);
+  dfree(st, s.k1);
+  dfree(st, s.amp);
+  dfree(st, s.segs);
+  s = Store{};
 }
 
 uint64_t round_cap(uint64_t need) {
-  uint64_t c = 1024;
+  uint64_t c = 1ull << kSegLog2;
   while (c < need) c = c + c / 2;
-  return c;
+  return (c + (1ull << kSegLog2) - 1) & ~((1ull << kSegLog2) - 1);
+}
+
+// Makes s hold at least `need` branches (contents are not kept).
+bool ensure_store(sqs_state* st, Store& s, uint64_t need) {
+  if (s.k0 && s.cap >= need) return true;
+  free_store(st, s);
+  const uint64_t cap = round_cap(need);
+  const uint64_t nseg = (cap >> kBucketLog2) + 1;
+  s.k0 = (uint64_t*)dalloc(st, cap * 8);
+  s.k1 = st->kw == 2 ? (uint64_t*)dalloc(st, cap * 8) : nullptr;
+  s.amp = dalloc(st, cap * amp_bytes(st));
+  s.segs = (unsigned int*)dalloc(st, nseg * 4);
+  s.cap = cap;
+  if (!s.k0 || (st->kw == 2 && !s.k1) || !s.amp || !s.segs) {
+    free_store(st, s);
+    return false;
+  }
+  cudaMemsetAsync(s.segs, 0, nseg * 4, st->stream);
+  return true;
 }
 
 uint64_t max_branches(const sqs_state* st) {
-  return st->total_bits >= 63 ? (1ull << 63) : (1ull << st->total_bits);
+  return st->total_bits >= 62 ? (1ull << 62) : (1ull << st->total_bits);
 }
 
 // Brackets one launch with trace events when tracing is on.
@@ -211,159 +268,190 @@ sqs_status check_usable(sqs_state* st) {
   return st->sticky;
 }
 
-// Makes `alt` hold at least `need` branches.
-sqs_status ensure_alt(sqs_state* st, uint64_t need) {
-  if (st->alt.cap >= need && st->alt.k0) return SQS_OK;
-  free_arr(st, st->alt);
-  if (!alloc_arr(st, st->alt, round_cap(need)))
-    return fail(st, SQS_ERR_OOM, "cannot allocate %llu branches", (unsigned long long)need);
-  return SQS_OK;
+// Folds the amplitude factors of one group of MUL ops into entries
+// [n_tab, n_tab + 2^bits) of the factor table: entry idx is the product, in
+// operation order, of the factors idx selects (2-bit or 1-bit fields).
+struct Group {
+  std::vector<const HostOp*> ops;
+  std::vector<uint32_t> shift, nbits;
+  uint32_t bits = 0;
+};
+
+void fold_group(Group& g, OpList& L) {
+  if (g.ops.empty()) return;
+  const uint32_t size = 1u << g.bits;
+  for (uint32_t idx = 0; idx < size; ++idx) {
+    std::complex<double> f(1.0, 0.0);
+    for (size_t j = 0; j < g.ops.size(); ++j) {
+      const uint32_t oc = (idx >> g.shift[j]) & ((1u << g.nbits[j]) - 1u);
+      if (oc == 1) f *= g.ops[j]->c0;
+      else if (oc == 2) f *= g.ops[j]->c1;
+    }
+    L.tab[L.n_tab + idx] = make_double2(f.real(), f.imag());
+  }
+  DevOp t;
+  std::memset(&t, 0, sizeof(t));
+  t.kind = sqs::OP_TABLE;
+  t.sel_bit = 128;
+  t.tab_off = L.n_tab;
+  L.op[L.n++] = t;
+  L.n_tab += size;
+  g = Group{};
 }
 
-sqs_status ensure_buckets(sqs_state* st, uint32_t B, uint32_t C) {
-  const uint64_t slots = (uint64_t)B * C;
-  if (st->bk_slots < slots || !st->bk.k0) {
-    dfree(st, st->bk.k0);
-    dfree(st, st->bk.k1);
-    dfree(st, st->bk.amp);
-    const uint64_t cap = round_cap(slots);
-    st->bk.k0 = (uint64_t*)dalloc(st, cap * 8);
-    st->bk.k1 = st->kw == 2 ? (uint64_t*)dalloc(st, cap * 8) : nullptr;
-    st->bk.amp = dalloc(st, cap * amp_bytes(st));
-    st->bk_slots = cap;
-    if (!st->bk.k0 || (st->kw == 2 && !st->bk.k1) || !st->bk.amp)
-      return fail(st, SQS_ERR_OOM, "cannot allocate merge buckets");
-  }
-  if (st->bk_counters < B || !st->bk.count) {
-    dfree(st, st->bk.count);
-    const uint32_t nc = std::max<uint32_t>(B, 1024);
-    st->bk.count = (unsigned int*)dalloc(st, (size_t)nc * 4);
-    if (!st->bk.count) return fail(st, SQS_ERR_OOM, "cannot allocate bucket counters");
-    cudaMemsetAsync(st->bk.count, 0, (size_t)nc * 4, st->stream);
-    st->bk_counters = nc;
-  }
-  st->bk.B = B;
-  st->bk.C = C;
-  return SQS_OK;
-}
-
-// Packs the queued operations into launch-sized lists.
-void pack_ops(const std::vector<DevOp>& ops, size_t from, size_t to, OpList& L) {
-  L.n = (uint32_t)(to - from);
+// Packs pending ops [from, ...) into one launch's list; returns how many
+// were consumed (the list or its factor table filled up, or all done).
+size_t pack_ops(const std::vector<HostOp>& ops, size_t from, OpList& L) {
+  L.n = 0;
+  L.n_tab = 0;
   L.touches_keys = L.touches_amps = L.drops = 0;
-  for (size_t i = from; i < to; ++i) {
-    L.op[i - from] = ops[i];
-    switch (ops[i].kind) {
-      case sqs::OP_MUL:
-        L.touches_amps = 1;
-        break;
-      case sqs::OP_MUL_XOR:
-        L.touches_amps = 1;
-        L.touches_keys = 1;
-        break;
-      case sqs::OP_PRUNE:
-        L.drops = 1;
-        break;
-      default:
-        L.touches_keys = 1;
-        break;
+  Group g;
+  size_t i = from;
+  constexpr uint32_t kGroupBits = 8;
+  for (; i < ops.size(); ++i) {
+    const HostOp& h = ops[i];
+    const uint32_t kind = h.d.kind;
+    const bool mul = kind == sqs::OP_MUL || kind == sqs::OP_MUL_XOR;
+    const uint32_t nb = mul ? (h.d.sel_bit < 128 ? 2u : 1u) : 0u;
+    // Room for this op, the table ops still to come, and the factor table.
+    const bool closes = (mul && g.bits + nb > kGroupBits) || kind == sqs::OP_PRUNE;
+    const uint32_t pend_tab = g.ops.empty() ? 0 : (1u << g.bits);
+    uint32_t need_tab = L.n_tab + pend_tab;
+    if (mul) need_tab = closes ? need_tab + (1u << nb) : L.n_tab + (1u << (g.bits + nb));
+    const uint32_t groups_after = (closes || g.ops.empty() ? 0u : 1u) + (mul ? 1u : 0u) +
+                                  (closes && !g.ops.empty() ? 1u : 0u);
+    if (L.n + 1 + groups_after > (uint32_t)sqs::kMaxOps || need_tab > (uint32_t)sqs::kTabEntries)
+      break;
+    if (closes) fold_group(g, L);
+    DevOp d = h.d;
+    if (mul) {
+      d.shift = g.bits;
+      g.ops.push_back(&h);
+      g.shift.push_back(g.bits);
+      g.nbits.push_back(nb);
+      g.bits += nb;
+      L.touches_amps = 1;
+      if (kind == sqs::OP_MUL_XOR) L.touches_keys = 1;
+    } else if (kind == sqs::OP_PRUNE) {
+      L.drops = 1;
+    } else {
+      L.touches_keys = 1;
     }
+    L.op[L.n++] = d;
   }
+  fold_group(g, L);
+  return i - from;
 }
 
-// Runs queued operations as standalone passes, leaving at most kMaxOps for
-// the kernel that follows (which fuses them).  keep_tail = false flushes all.
-sqs_status run_pending(sqs_state* st, bool keep_tail) {
-  size_t n = st->pending.size();
-  size_t upto = keep_tail ? (n > (size_t)sqs::kMaxOps ? n - sqs::kMaxOps : 0) : n;
-  size_t from = 0;
-  OpList& L = st->ops_buf;
-  while (from < upto) {
-    const size_t to = std::min(upto, from + (size_t)sqs::kMaxOps);
-    pack_ops(st->pending, from, to, L);
-    cudaError_t e;
-    if (L.drops) {
-      const uint64_t need = st->ub;
-      sqs_status s = ensure_alt(st, need);
-      if (s != SQS_OK) return s;
-      const int out_slot = (st->cur_slot + 1) & 3;
+// Standalone pass over the current state with the packed list.
+sqs_status run_list(sqs_state* st, const OpList& L) {
+  cudaError_t e = cudaSuccess;
+  const uint64_t in_slots = st->cur.slots(st->ub);
+  if (L.drops) {
+    const uint64_t chunks = std::max<uint64_t>(1, (in_slots + (1ull << kSegLog2) - 1) >> kSegLog2);
+    if (chunks > 0xffffffffull) return st->sticky = fail(st, SQS_ERR_CAPACITY, "state too large");
+    if (!ensure_store(st, st->alt, chunks << kSegLog2))
+      return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate %llu branches",
+                               (unsigned long long)(chunks << kSegLog2));
+    st->alt.set_segments(kSegLog2, (uint32_t)chunks);
+    const int out_slot = (st->cur_slot + 1) & 3;
+    {
       Traced tr(st, SQS_K_COMPACT);
-      e = sqs::launch_apply_compact(launch_of(st, st->ub), st->kw, st->amp32, st->ctl, st->cur,
-                                    st->cur_slot, st->alt, out_slot, L);
-      std::swap(st->cur, st->alt);
-      st->cur_slot = out_slot;
-    } else if (L.touches_keys || L.touches_amps) {
-      Traced tr(st, SQS_K_APPLY);
-      e = sqs::launch_apply_inplace(launch_of(st, st->ub), st->kw, st->amp32, st->ctl, st->cur,
-                                    st->cur_slot, L);
-    } else {
-      e = cudaSuccess;
+      e = sqs::launch_apply_compact(launch_of(st, in_slots), st->kw, st->amp32, st->ctl,
+                                    st->cur.view(), st->cur_slot, st->alt.view(), out_slot, L);
     }
-    if (e != cudaSuccess) return cuda_fail(st, e, "launch");
-    from = to;
+    std::swap(st->cur, st->alt);
+    st->cur_slot = out_slot;
+  } else if (L.touches_keys || L.touches_amps) {
+    Traced tr(st, SQS_K_APPLY);
+    e = sqs::launch_apply_inplace(launch_of(st, in_slots), st->kw, st->amp32, st->ctl,
+                                  st->cur.view(), st->cur_slot, L);
   }
-  st->pending.erase(st->pending.begin(), st->pending.begin() + upto);
+  if (e != cudaSuccess) return cuda_fail(st, e, "launch");
+  return SQS_OK;
+}
+
+// Runs queued operations as standalone passes.  With keep_tail, the last
+// launch-sized group is left packed in st->ops_buf for the kernel that
+// follows to fuse; otherwise everything runs.
+sqs_status run_pending(sqs_state* st, bool keep_tail) {
+  OpList& L = st->ops_buf;
+  size_t from = 0;
+  for (;;) {
+    const size_t used = pack_ops(st->pending, from, L);
+    const bool last = from + used >= st->pending.size();
+    if (last && keep_tail) break;
+    sqs_status s = run_list(st, L);
+    if (s != SQS_OK) return s;
+    from += used;
+    if (last) {
+      L.n = 0;
+      L.n_tab = 0;
+      L.touches_keys = L.touches_amps = L.drops = 0;
+      break;
+    }
+  }
+  st->pending.clear();
   return SQS_OK;
 }
 
 // One interference step: fused pending run + partition + pair.
 sqs_status run_branching(sqs_state* st, const Gate1& g) {
-  sqs_status s = run_pending(st, true);
-  if (s != SQS_OK) return s;
-  OpList& L = st->ops_buf;
-  pack_ops(st->pending, 0, st->pending.size(), L);
-  st->pending.clear();
-  // From here on a failure leaves the queue half-applied: errors are sticky.
-
-  uint64_t out_ub = std::min(max_branches(st), 2 * st->ub);
-  if (st->alt.cap < out_ub) {
+  sqs_status s = run_pending(st, true);  // leaves the fused tail in ops_buf
+  if (s != SQS_OK) return st->sticky = s;
+  const OpList& L = st->ops_buf;
+  const uint64_t C = 1ull << kBucketLog2;
+  const uint64_t target = C * 3 / 4;  // mean bucket fill: overflow is ~18 sigma away
+  uint64_t B = std::max<uint64_t>(1, (st->ub + target - 1) / target);
+  if ((B << kSegLog2) > st->alt.cap && st->ub > 1) {
     // The bound outgrew the allocation: learn the exact count first.
     s = sync_ctl(st);
     if (s != SQS_OK) return s;
-    out_ub = std::min(max_branches(st), 2 * st->ub);
+    B = std::max<uint64_t>(1, (st->ub + target - 1) / target);
   }
-  s = ensure_alt(st, out_ub);
-  if (s != SQS_OK) return st->sticky = s;
-  const uint32_t C = (uint32_t)sqs::pair_capacity(st->kw, st->amp32);
-  const uint64_t target = (uint64_t)C * 3 / 4;
-  const uint64_t B64 = std::max<uint64_t>(1, (st->ub + target - 1) / target);
-  if (B64 > 0x7fffffffull) return st->sticky = fail(st, SQS_ERR_CAPACITY, "too many buckets");
-  s = ensure_buckets(st, (uint32_t)B64, C);
-  if (s != SQS_OK) return st->sticky = s;
+  if (B > 0x7fffffffull) return st->sticky = fail(st, SQS_ERR_CAPACITY, "too many buckets");
+  if (!ensure_store(st, st->bk, B << kBucketLog2) || !ensure_store(st, st->alt, B << kSegLog2))
+    return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate %llu branches",
+                             (unsigned long long)(B << kSegLog2));
+  st->bk.set_segments(kBucketLog2, (uint32_t)B);
+  st->alt.set_segments(kSegLog2, (uint32_t)B);
 
+  const uint64_t in_slots = st->cur.slots(st->ub);
   const int out_slot = (st->cur_slot + 1) & 3;
   cudaError_t e;
   {
     Traced tr(st, SQS_K_PARTITION);
-    e = sqs::launch_partition(launch_of(st, st->ub), st->kw, st->amp32, st->ctl, st->cur,
-                              st->cur_slot, L, g, st->bk, st->alt, out_slot);
+    e = sqs::launch_partition(launch_of(st, in_slots), st->kw, st->amp32, st->ctl,
+                              st->cur.view(), st->cur_slot, L, g, st->bk.view());
   }
   if (e != cudaSuccess) return cuda_fail(st, e, "partition launch");
   {
     Traced tr(st, SQS_K_PAIR);
-    e = sqs::launch_pair(launch_of(st, st->ub), st->kw, st->amp32, st->ctl, g, st->bk, st->alt,
-                         out_slot);
+    e = sqs::launch_pair(launch_of(st, in_slots), st->kw, st->amp32, st->ctl, g, st->bk.view(),
+                         st->alt.view(), out_slot);
   }
   if (e != cudaSuccess) return cuda_fail(st, e, "pair launch");
   std::swap(st->cur, st->alt);
   st->cur_slot = out_slot;
-  st->ub = out_ub;
+  st->ub = std::min(max_branches(st), 2 * st->ub);
   return SQS_OK;
 }
 
 bool is_zero(double re, double im) { return re == 0.0 && im == 0.0; }
 
-DevOp blank_op(uint32_t kind) {
-  DevOp o;
-  std::memset(&o, 0, sizeof(o));
-  o.kind = kind;
-  o.sel_bit = 128;
+HostOp blank_op(uint32_t kind) {
+  HostOp o;
+  std::memset(&o.d, 0, sizeof(o.d));
+  o.d.kind = kind;
+  o.d.sel_bit = 128;
+  o.c0 = o.c1 = std::complex<double>(1.0, 0.0);
   return o;
 }
 
-void push_prune(sqs_state* st) {
-  DevOp o = blank_op(sqs::OP_PRUNE);
-  o.eps2 = st->eps * st->eps;
+void push_prune(sqs_state* st, double eps) {
+  HostOp o = blank_op(sqs::OP_PRUNE);
+  o.d.eps = eps;
+  o.d.eps2 = eps * eps;
   st->pending.push_back(o);
 }
 
@@ -384,38 +472,54 @@ sqs_status apply_1q(sqs_state* st, uint32_t reg, uint32_t bit, const double* m,
 
   if (mode == 0 && is_zero(m[2], m[3]) && is_zero(m[4], m[5])) {
     // Diagonal: phases only (the _operate_diagonal strategy, Supp. B).
-    DevOp o = blank_op(sqs::OP_MUL);
-    o.pmask[0] = cm[0], o.pmask[1] = cm[1], o.pval[0] = cv[0], o.pval[1] = cv[1];
-    o.sel_bit = t;
-    o.c[0] = m[0], o.c[1] = m[1], o.c[2] = m[6], o.c[3] = m[7];
+    HostOp o = blank_op(sqs::OP_MUL);
+    o.d.pmask[0] = cm[0], o.d.pmask[1] = cm[1], o.d.pval[0] = cv[0], o.d.pval[1] = cv[1];
+    o.d.sel_bit = t;
+    o.c0 = std::complex<double>(m[0], m[1]);
+    o.c1 = std::complex<double>(m[6], m[7]);
     st->pending.push_back(o);
-    push_prune(st);
+    push_prune(st, st->eps);
     return SQS_OK;
   }
   if (mode == 0 && is_zero(m[0], m[1]) && is_zero(m[6], m[7])) {
     // Anti-diagonal: flip plus phase (the _operate_off_diagonal strategy).
     // A branch with bit 0 moves to bit 1 with factor U10; bit 1 moves to 0 with U01.
-    DevOp o = blank_op(sqs::OP_MUL_XOR);
-    o.pmask[0] = cm[0], o.pmask[1] = cm[1], o.pval[0] = cv[0], o.pval[1] = cv[1];
-    o.sel_bit = t;
-    o.c[0] = m[4], o.c[1] = m[5], o.c[2] = m[2], o.c[3] = m[3];
-    o.xmask[t >> 6] = 1ull << (t & 63);
+    HostOp o = blank_op(sqs::OP_MUL_XOR);
+    o.d.pmask[0] = cm[0], o.d.pmask[1] = cm[1], o.d.pval[0] = cv[0], o.d.pval[1] = cv[1];
+    o.d.sel_bit = t;
+    o.c0 = std::complex<double>(m[4], m[5]);
+    o.c1 = std::complex<double>(m[2], m[3]);
+    o.d.xmask[t >> 6] = 1ull << (t & 63);
     st->pending.push_back(o);
-    push_prune(st);
+    push_prune(st, st->eps);
     return SQS_OK;
   }
   Gate1 g;
   std::memset(&g, 0, sizeof(g));
   g.t = t;
   g.mode = (uint32_t)mode;
+  if (mode == 0 && m[1] == 0.0 && m[3] == 0.0 && m[5] == 0.0 && m[7] == 0.0) g.mode = 2;
   g.cmask[0] = cm[0], g.cmask[1] = cm[1], g.cval[0] = cv[0], g.cval[1] = cv[1];
   if (mode == 0)
     for (int i = 0; i < 8; ++i) g.u[i] = m[i];
+  for (int i = 0; i < 8; ++i) g.uf[i] = (float)g.u[i];
+  if (mode == 0) {
+    // Rows of a column equal up to sign share one product per branch.
+    auto same = [&](int r0, int r1, double sgn) {
+      return m[2 * r1] == sgn * m[2 * r0] && m[2 * r1 + 1] == sgn * m[2 * r0 + 1];
+    };
+    if (same(0, 2, 1.0)) g.reuse |= 1u;
+    else if (same(0, 2, -1.0)) g.reuse |= 1u | 4u;
+    if (same(1, 3, 1.0)) g.reuse |= 2u;
+    else if (same(1, 3, -1.0)) g.reuse |= 2u | 8u;
+  }
   g.ang_off = mode == 1 ? st->offset[angle_reg] : 0;
   g.ang_w = mode == 1 ? st->width[angle_reg] : 0;
   g.scale = scale;
   g.offset = offset;
+  g.eps = st->eps;
   g.eps2 = st->eps * st->eps;
+  g.epsf = (float)st->eps;
   return run_branching(st, g);
 }
 
@@ -423,6 +527,44 @@ sqs_status flush_all(sqs_state* st) {
   sqs_status s = check_usable(st);
   if (s != SQS_OK) return s;
   return run_pending(st, false);
+}
+
+sqs_status ensure_scratch(sqs_state* st, size_t bytes) {
+  if (st->scratch_bytes >= bytes && st->scratch) return SQS_OK;
+  dfree(st, st->scratch);
+  st->scratch = (double*)dalloc(st, bytes);
+  st->scratch_bytes = st->scratch ? bytes : 0;
+  return st->scratch ? SQS_OK : fail(st, SQS_ERR_OOM, "cannot allocate scratch");
+}
+
+// Copies a segmented current array into a dense one (waits).
+sqs_status densify(sqs_state* st) {
+  if (!st->cur.segmented) return SQS_OK;
+  const uint32_t ns = st->cur.n_seg;
+  std::vector<unsigned int> cnt(ns);
+  cudaError_t e = cudaMemcpyAsync(cnt.data(), st->cur.segs, (size_t)ns * 4,
+                                  cudaMemcpyDeviceToHost, st->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) return cuda_fail(st, e, "densify");
+  std::vector<uint64_t> off(ns);
+  uint64_t total = 0;
+  for (uint32_t i = 0; i < ns; ++i) {
+    off[i] = total;
+    total += cnt[i];
+  }
+  sqs_status s = ensure_scratch(st, (size_t)ns * 8 + 16);
+  if (s != SQS_OK) return s;
+  if (!ensure_store(st, st->alt, std::max<uint64_t>(total, 1)))
+    return st->sticky = fail(st, SQS_ERR_OOM, "densify");
+  st->alt.set_dense();
+  e = cudaMemcpyAsync(st->scratch, off.data(), (size_t)ns * 8, cudaMemcpyHostToDevice, st->stream);
+  if (e == cudaSuccess)
+    e = sqs::launch_densify(launch_of(st, total), st->kw, st->amp32, st->cur.view(),
+                            (const uint64_t*)st->scratch, st->alt.view());
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) return cuda_fail(st, e, "densify");
+  std::swap(st->cur, st->alt);
+  return SQS_OK;
 }
 
 }  // namespace
@@ -477,7 +619,7 @@ sqs_status sqs_state_create(const uint32_t* reg_widths, uint32_t n_regs, uint32_
   }
   st->ctl = (Ctl*)dalloc(st, sizeof(Ctl));
   const uint64_t cap = round_cap(std::max<uint64_t>(capacity_hint, 1024));
-  if (!st->ctl || !alloc_arr(st, st->cur, cap) || !alloc_arr(st, st->alt, cap)) {
+  if (!st->ctl || !ensure_store(st, st->cur, cap) || !ensure_store(st, st->alt, cap)) {
     sqs_state_destroy(st);
     return SQS_ERR_OOM;
   }
@@ -492,12 +634,9 @@ sqs_status sqs_state_create(const uint32_t* reg_widths, uint32_t n_regs, uint32_
 void sqs_state_destroy(sqs_state* st) {
   if (!st) return;
   cudaStreamSynchronize(st->stream);
-  free_arr(st, st->cur);
-  free_arr(st, st->alt);
-  dfree(st, st->bk.k0);
-  dfree(st, st->bk.k1);
-  dfree(st, st->bk.amp);
-  dfree(st, st->bk.count);
+  free_store(st, st->cur);
+  free_store(st, st->alt);
+  free_store(st, st->bk);
   dfree(st, st->ctl);
   dfree(st, st->scratch);
   for (sqs_table* t : st->tables) {
@@ -518,10 +657,12 @@ sqs_status sqs_state_reset(sqs_state* st) {
   st->err.clear();
   st->cur_slot = 0;
   st->ub = 1;
-  if (st->bk.count) cudaMemsetAsync(st->bk.count, 0, (size_t)st->bk_counters * 4, st->stream);
+  if (st->bk.segs)
+    cudaMemsetAsync(st->bk.segs, 0, ((st->bk.cap >> kBucketLog2) + 1) * 4, st->stream);
+  st->cur.set_dense();
   st->call = 1;  // API calls are numbered from the reset
   Traced tr(st, SQS_K_INIT);
-  cudaError_t e = sqs::launch_init(launch_of(st, 1), st->ctl, st->cur, 0, st->amp32);
+  cudaError_t e = sqs::launch_init(launch_of(st, 1), st->ctl, st->cur.view(), 0, st->amp32);
   if (e != cudaSuccess) return cuda_fail(st, e, "reset");
   return SQS_OK;
 }
@@ -569,7 +710,7 @@ sqs_status sqs_apply_perm(sqs_state* st, const sqs_perm_op* ops, uint32_t n_ops)
   if (s != SQS_OK) return s;
   st->call++;
   if (n_ops && !ops) return fail(st, SQS_ERR_ARG, "null ops");
-  std::vector<DevOp> add;
+  std::vector<HostOp> add;
   add.reserve(n_ops);
   const uint32_t nr = (uint32_t)st->width.size();
   for (uint32_t i = 0; i < n_ops; ++i) {
@@ -578,7 +719,8 @@ sqs_status sqs_apply_perm(sqs_state* st, const sqs_perm_op* ops, uint32_t n_ops)
     uint64_t cm[2], cv[2];
     if (!encode_ctrls(st, p.ctrl, p.n_ctrl, cm, cv))
       return fail(st, SQS_ERR_ARG, "op %u: bad controls", i);
-    DevOp o = blank_op(sqs::OP_XOR);
+    HostOp h = blank_op(sqs::OP_XOR);
+    DevOp& o = h.d;
     o.pmask[0] = cm[0], o.pmask[1] = cm[1], o.pval[0] = cv[0], o.pval[1] = cv[1];
     o.dst_off = st->offset[p.reg];
     o.dst_w = st->width[p.reg];
@@ -626,7 +768,7 @@ sqs_status sqs_apply_perm(sqs_state* st, const sqs_perm_op* ops, uint32_t n_ops)
       default:
         return fail(st, SQS_ERR_ARG, "op %u: unknown kind %u", i, p.kind);
     }
-    add.push_back(o);
+    add.push_back(h);
   }
   st->pending.insert(st->pending.end(), add.begin(), add.end());
   return SQS_OK;
@@ -639,10 +781,9 @@ sqs_status sqs_apply_phase(sqs_state* st, const sqs_ctrl* pred, uint32_t n_pred,
   if (!std::isfinite(phi)) return fail(st, SQS_ERR_ARG, "non-finite phase");
   uint64_t cm[2], cv[2];
   if (!encode_ctrls(st, pred, n_pred, cm, cv)) return fail(st, SQS_ERR_ARG, "bad predicates");
-  DevOp o = blank_op(sqs::OP_MUL);
-  o.pmask[0] = cm[0], o.pmask[1] = cm[1], o.pval[0] = cv[0], o.pval[1] = cv[1];
-  o.c[0] = std::cos(phi);
-  o.c[1] = std::sin(phi);
+  HostOp o = blank_op(sqs::OP_MUL);
+  o.d.pmask[0] = cm[0], o.d.pmask[1] = cm[1], o.d.pval[0] = cv[0], o.d.pval[1] = cv[1];
+  o.c0 = std::complex<double>(std::cos(phi), std::sin(phi));
   st->pending.push_back(o);
   return SQS_OK;
 }
@@ -688,14 +829,14 @@ static sqs_status qram(sqs_state* st, uint32_t addr_reg, uint32_t data_reg, cons
   bool owned = false;
   for (sqs_table* x : st->tables) owned |= (x == t);
   if (!owned) return fail(st, SQS_ERR_ARG, "table belongs to another state");
-  DevOp o = blank_op(sqs::OP_QRAM);
-  o.dst_off = st->offset[data_reg];
-  o.dst_w = st->width[data_reg];
-  o.src_off = st->offset[addr_reg];
-  o.src_w = st->width[addr_reg];
-  o.table = t->dev;
-  o.n_entries = t->n;
-  o.entry_bytes = t->bytes;
+  HostOp o = blank_op(sqs::OP_QRAM);
+  o.d.dst_off = st->offset[data_reg];
+  o.d.dst_w = st->width[data_reg];
+  o.d.src_off = st->offset[addr_reg];
+  o.d.src_w = st->width[addr_reg];
+  o.d.table = t->dev;
+  o.d.n_entries = t->n;
+  o.d.constant = t->bytes;
   st->pending.push_back(o);
   return SQS_OK;
 }
@@ -714,9 +855,7 @@ sqs_status sqs_prune(sqs_state* st, double eps, uint64_t* nnz_out) {
   sqs_status s = check_usable(st);
   if (s != SQS_OK) return s;
   if (!(eps >= 0.0) || std::isinf(eps)) return fail(st, SQS_ERR_ARG, "bad eps");
-  DevOp o = blank_op(sqs::OP_PRUNE);
-  o.eps2 = eps * eps;
-  st->pending.push_back(o);
+  push_prune(st, eps);
   s = run_pending(st, false);
   if (s != SQS_OK) return s;
   if (nnz_out) {
@@ -727,13 +866,6 @@ sqs_status sqs_prune(sqs_state* st, double eps, uint64_t* nnz_out) {
   return SQS_OK;
 }
 
-static sqs_status ensure_scratch(sqs_state* st, size_t bytes) {
-  if (st->scratch_bytes >= bytes && st->scratch) return SQS_OK;
-  dfree(st, st->scratch);
-  st->scratch = (double*)dalloc(st, bytes);
-  st->scratch_bytes = st->scratch ? bytes : 0;
-  return st->scratch ? SQS_OK : fail(st, SQS_ERR_OOM, "cannot allocate scratch");
-}
 
 sqs_status sqs_probabilities_device(sqs_state* st, uint32_t reg, double* probs_dev,
                                     double* norm2_dev) {
@@ -750,8 +882,9 @@ sqs_status sqs_probabilities_device(sqs_state* st, uint32_t reg, double* probs_d
   if (e == cudaSuccess && norm2_dev) e = cudaMemsetAsync(norm2_dev, 0, sizeof(double), st->stream);
   if (e == cudaSuccess) {
     Traced tr(st, SQS_K_PROB);
-    e = sqs::launch_probabilities(launch_of(st, st->ub), st->kw, st->amp32, st->ctl, st->cur,
-                                  st->cur_slot, st->offset[reg], w, probs_dev, norm2_dev);
+    e = sqs::launch_probabilities(launch_of(st, st->cur.slots(st->ub)), st->kw, st->amp32,
+                                  st->ctl, st->cur.view(), st->cur_slot, st->offset[reg], w,
+                                  probs_dev, norm2_dev);
   }
   if (e != cudaSuccess) return cuda_fail(st, e, "probabilities");
   return SQS_OK;
@@ -812,6 +945,8 @@ sqs_status sqs_export(sqs_state* st, uint64_t* keys, double* amps, uint64_t cap,
   if (cnt > cap) return fail(st, SQS_ERR_ARG, "export needs %llu branches", (unsigned long long)cnt);
   if (cnt == 0) return SQS_OK;
   if (!keys || !amps) return fail(st, SQS_ERR_ARG, "null buffers");
+  s = densify(st);
+  if (s != SQS_OK) return s;
   cudaError_t e;
   if (st->kw == 1) {
     e = cudaMemcpyAsync(keys, st->cur.k0, cnt * 8, cudaMemcpyDeviceToHost, st->stream);
@@ -825,7 +960,8 @@ sqs_status sqs_export(sqs_state* st, uint64_t* keys, double* amps, uint64_t cap,
     if (st->amp32) {
       s = ensure_scratch(st, cnt * 16);
       if (s != SQS_OK) return s;
-      e = sqs::launch_to_f64(launch_of(st, cnt), st->ctl, st->cur, st->cur_slot, st->scratch);
+      e = sqs::launch_to_f64(launch_of(st, cnt), st->ctl, st->cur.view(), st->cur_slot,
+                             st->scratch);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(amps, st->scratch, cnt * 16, cudaMemcpyDeviceToHost, st->stream);
     } else {
@@ -852,10 +988,9 @@ sqs_status sqs_import(sqs_state* st, const uint64_t* keys, const double* amps, u
                                               (unsigned long long)i);
   }
   st->pending.clear();
-  if (st->cur.cap < n) {
-    free_arr(st, st->cur);
-    if (!alloc_arr(st, st->cur, round_cap(n))) return fail(st, SQS_ERR_OOM, "import");
-  }
+  if (!ensure_store(st, st->cur, std::max<uint64_t>(n, 1)))
+    return fail(st, SQS_ERR_OOM, "import");
+  st->cur.set_dense();
   cudaError_t e = cudaSuccess;
   if (n) {
     if (st->kw == 1) {
@@ -872,7 +1007,7 @@ sqs_status sqs_import(sqs_state* st, const uint64_t* keys, const double* amps, u
         if (s != SQS_OK) return s;
         e = cudaMemcpyAsync(st->scratch, amps, n * 16, cudaMemcpyHostToDevice, st->stream);
         if (e == cudaSuccess)
-          e = sqs::launch_from_f64(launch_of(st, n), st->ctl, st->cur, st->scratch, n);
+          e = sqs::launch_from_f64(launch_of(st, n), st->ctl, st->cur.view(), st->scratch, n);
       } else {
         e = cudaMemcpyAsync(st->cur.amp, amps, n * 16, cudaMemcpyHostToDevice, st->stream);
       }

@@ -12,58 +12,75 @@ namespace sqs {
 // in registers by whichever kernel next streams the state (Sec. II.D.1: every
 // branch is processed independently, so a run of such operations is one
 // per-branch function and one pass over memory).
+//
+// Amplitude factors are folded: each OP_MUL / OP_MUL_XOR only records its
+// outcome (not applied / factor c0 / factor c1) in a few bits of a per-branch
+// index, and OP_TABLE multiplies the amplitude once by the product of the
+// selected factors, precomputed on the host for every index.  FP64 arithmetic
+// is the scarce resource on this GPU; integer work is not.
 // ---------------------------------------------------------------------------
 enum OpKind : uint32_t {
-  OP_XOR = 0,        // key ^= xmask                                 (X, CNOT, Toffoli)
+  OP_XOR = 0,        // key ^= xmask                                   (X, CNOT, Toffoli)
   OP_ADD_REG = 1,    // dst := dst + src  (mod 2^w)
   OP_SUB_REG = 2,    // dst := dst - src
   OP_ADD_CONST = 3,  // dst := dst + constant
   OP_SWAP = 4,       // exchange dst and src fields (equal width)
   OP_QRAM = 5,       // dst := dst XOR (T[src] & mask(w_dst)), src = address field
-  OP_MUL = 6,        // amp *= (bit sel of key ? c1 : c0)             (phases, diag U)
-  OP_MUL_XOR = 7,    // amp *= (bit sel ? c1 : c0); key ^= xmask        (anti-diagonal U)
-  OP_PRUNE = 8       // drop the branch when |amp|^2 < eps2
+  OP_MUL = 6,        // record factor choice (bit sel of key: c1, else c0) (phases, diag U)
+  OP_MUL_XOR = 7,    // the same, then key ^= xmask                     (anti-diagonal U)
+  OP_TABLE = 8,      // amp *= tab[tab_off + idx] unless idx == 0; idx := 0
+  OP_PRUNE = 9       // drop the branch when |amp| < eps
 };
 
 struct DevOp {
   uint32_t kind;
   uint32_t dst_off, dst_w;  // destination field (bit offset, width)
   uint32_t src_off, src_w;  // source field (register operand or QRAM address)
-  uint32_t sel_bit;         // OP_MUL*: key bit choosing c0 / c1 (128 = always c0)
-  uint32_t entry_bytes;     // OP_QRAM: 1, 2, 4 or 8
-  uint32_t pad0;
+  uint32_t sel_bit;         // OP_MUL*: key bit choosing c0 / c1 (128 = no choice)
+  uint32_t shift;           // OP_MUL*: position of this op's outcome in the index
+  uint32_t tab_off;         // OP_TABLE: first entry of this group's table
   uint64_t pmask[2], pval[2];  // predicate: (key & pmask) == pval
   uint64_t xmask[2];           // OP_XOR / OP_MUL_XOR
-  uint64_t constant;           // OP_ADD_CONST (already reduced mod 2^w)
+  uint64_t constant;           // OP_ADD_CONST (already reduced mod 2^w); QRAM: entry bytes
   uint64_t n_entries;          // OP_QRAM table length
   const void* table;           // OP_QRAM device table
-  double c[4];                 // OP_MUL*: c0 = (c[0], c[1]), c1 = (c[2], c[3])
-  double eps2;                 // OP_PRUNE
+  double eps, eps2;            // OP_PRUNE
 };
 
-constexpr int kMaxOps = 48;  // fused operations per launch (kernel parameter space)
+constexpr int kMaxOps = 64;      // fused operations per launch
+constexpr int kTabEntries = 512;  // folded factor entries per launch
 
 struct OpList {
   uint32_t n;
   uint32_t touches_keys;  // some op changes keys
   uint32_t touches_amps;  // some op changes amplitudes
   uint32_t drops;         // some op may drop branches (OP_PRUNE)
+  uint32_t n_tab;         // used entries of tab
+  uint32_t pad[3];
   DevOp op[kMaxOps];
+  double2 tab[kTabEntries];
 };
 
 // ---------------------------------------------------------------------------
 // Device memory views.
 // ---------------------------------------------------------------------------
-struct Arr {          // one SoA branch array
+// One SoA branch array.  Dense (seg_cnt == null): branches [0, n) with n in
+// the control block.  Segmented: segment s holds seg_cnt[s] branches starting
+// at s << seg_log2; the slots after them are unused.  Kernels that compact
+// write one segment per CTA, which needs no global ordering.
+struct Arr {
   uint64_t* k0;       // key bits 0..63
   uint64_t* k1;       // key bits 64..127 (null when keys are one word)
   void* amp;          // double2[cap] or float2[cap]
   uint64_t cap;       // capacity in branches
+  unsigned int* seg_cnt;
+  uint32_t seg_log2;
+  uint32_t n_seg;
 };
 
-// Device control block.  The branch count of the current array lives in a
-// small ring: an operation that writes a new array appends into cnt[out] and
-// clears cnt[(out + 1) & 3] for the operation after it.
+// Device control block.  The total branch count of the current array lives
+// in a small ring: an operation that writes a new array adds into cnt[out]
+// and clears cnt[(out + 1) & 3] for the operation after it.
 struct Ctl {
   unsigned long long cnt[4];
   unsigned long long peak;
@@ -78,22 +95,19 @@ constexpr unsigned int kErrCapacity = 1u;  // output array too small
 constexpr unsigned int kErrBucket = 2u;    // a hash bucket overflowed
 constexpr unsigned int kErrProbe = 4u;     // a bounded hash probe ran out
 
-struct Buckets {     // hash-partitioned staging for the merge
-  uint64_t* k0;
-  uint64_t* k1;
-  void* amp;
-  unsigned int* count;  // B counters, zero between uses
-  uint32_t B, C;        // buckets, capacity per bucket (branches)
-};
-
 struct Gate1 {            // the interference operation of one merge step
   uint32_t t;             // target key bit
-  uint32_t mode;          // 0: constant matrix U, 1: RY from a register value
+  uint32_t mode;          // 0: complex U, 1: RY from a register value, 2: real U
   uint64_t cmask[2], cval[2];  // controls
   double u[8];            // U row-major (re, im)
+  float uf[8];            // U rounded to FP32 (FP32-storage states)
+  // Product reuse: bit 0 set when U10 = +-U00 (bit 2: minus), bit 1 when
+  // U11 = +-U01 (bit 3: minus); each column then costs one product per branch.
+  uint32_t reuse;
   uint32_t ang_off, ang_w;     // mode 1: angle register field
   double scale, offset;        // mode 1: theta = scale * value + offset
-  double eps2;            // prune threshold squared (strictly-less removes)
+  double eps, eps2;       // pruning threshold and its square (|a| < eps removes)
+  float epsf;             // eps rounded to FP32
 };
 
 struct Launch {
@@ -107,19 +121,29 @@ struct Launch {
 cudaError_t launch_init(const Launch& L, Ctl* ctl, Arr a, int slot, bool amp32);
 cudaError_t launch_apply_inplace(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr a, int slot,
                                  const OpList& ops);
+// Streams `in` through the run into a segmented `out` (one segment per
+// 2^out.seg_log2 input slots), dropping pruned branches.
 cudaError_t launch_apply_compact(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in,
                                  int in_slot, Arr out, int out_slot, const OpList& ops);
+// Streams `in` through the run and scatters every branch into the hash bucket
+// of its pair class (key with the target bit cleared).  bk is segmented with
+// bk.n_seg buckets of 2^bk.seg_log2 slots, counters zero on entry.
 cudaError_t launch_partition(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
-                             const OpList& ops, const Gate1& g, Buckets bk, Arr out,
-                             int out_slot);
-cudaError_t launch_pair(const Launch& L, int kw, bool amp32, Ctl* ctl, const Gate1& g,
-                        Buckets bk, Arr out, int out_slot);
+                             const OpList& ops, const Gate1& g, Arr bk);
+// One CTA per bucket: pair, apply the 2x2, prune; bucket b's survivors become
+// segment b of `out` (segment capacity 2 x bucket capacity).  Resets the
+// bucket counters.
+cudaError_t launch_pair(const Launch& L, int kw, bool amp32, Ctl* ctl, const Gate1& g, Arr bk,
+                        Arr out, int out_slot);
 cudaError_t launch_probabilities(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr a, int slot,
                                  uint32_t off, uint32_t w, double* probs, double* norm2);
+// Copies a segmented array into a dense one given exclusive segment offsets.
+cudaError_t launch_densify(const Launch& L, int kw, bool amp32, Arr in, const uint64_t* offsets,
+                           Arr out);
 cudaError_t launch_to_f64(const Launch& L, Ctl* ctl, Arr a, int slot, double* out);
 cudaError_t launch_from_f64(const Launch& L, Ctl* ctl, Arr a, const double* in, uint64_t n);
 
-int pair_capacity(int kw, bool amp32);       // branches per bucket
+int pair_log2_capacity(int kw, bool amp32);  // log2 branches per bucket
 size_t pair_smem_bytes(int kw, bool amp32);  // dynamic shared memory of one bucket CTA
 
 }  // namespace sqs

@@ -2,21 +2,24 @@
 //
 // The state is a structure of arrays: k0[] (key bits 0..63), k1[] (bits
 // 64..127, two-word keys only) and amp[] (complex<double> or complex<float>),
-// with its branch count in device memory (Ctl::cnt).  Every kernel here is a
-// bandwidth-bound stream over those arrays; nothing is a dense contraction, so
-// no tensor cores are used.
+// dense or split into fixed-capacity segments (sqs_internal.h, Arr).  Every
+// kernel is a stream over those arrays; nothing is a dense contraction, so no
+// tensor cores are used.  FP64 instructions are kept to the minimum the
+// arithmetic needs: this GPU issues about two FP64 instructions per SM per
+// clock, so a few dozen of them per branch would cost more time than moving
+// the branch through HBM.
 //
 //  k_apply_inplace   runs of non-interference operations, fused (Sec. II.D.1)
 //  k_apply_compact   the same when the run may drop branches (pruning)
 //  k_partition       fused run + the first half of an interference operation:
-//                    scatters each controlled branch into a hash bucket keyed
-//                    by its pair class (key with the target bit cleared), so
-//                    the two members of a coherent pair (Sec. II.D.2: branches
-//                    equal on every idle qubit) meet in one bucket
+//                    scatters every branch into a hash bucket keyed by its
+//                    pair class (key with the target bit cleared), so the two
+//                    members of a coherent pair (Sec. II.D.2: branches equal on
+//                    every idle qubit) meet in one bucket
 //  k_pair            one CTA per bucket: pairs the members in a shared-memory
-//                    open-addressing table, applies the 2x2 (FP64), drops
-//                    |a| < eps, appends the survivors with warp-ballot
-//                    compaction
+//                    open-addressing table, applies the 2x2, drops |a| < eps,
+//                    appends the survivors to the CTA's own output segment with
+//                    warp-ballot compaction
 //  k_probabilities   FP64 marginal probabilities and norm
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -81,43 +84,112 @@ __device__ __forceinline__ uint64_t khash(u128 k) {
 }
 
 // ---- amplitudes ------------------------------------------------------------
-__device__ __forceinline__ double2 ld_amp(const double2* p, uint64_t i) { return p[i]; }
-__device__ __forceinline__ double2 ld_amp(const float2* p, uint64_t i) {
-  const float2 f = p[i];
-  return make_double2((double)f.x, (double)f.y);
-}
-__device__ __forceinline__ void st_amp(double2* p, uint64_t i, double2 v) { p[i] = v; }
-__device__ __forceinline__ void st_amp(float2* p, uint64_t i, double2 v) {
-  p[i] = make_float2((float)v.x, (float)v.y);
-}
-
-// (a.x + i a.y)(b.x + i b.y), each product rounded, then one rounded sum.
+// Arithmetic runs in the storage type: FP64 states in FP64, FP32 states in
+// FP32 (the FP32 pipe is 64x wider than the FP64 pipe here).  Two-term sums
+// of FP32 products are single FP32 roundings of the exact sum, which is the
+// value an FP64 accumulation rounded to the FP32 store would give.
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  // Each product rounded, then one rounded sum: the operations of a
+  // complex<double> product on the host, up to commutation.
   return make_double2(__dsub_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)),
                       __dadd_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(__fsub_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)),
+                     __fadd_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+}
+// Real coefficient: (u + 0i)(a.x + i a.y) evaluated as above is exactly these
+// two products.
+__device__ __forceinline__ double2 rmul(double u, double2 a) {
+  return make_double2(__dmul_rn(u, a.x), __dmul_rn(u, a.y));
+}
+__device__ __forceinline__ float2 rmul(float u, float2 a) {
+  return make_float2(__fmul_rn(u, a.x), __fmul_rn(u, a.y));
 }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
   return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
 }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
+}
+// Exact negation by the sign bits (no arithmetic instruction).
+__device__ __forceinline__ double2 cneg(double2 a) {
+  return make_double2(__longlong_as_double(__double_as_longlong(a.x) ^ (long long)0x8000000000000000ull),
+                      __longlong_as_double(__double_as_longlong(a.y) ^ (long long)0x8000000000000000ull));
+}
+__device__ __forceinline__ float2 cneg(float2 a) {
+  return make_float2(__int_as_float(__float_as_int(a.x) ^ (int)0x80000000u),
+                     __int_as_float(__float_as_int(a.y) ^ (int)0x80000000u));
+}
 __device__ __forceinline__ double norm2(double2 a) {
   return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
 }
+__device__ __forceinline__ double norm2(float2 a) {
+  const double x = (double)a.x, y = (double)a.y;
+  return __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
+}
+// |a| >= eps?  Certain, without floating-point arithmetic, when one component
+// already reaches eps in magnitude (IEEE order of non-negative values is
+// integer order); otherwise |a|^2 is compared with eps^2 in FP64.
+__device__ __forceinline__ bool keep_amp(double2 a, double eps, float, double eps2) {
+  const unsigned long long e = (unsigned long long)__double_as_longlong(eps);
+  const unsigned long long ax =
+      (unsigned long long)__double_as_longlong(a.x) & 0x7fffffffffffffffull;
+  const unsigned long long ay =
+      (unsigned long long)__double_as_longlong(a.y) & 0x7fffffffffffffffull;
+  if (ax >= e || ay >= e) return true;
+  return !(norm2(a) < eps2);
+}
+__device__ __forceinline__ bool keep_amp(float2 a, double, float epsf, double eps2) {
+  const unsigned int e = (unsigned int)__float_as_int(epsf);
+  const unsigned int ax = (unsigned int)__float_as_int(a.x) & 0x7fffffffu;
+  const unsigned int ay = (unsigned int)__float_as_int(a.y) & 0x7fffffffu;
+  if (ax >= e || ay >= e) return true;
+  return !(norm2(a) < eps2);
+}
+__device__ __forceinline__ void to_amp(double2& out, double2 v) { out = v; }
+__device__ __forceinline__ void to_amp(float2& out, double2 v) {
+  out = make_float2((float)v.x, (float)v.y);
+}
+__device__ __forceinline__ double2 to_f64(double2 v) { return v; }
+__device__ __forceinline__ double2 to_f64(float2 v) { return make_double2(v.x, v.y); }
 
 // ---- keys --------------------------------------------------------------------
 template <int KW>
-__device__ __forceinline__ typename KT<KW>::T ld_key(const Arr& a, uint64_t i);
-template <>
-__device__ __forceinline__ uint64_t ld_key<1>(const Arr& a, uint64_t i) {
-  return a.k0[i];
-}
-template <>
-__device__ __forceinline__ u128 ld_key<2>(const Arr& a, uint64_t i) {
-  return mk<2>(a.k0[i], a.k1[i]);
+__device__ __forceinline__ typename KT<KW>::T ld_key(const Arr& a, uint64_t i) {
+  return mk<KW>(a.k0[i], KW == 2 ? a.k1[i] : 0ull);
 }
 template <int KW>
 __device__ __forceinline__ void st_key(const Arr& a, uint64_t i, typename KT<KW>::T k) {
   a.k0[i] = lo64(k);
   if (KW == 2) a.k1[i] = hi64(k);
+}
+
+// ---- layout ----------------------------------------------------------------------
+// Number of slots to visit and whether slot i holds a branch.
+__device__ __forceinline__ uint64_t slots_of(const Arr& a, const Ctl* ctl, int slot) {
+  return a.seg_cnt ? ((uint64_t)a.n_seg << a.seg_log2) : ctl->cnt[slot];
+}
+__device__ __forceinline__ bool slot_live(const Arr& a, uint64_t i) {
+  if (!a.seg_cnt) return true;
+  return (uint32_t)(i & ((1ull << a.seg_log2) - 1ull)) < a.seg_cnt[i >> a.seg_log2];
+}
+
+// Calls f(i) for every live slot: grid-stride over a dense array, or CTA per
+// segment (live branches are a prefix of each segment).
+template <class F>
+__device__ __forceinline__ void for_each_live(const Arr& a, uint64_t n_dense, F f) {
+  if (!a.seg_cnt) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_dense; i += stride)
+      f(i);
+  } else {
+    for (uint32_t sg = blockIdx.x; sg < a.n_seg; sg += gridDim.x) {
+      const uint32_t n = a.seg_cnt[sg];
+      const uint64_t base = (uint64_t)sg << a.seg_log2;
+      for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) f(base + j);
+    }
+  }
 }
 
 // ---- errors --------------------------------------------------------------------
@@ -128,93 +200,65 @@ __device__ __forceinline__ void raise_err(Ctl* ctl, unsigned int bit, uint32_t s
 }
 
 // ---- fused operation run ---------------------------------------------------------
-template <int KW>
-__device__ __forceinline__ bool apply_ops(const OpList& L, typename KT<KW>::T& k, double2& a) {
+// tab: the folded factors in the storage type (shared-memory copy).
+template <int KW, class AT>
+__device__ __forceinline__ bool apply_ops(const OpList& L, const AT* tab, typename KT<KW>::T& k,
+                                          AT& a) {
   typedef typename KT<KW>::T K;
+  uint32_t idx = 0;
 #pragma unroll 1
   for (uint32_t o = 0; o < L.n; ++o) {
     const DevOp& op = L.op[o];
+    const uint32_t kind = op.kind;
     const bool on = (k & mk<KW>(op.pmask[0], op.pmask[1])) == mk<KW>(op.pval[0], op.pval[1]);
-    switch (op.kind) {
-      case OP_XOR:
-        if (on) k ^= mk<KW>(op.xmask[0], op.xmask[1]);
-        break;
-      case OP_ADD_REG:
-        if (on)
-          k = set_field<K>(k, op.dst_off, op.dst_w,
-                           get_field(k, op.dst_off, op.dst_w) + get_field(k, op.src_off, op.src_w));
-        break;
-      case OP_SUB_REG:
-        if (on)
-          k = set_field<K>(k, op.dst_off, op.dst_w,
-                           get_field(k, op.dst_off, op.dst_w) - get_field(k, op.src_off, op.src_w));
-        break;
-      case OP_ADD_CONST:
-        if (on)
-          k = set_field<K>(k, op.dst_off, op.dst_w, get_field(k, op.dst_off, op.dst_w) + op.constant);
-        break;
-      case OP_SWAP:
-        if (on) {
-          const uint64_t v1 = get_field(k, op.dst_off, op.dst_w);
-          const uint64_t v2 = get_field(k, op.src_off, op.src_w);
-          k = set_field<K>(set_field<K>(k, op.dst_off, op.dst_w, v2), op.src_off, op.src_w, v1);
-        }
-        break;
-      case OP_QRAM:
-        if (on) {
-          const uint64_t addr = get_field(k, op.src_off, op.src_w);
-          uint64_t d = 0;
-          if (addr < op.n_entries) {
-            switch (op.entry_bytes) {
-              case 1: d = __ldg((const uint8_t*)op.table + addr); break;
-              case 2: d = __ldg((const uint16_t*)op.table + addr); break;
-              case 4: d = __ldg((const uint32_t*)op.table + addr); break;
-              default: d = __ldg((const unsigned long long*)op.table + addr); break;
-            }
+    if (kind == OP_XOR) {
+      if (on) k ^= mk<KW>(op.xmask[0], op.xmask[1]);
+    } else if (kind == OP_MUL || kind == OP_MUL_XOR) {
+      if (on) {
+        const uint32_t one = op.sel_bit < 128 ? (uint32_t)((k >> op.sel_bit) & (K)1) : 0u;
+        idx |= (1u + one) << op.shift;
+        if (kind == OP_MUL_XOR) k ^= mk<KW>(op.xmask[0], op.xmask[1]);
+      }
+    } else if (kind == OP_ADD_REG || kind == OP_SUB_REG || kind == OP_ADD_CONST) {
+      if (on) {
+        const uint64_t d = get_field(k, op.dst_off, op.dst_w);
+        const uint64_t s = kind == OP_ADD_CONST ? op.constant : get_field(k, op.src_off, op.src_w);
+        k = set_field<K>(k, op.dst_off, op.dst_w, kind == OP_SUB_REG ? d - s : d + s);
+      }
+    } else if (kind == OP_TABLE) {
+      if (idx) a = cmul(a, tab[op.tab_off + idx]);
+      idx = 0;
+    } else if (kind == OP_QRAM) {
+      if (on) {
+        const uint64_t addr = get_field(k, op.src_off, op.src_w);
+        uint64_t d = 0;
+        if (addr < op.n_entries) {
+          switch ((uint32_t)op.constant) {
+            case 1: d = __ldg((const uint8_t*)op.table + addr); break;
+            case 2: d = __ldg((const uint16_t*)op.table + addr); break;
+            case 4: d = __ldg((const uint32_t*)op.table + addr); break;
+            default: d = __ldg((const unsigned long long*)op.table + addr); break;
           }
-          k = set_field<K>(k, op.dst_off, op.dst_w, get_field(k, op.dst_off, op.dst_w) ^ d);
         }
-        break;
-      case OP_MUL:
-      case OP_MUL_XOR:
-        if (on) {
-          const bool one = op.sel_bit < 128 && ((k >> op.sel_bit) & (K)1) != (K)0;
-          const double2 c = one ? make_double2(op.c[2], op.c[3]) : make_double2(op.c[0], op.c[1]);
-          a = cmul(a, c);
-          if (op.kind == OP_MUL_XOR) k ^= mk<KW>(op.xmask[0], op.xmask[1]);
-        }
-        break;
-      case OP_PRUNE:
-        if (norm2(a) < op.eps2) return false;
-        break;
-      default:
-        break;
+        k = set_field<K>(k, op.dst_off, op.dst_w, get_field(k, op.dst_off, op.dst_w) ^ d);
+      }
+    } else if (kind == OP_SWAP) {
+      if (on) {
+        const uint64_t v1 = get_field(k, op.dst_off, op.dst_w);
+        const uint64_t v2 = get_field(k, op.src_off, op.src_w);
+        k = set_field<K>(set_field<K>(k, op.dst_off, op.dst_w, v2), op.src_off, op.src_w, v1);
+      }
+    } else if (kind == OP_PRUNE) {
+      if (!keep_amp(a, op.eps, (float)op.eps, op.eps2)) return false;
     }
   }
   return true;
 }
 
-// Warp-aggregated append of up to one branch per lane into `out`; returns the
-// base reserved for the warp's survivors.  Lanes with keep == false write
-// nothing.  Every lane of the warp must call it.
-template <int KW, class AT>
-__device__ __forceinline__ void warp_append(Ctl* ctl, uint32_t seq, Arr out, int out_slot,
-                                            bool keep, typename KT<KW>::T k, double2 a) {
-  const unsigned int lane = threadIdx.x & 31u;
-  const unsigned int ball = __ballot_sync(0xffffffffu, keep);
-  if (ball == 0u) return;
-  unsigned long long base = 0;
-  if (lane == 0) base = atomicAdd(&ctl->cnt[out_slot], (unsigned long long)__popc(ball));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (keep) {
-    const unsigned long long pos = base + __popc(ball & ((1u << lane) - 1u));
-    if (pos < out.cap) {
-      st_key<KW>(out, pos, k);
-      st_amp((AT*)out.amp, pos, a);
-    } else {
-      raise_err(ctl, kErrCapacity, seq, pos + 1);
-    }
-  }
+template <class AT>
+__device__ __forceinline__ void load_tab(const OpList& L, AT* tab) {
+  for (uint32_t i = threadIdx.x; i < L.n_tab; i += blockDim.x) to_amp(tab[i], L.tab[i]);
+  __syncthreads();
 }
 
 template <class AT>
@@ -222,7 +266,7 @@ __global__ void k_init(Ctl* ctl, Arr a, int slot) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     a.k0[0] = 0;
     if (a.k1) a.k1[0] = 0;
-    st_amp((AT*)a.amp, 0, make_double2(1.0, 0.0));
+    to_amp(((AT*)a.amp)[0], make_double2(1.0, 0.0));
     for (int s = 0; s < 4; ++s) ctl->cnt[s] = 0;
     ctl->cnt[slot] = 1;
     ctl->peak = 1;
@@ -234,104 +278,188 @@ __global__ void k_init(Ctl* ctl, Arr a, int slot) {
 }
 
 // ---------------------------------------------------------------------------
+constexpr int kStreamThreads = 256;
+
 template <int KW, class AT, bool TK, bool TA>
-__global__ void __launch_bounds__(256) k_apply_inplace(Ctl* ctl, Arr a, int slot,
-                                                       const __grid_constant__ OpList ops,
-                                                       uint32_t seq) {
+__global__ void __launch_bounds__(kStreamThreads)
+    k_apply_inplace(Ctl* ctl, Arr a, int slot, const __grid_constant__ OpList ops, uint32_t seq) {
+  __shared__ AT tab[kTabEntries];
   if (ctl->err) return;
-  const unsigned long long n = ctl->cnt[slot];
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, n);
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  load_tab(ops, tab);
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, ctl->cnt[slot]);
+  for_each_live(a, ctl->cnt[slot], [&](uint64_t i) {
     typename KT<KW>::T k = ld_key<KW>(a, i);
-    double2 v = TA ? ld_amp((const AT*)a.amp, i) : make_double2(0.0, 0.0);
-    apply_ops<KW>(ops, k, v);
+    AT v;
+    if (TA) v = ((const AT*)a.amp)[i];
+    apply_ops<KW, AT>(ops, tab, k, v);
     if (TK) st_key<KW>(a, i, k);
-    if (TA) st_amp((AT*)a.amp, i, v);
-  }
+    if (TA) ((AT*)a.amp)[i] = v;
+  });
 }
 
+// Input segment (or dense chunk) c of 2^out.seg_log2 slots is compacted into
+// output segment c.
 template <int KW, class AT>
-__global__ void __launch_bounds__(256) k_apply_compact(Ctl* ctl, Arr in, int in_slot, Arr out,
-                                                       int out_slot,
-                                                       const __grid_constant__ OpList ops,
-                                                       uint32_t seq) {
+__global__ void __launch_bounds__(kStreamThreads)
+    k_apply_compact(Ctl* ctl, Arr in, int in_slot, Arr out, int out_slot,
+                    const __grid_constant__ OpList ops, uint32_t seq) {
+  __shared__ AT tab[kTabEntries];
+  __shared__ unsigned int seg_fill;
   if (ctl->err) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[(out_slot + 1) & 3] = 0;
-  const unsigned long long n = ctl->cnt[in_slot];
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, n);
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  // The loop bound is rounded up to whole warps so every lane joins the ballot.
-  const uint64_t n_pad = (n + 31ull) & ~31ull;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += stride) {
-    bool keep = false;
-    typename KT<KW>::T k = 0;
-    double2 v = make_double2(0.0, 0.0);
-    if (i < n) {
-      k = ld_key<KW>(in, i);
-      v = ld_amp((const AT*)in.amp, i);
-      keep = apply_ops<KW>(ops, k, v);
-    }
-    warp_append<KW, AT>(ctl, seq, out, out_slot, keep, k, v);
+  load_tab(ops, tab);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->cnt[(out_slot + 1) & 3] = 0;
+    atomicMax(&ctl->peak, ctl->cnt[in_slot]);
   }
-}
-
-// ---------------------------------------------------------------------------
-template <int KW, class AT>
-__global__ void __launch_bounds__(256) k_partition(Ctl* ctl, Arr in, int in_slot,
-                                                   const __grid_constant__ OpList ops, Gate1 g,
-                                                   Buckets bk, Arr out, int out_slot,
-                                                   uint32_t seq) {
-  typedef typename KT<KW>::T K;
-  if (ctl->err) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[(out_slot + 1) & 3] = 0;
-  const unsigned long long n = ctl->cnt[in_slot];
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, n);
-  const K cmask = mk<KW>(g.cmask[0], g.cmask[1]);
-  const K cval = mk<KW>(g.cval[0], g.cval[1]);
-  const K bmask = ((K)1) << g.t;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t n_pad = (n + 31ull) & ~31ull;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += stride) {
-    bool alive = false;
-    K k = 0;
-    double2 v = make_double2(0.0, 0.0);
-    if (i < n) {
-      k = ld_key<KW>(in, i);
-      v = ld_amp((const AT*)in.amp, i);
-      alive = apply_ops<KW>(ops, k, v);
-    }
-    const bool ctrl = alive && ((k & cmask) == cval);
-    if (ctrl) {
-      const uint64_t h = khash(k & ~bmask);
-      const uint32_t b = (uint32_t)(((h >> 32) * (uint64_t)bk.B) >> 32);
-      const unsigned int pos = atomicAdd(&bk.count[b], 1u);
-      if (pos < bk.C) {
-        const uint64_t j = (uint64_t)b * bk.C + pos;
-        bk.k0[j] = lo64(k);
-        if (KW == 2) bk.k1[j] = hi64(k);
-        st_amp((AT*)bk.amp, j, v);
-      } else {
-        raise_err(ctl, kErrBucket, seq, (unsigned long long)pos + 1);
+  const uint64_t n_dense = ctl->cnt[in_slot];
+  const uint64_t chunk = 1ull << out.seg_log2;
+  const unsigned int lane = threadIdx.x & 31u;
+  // Every output segment gets its count written, including those past the
+  // device-side count (the host sized them from an upper bound).
+  for (uint64_t c = blockIdx.x; c < out.n_seg; c += gridDim.x) {
+    if (threadIdx.x == 0) seg_fill = 0;
+    __syncthreads();
+    const uint64_t base = c << out.seg_log2;
+    uint64_t cnt;
+    if (in.seg_cnt)
+      cnt = c < in.n_seg ? in.seg_cnt[c] : 0;
+    else
+      cnt = base >= n_dense ? 0 : (n_dense - base < chunk ? n_dense - base : chunk);
+    for (uint64_t r = 0; r < cnt; r += blockDim.x) {
+      const uint64_t i = base + r + threadIdx.x;
+      bool keep = false;
+      typename KT<KW>::T k = 0;
+      AT v;
+      if (r + threadIdx.x < cnt) {
+        k = ld_key<KW>(in, i);
+        v = ((const AT*)in.amp)[i];
+        keep = apply_ops<KW, AT>(ops, tab, k, v);
+      }
+      const unsigned int ball = __ballot_sync(0xffffffffu, keep);
+      unsigned int wbase = 0;
+      if (lane == 0 && ball) wbase = atomicAdd(&seg_fill, (unsigned int)__popc(ball));
+      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      if (keep) {
+        const uint64_t pos = base + wbase + __popc(ball & ((1u << lane) - 1u));
+        st_key<KW>(out, pos, k);
+        ((AT*)out.amp)[pos] = v;
       }
     }
-    // Branches the controls leave alone go straight to the output.
-    warp_append<KW, AT>(ctl, seq, out, out_slot, alive && !ctrl, k, v);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      out.seg_cnt[c] = seg_fill;
+      if (seg_fill) atomicAdd(&ctl->cnt[out_slot], (unsigned long long)seg_fill);
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
+template <int KW, class AT>
+__global__ void __launch_bounds__(kStreamThreads)
+    k_partition(Ctl* ctl, Arr in, int in_slot, const __grid_constant__ OpList ops, Gate1 g,
+                Arr bk, uint32_t seq) {
+  typedef typename KT<KW>::T K;
+  __shared__ AT tab[kTabEntries];
+  if (ctl->err) return;
+  load_tab(ops, tab);
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, ctl->cnt[in_slot]);
+  const K bmask = ((K)1) << g.t;
+  const uint32_t C = 1u << bk.seg_log2;
+  for_each_live(in, ctl->cnt[in_slot], [&](uint64_t i) {
+    K k = ld_key<KW>(in, i);
+    AT v = ((const AT*)in.amp)[i];
+    if (!apply_ops<KW, AT>(ops, tab, k, v)) return;
+    const uint64_t h = khash(k & ~bmask);
+    const uint32_t b = (uint32_t)(((h >> 32) * (uint64_t)bk.n_seg) >> 32);
+    const unsigned int pos = atomicAdd(&bk.seg_cnt[b], 1u);
+    if (pos < C) {
+      const uint64_t j = ((uint64_t)b << bk.seg_log2) + pos;
+      st_key<KW>(bk, j, k);
+      ((AT*)bk.amp)[j] = v;
+    } else {
+      raise_err(ctl, kErrBucket, seq, (unsigned long long)pos + 1);
+    }
+  });
+}
+
+// ---------------------------------------------------------------------------
+// The 2x2 of one merge step on a pair class: children (o0, o1) of the
+// members a0 (bit 0, present when has0) and a1 (bit 1, present when has1).
+// Coefficients in the storage type; products shared between the rows of a
+// column when the host flagged U10 = +-U00 or U11 = +-U01.
+template <class AT>
+struct Coef;
+template <>
+struct Coef<double2> {
+  typedef double S;
+  __device__ static double2 c(const Gate1& g, int e) { return make_double2(g.u[2 * e], g.u[2 * e + 1]); }
+  __device__ static double r(const Gate1& g, int e) { return g.u[2 * e]; }
+};
+template <>
+struct Coef<float2> {
+  typedef float S;
+  __device__ static float2 c(const Gate1& g, int e) { return make_float2(g.uf[2 * e], g.uf[2 * e + 1]); }
+  __device__ static float r(const Gate1& g, int e) { return g.uf[2 * e]; }
+};
+
+template <class AT>
+__device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, bool has0, AT a0,
+                                         bool has1, AT a1, AT& o0, AT& o1) {
+  typedef typename Coef<AT>::S S;
+  AT p00, p10, p01, p11;  // row r, column s: U[r][s] * a_s
+  if (g.mode == 2 || g.mode == 1) {
+    S u00, u01, u10, u11;
+    if (g.mode == 1) {
+      const double theta = g.scale * (double)angle_value + g.offset;
+      double sn, cs;
+      sincos(theta * 0.5, &sn, &cs);
+      u00 = (S)cs, u01 = (S)-sn, u10 = (S)sn, u11 = (S)cs;
+    } else {
+      u00 = Coef<AT>::r(g, 0), u01 = Coef<AT>::r(g, 1), u10 = Coef<AT>::r(g, 2),
+      u11 = Coef<AT>::r(g, 3);
+    }
+    if (has0) {
+      p00 = rmul(u00, a0);
+      p10 = (g.reuse & 1u) ? ((g.reuse & 4u) ? cneg(p00) : p00) : rmul(u10, a0);
+    }
+    if (has1) {
+      p01 = rmul(u01, a1);
+      p11 = (g.reuse & 2u) ? ((g.reuse & 8u) ? cneg(p01) : p01) : rmul(u11, a1);
+    }
+  } else {
+    if (has0) {
+      p00 = cmul(Coef<AT>::c(g, 0), a0);
+      p10 = (g.reuse & 1u) ? ((g.reuse & 4u) ? cneg(p00) : p00) : cmul(Coef<AT>::c(g, 2), a0);
+    }
+    if (has1) {
+      p01 = cmul(Coef<AT>::c(g, 1), a1);
+      p11 = (g.reuse & 2u) ? ((g.reuse & 8u) ? cneg(p01) : p01) : cmul(Coef<AT>::c(g, 3), a1);
+    }
+  }
+  if (has0 && has1) {
+    o0 = cadd(p00, p01);
+    o1 = cadd(p10, p11);
+  } else if (has0) {
+    o0 = p00;
+    o1 = p10;
+  } else {
+    o0 = p01;
+    o1 = p11;
+  }
+}
+
 // One CTA per bucket.  Shared memory: keys[C], amps[C] (storage type),
-// slots[S] (S = 2C, 0 = empty, else index + 1), partner[C].
+// slots[2C] (0 = empty, else index + 1), partner[C].
 constexpr int kPairThreads = 256;
 
 template <int KW, class AT>
-__global__ void __launch_bounds__(kPairThreads) k_pair(Ctl* ctl, Gate1 g, Buckets bk, Arr out,
-                                                       int out_slot, uint32_t seq) {
+__global__ void __launch_bounds__(kPairThreads)
+    k_pair(Ctl* ctl, Gate1 g, Arr bk, Arr out, int out_slot, uint32_t seq) {
   typedef typename KT<KW>::T K;
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned int fill;
   if (ctl->err) return;
-  const uint32_t C = bk.C;
+  const uint32_t C = 1u << bk.seg_log2;
   const uint32_t S = 2u * C;
   K* skey = (K*)smem;
   AT* samp = (AT*)(smem + (size_t)C * sizeof(K));
@@ -339,21 +467,28 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(Ctl* ctl, Gate1 g, Bucket
   int* partner = (int*)(slot + S);
 
   const uint32_t b = blockIdx.x;
-  const uint32_t n = bk.count[b];
+  if (b == 0 && threadIdx.x == 0) ctl->cnt[(out_slot + 1) & 3] = 0;
+  const uint32_t n = bk.seg_cnt[b];
   if (n > C) return;  // overflow already flagged by the partition
-  const uint64_t base = (uint64_t)b * C;
+  const uint64_t base = (uint64_t)b << bk.seg_log2;
+#pragma unroll 4
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    skey[i] = mk<KW>(bk.k0[base + i], KW == 2 ? bk.k1[base + i] : 0ull);
+    skey[i] = ld_key<KW>(bk, base + i);
     samp[i] = ((const AT*)bk.amp)[base + i];
     partner[i] = -1;
   }
   for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) slot[i] = 0u;
+  if (threadIdx.x == 0) fill = 0;
   __syncthreads();
-  if (threadIdx.x == 0) bk.count[b] = 0u;  // bucket is clean for the next use
+  if (threadIdx.x == 0) bk.seg_cnt[b] = 0u;  // bucket is clean for the next use
 
   const K bmask = ((K)1) << g.t;
+  const K cmask = mk<KW>(g.cmask[0], g.cmask[1]);
+  const K cval = mk<KW>(g.cval[0], g.cval[1]);
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const K p = skey[i] & ~bmask;
+    const K k = skey[i];
+    if ((k & cmask) != cval) continue;  // passes through unchanged
+    const K p = k & ~bmask;
     uint32_t h = (uint32_t)khash(p) & (S - 1u);
     // At most C entries live in 2C slots, so a free slot or the partner is
     // always found within S probes; the bound only guards against misuse.
@@ -373,99 +508,59 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(Ctl* ctl, Gate1 g, Bucket
   }
   __syncthreads();
 
-  // Emission in two sweeps over the same rounds: the first counts the
-  // surviving children of every (round, warp), a scan turns the counts into
-  // offsets and one atomic per CTA reserves the output run; the second sweep
-  // recomputes the children and writes them, each warp to a contiguous range.
-  const uint32_t rounds = (n + blockDim.x - 1u) / blockDim.x;
-  const uint32_t nwarps = blockDim.x >> 5;
-  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint64_t obase = (uint64_t)b << out.seg_log2;
+  const uint32_t lane = threadIdx.x & 31u;
   const unsigned int lt = (1u << lane) - 1u;
-  unsigned long long* woff = (unsigned long long*)(partner + C);  // rounds * nwarps + 1
-  for (int sweep = 0; sweep < 2; ++sweep) {
-    for (uint32_t r = 0; r < rounds; ++r) {
-      const uint32_t i = r * blockDim.x + threadIdx.x;
-      bool keep0 = false, keep1 = false;
-      K p = 0;
-      double2 o0 = make_double2(0.0, 0.0), o1 = make_double2(0.0, 0.0);
-      if (i < n) {
-        const K k = skey[i];
+  const uint32_t rounds = (n + blockDim.x - 1u) / blockDim.x;
+  for (uint32_t r = 0; r < rounds; ++r) {
+    const uint32_t i = r * blockDim.x + threadIdx.x;
+    bool keep0 = false, keep1 = false;
+    K k0 = 0, k1 = 0;
+    AT o0, o1;
+    if (i < n) {
+      const K k = skey[i];
+      const AT ai = samp[i];
+      if ((k & cmask) != cval) {
+        keep0 = true;  // controls not met: the branch is unchanged
+        k0 = k;
+        o0 = ai;
+      } else {
         const bool kt = (k & bmask) != (K)0;
         const int j = partner[i];
         if (!(kt && j >= 0)) {  // the bit-1 member of a pair is emitted by its partner
-          p = k & ~bmask;
-          double2 U00, U01, U10, U11;
-          if (g.mode == 1) {
-            const double theta = g.scale * (double)get_field(p, g.ang_off, g.ang_w) + g.offset;
-            double sn, cs;
-            sincos(theta * 0.5, &sn, &cs);
-            U00 = make_double2(cs, 0.0);
-            U01 = make_double2(-sn, 0.0);
-            U10 = make_double2(sn, 0.0);
-            U11 = make_double2(cs, 0.0);
-          } else {
-            U00 = make_double2(g.u[0], g.u[1]);
-            U01 = make_double2(g.u[2], g.u[3]);
-            U10 = make_double2(g.u[4], g.u[5]);
-            U11 = make_double2(g.u[6], g.u[7]);
-          }
-          const double2 ai = ld_amp(samp, i);
-          if (!kt) {
-            o0 = cmul(U00, ai);
-            o1 = cmul(U10, ai);
-            if (j >= 0) {
-              const double2 aj = ld_amp(samp, (uint64_t)j);
-              o0 = cadd(o0, cmul(U01, aj));
-              o1 = cadd(o1, cmul(U11, aj));
-            }
-          } else {
-            o0 = cmul(U01, ai);
-            o1 = cmul(U11, ai);
-          }
-          keep0 = !(norm2(o0) < g.eps2);
-          keep1 = !(norm2(o1) < g.eps2);
-        }
-      }
-      const unsigned int b0 = __ballot_sync(0xffffffffu, keep0);
-      const unsigned int b1 = __ballot_sync(0xffffffffu, keep1);
-      if (sweep == 0) {
-        if (lane == 0) woff[r * nwarps + warp] = (unsigned long long)(__popc(b0) + __popc(b1));
-        continue;
-      }
-      const unsigned long long wbase = woff[r * nwarps + warp];
-      if (keep0) {
-        const unsigned long long pos = wbase + __popc(b0 & lt);
-        if (pos < out.cap) {
-          st_key<KW>(out, pos, p);
-          st_amp((AT*)out.amp, pos, o0);
-        } else {
-          raise_err(ctl, kErrCapacity, seq, pos + 1);
-        }
-      }
-      if (keep1) {
-        const unsigned long long pos = wbase + __popc(b0) + __popc(b1 & lt);
-        if (pos < out.cap) {
-          st_key<KW>(out, pos, p | bmask);
-          st_amp((AT*)out.amp, pos, o1);
-        } else {
-          raise_err(ctl, kErrCapacity, seq, pos + 1);
+          k0 = k & ~bmask;
+          k1 = k | bmask;
+          const uint64_t av = g.mode == 1 ? get_field(k0, g.ang_off, g.ang_w) : 0ull;
+          if (!kt)
+            children<AT>(g, av, true, ai, j >= 0, j >= 0 ? samp[j] : ai, o0, o1);
+          else
+            children<AT>(g, av, false, ai, true, ai, o0, o1);
+          keep0 = keep_amp(o0, g.eps, g.epsf, g.eps2);
+          keep1 = keep_amp(o1, g.eps, g.epsf, g.eps2);
         }
       }
     }
-    if (sweep == 0) {
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        unsigned long long run = 0;
-        for (uint32_t q = 0; q < rounds * nwarps; ++q) {
-          const unsigned long long c = woff[q];
-          woff[q] = run;
-          run += c;
-        }
-        const unsigned long long base = run ? atomicAdd(&ctl->cnt[out_slot], run) : 0ull;
-        for (uint32_t q = 0; q < rounds * nwarps; ++q) woff[q] += base;
-      }
-      __syncthreads();
+    const unsigned int b0 = __ballot_sync(0xffffffffu, keep0);
+    const unsigned int b1 = __ballot_sync(0xffffffffu, keep1);
+    const unsigned int tot = __popc(b0) + __popc(b1);
+    unsigned int wbase = 0;
+    if (lane == 0 && tot) wbase = atomicAdd(&fill, tot);
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    if (keep0) {
+      const uint64_t pos = obase + wbase + __popc(b0 & lt);
+      st_key<KW>(out, pos, k0);
+      ((AT*)out.amp)[pos] = o0;
     }
+    if (keep1) {
+      const uint64_t pos = obase + wbase + __popc(b0) + __popc(b1 & lt);
+      st_key<KW>(out, pos, k1);
+      ((AT*)out.amp)[pos] = o1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    out.seg_cnt[b] = fill;
+    if (fill) atomicAdd(&ctl->cnt[out_slot], (unsigned long long)fill);
   }
 }
 
@@ -474,9 +569,9 @@ constexpr int kProbThreads = 256;
 constexpr uint32_t kSmemBinsLog2 = 11;
 
 template <int KW, class AT>
-__global__ void __launch_bounds__(kProbThreads) k_probabilities(Ctl* ctl, Arr a, int slot,
-                                                                uint32_t off, uint32_t w,
-                                                                double* probs, double* nrm) {
+__global__ void __launch_bounds__(kProbThreads)
+    k_probabilities(Ctl* ctl, Arr a, int slot, uint32_t off, uint32_t w, double* probs,
+                    double* nrm) {
   __shared__ double bins[1u << kSmemBinsLog2];
   __shared__ double red[kProbThreads / 32];
   if (ctl->err) return;
@@ -484,13 +579,10 @@ __global__ void __launch_bounds__(kProbThreads) k_probabilities(Ctl* ctl, Arr a,
   if (smem_bins)
     for (uint32_t v = threadIdx.x; v < (1u << w); v += blockDim.x) bins[v] = 0.0;
   __syncthreads();
-  const unsigned long long n = ctl->cnt[slot];
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, n);
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, ctl->cnt[slot]);
   double acc = 0.0;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const double2 v = ld_amp((const AT*)a.amp, i);
-    const double p = norm2(v);
+  for_each_live(a, ctl->cnt[slot], [&](uint64_t i) {
+    const double p = norm2(((const AT*)a.amp)[i]);
     acc += p;
     if (probs) {
       const uint64_t val = get_field(ld_key<KW>(a, i), off, w);
@@ -499,7 +591,7 @@ __global__ void __launch_bounds__(kProbThreads) k_probabilities(Ctl* ctl, Arr a,
       else
         atomicAdd(&probs[val], p);
     }
-  }
+  });
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31u) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -508,9 +600,24 @@ __global__ void __launch_bounds__(kProbThreads) k_probabilities(Ctl* ctl, Arr a,
     for (int q = 0; q < kProbThreads / 32; ++q) t += red[q];
     if (nrm) atomicAdd(nrm, t);
   }
-  if (smem_bins)
+  if (smem_bins) {
+    __syncthreads();
     for (uint32_t v = threadIdx.x; v < (1u << w); v += blockDim.x)
       if (bins[v] != 0.0) atomicAdd(&probs[v], bins[v]);
+  }
+}
+
+// One CTA per segment: copy it to its dense offset.
+template <int KW, class AT>
+__global__ void k_densify(Arr in, const uint64_t* offsets, Arr out) {
+  const uint32_t s = blockIdx.x;
+  const uint32_t n = in.seg_cnt[s];
+  const uint64_t src = (uint64_t)s << in.seg_log2;
+  const uint64_t dst = offsets[s];
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    st_key<KW>(out, dst + i, ld_key<KW>(in, src + i));
+    ((AT*)out.amp)[dst + i] = ((const AT*)in.amp)[src + i];
+  }
 }
 
 __global__ void k_to_f64(Ctl* ctl, const float2* amp, int slot, double2* out) {
@@ -546,77 +653,77 @@ cudaError_t launch_init(const Launch& L, Ctl* ctl, Arr a, int slot, bool amp32) 
   return cudaGetLastError();
 }
 
+#define SQS_DISPATCH(kw, amp32, MACRO) \
+  do {                                 \
+    if (kw == 1) {                     \
+      if (amp32) MACRO(1, float2);     \
+      else MACRO(1, double2);          \
+    } else {                           \
+      if (amp32) MACRO(2, float2);     \
+      else MACRO(2, double2);          \
+    }                                  \
+  } while (0)
+
 template <int KW, class AT>
 static void apply_inplace_t(const Launch& L, Ctl* ctl, Arr a, int slot, const OpList& ops) {
-  const int g = stream_grid(L, 256);
+  const int g = stream_grid(L, kStreamThreads);
   if (ops.touches_keys && ops.touches_amps)
-    k_apply_inplace<KW, AT, true, true><<<g, 256, 0, L.stream>>>(ctl, a, slot, ops, L.seq);
+    k_apply_inplace<KW, AT, true, true>
+        <<<g, kStreamThreads, 0, L.stream>>>(ctl, a, slot, ops, L.seq);
   else if (ops.touches_keys)
-    k_apply_inplace<KW, AT, true, false><<<g, 256, 0, L.stream>>>(ctl, a, slot, ops, L.seq);
+    k_apply_inplace<KW, AT, true, false>
+        <<<g, kStreamThreads, 0, L.stream>>>(ctl, a, slot, ops, L.seq);
   else
-    k_apply_inplace<KW, AT, false, true><<<g, 256, 0, L.stream>>>(ctl, a, slot, ops, L.seq);
+    k_apply_inplace<KW, AT, false, true>
+        <<<g, kStreamThreads, 0, L.stream>>>(ctl, a, slot, ops, L.seq);
 }
 
 cudaError_t launch_apply_inplace(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr a, int slot,
                                  const OpList& ops) {
-  if (kw == 1) {
-    if (amp32) apply_inplace_t<1, float2>(L, ctl, a, slot, ops);
-    else apply_inplace_t<1, double2>(L, ctl, a, slot, ops);
-  } else {
-    if (amp32) apply_inplace_t<2, float2>(L, ctl, a, slot, ops);
-    else apply_inplace_t<2, double2>(L, ctl, a, slot, ops);
-  }
+#define SQS_AI(KW_, AT_) apply_inplace_t<KW_, AT_>(L, ctl, a, slot, ops)
+  SQS_DISPATCH(kw, amp32, SQS_AI);
+#undef SQS_AI
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply_compact(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in,
                                  int in_slot, Arr out, int out_slot, const OpList& ops) {
-  const int g = stream_grid(L, 256);
-#define SQS_AC(KW_, AT_) \
-  k_apply_compact<KW_, AT_><<<g, 256, 0, L.stream>>>(ctl, in, in_slot, out, out_slot, ops, L.seq)
-  if (kw == 1) {
-    if (amp32) SQS_AC(1, float2);
-    else SQS_AC(1, double2);
-  } else {
-    if (amp32) SQS_AC(2, float2);
-    else SQS_AC(2, double2);
-  }
+  const uint64_t chunks = (L.n_hint + (1ull << out.seg_log2) - 1) >> out.seg_log2;
+  uint64_t g = chunks < 1 ? 1 : chunks;
+  if (g > (uint64_t)L.sm_count * 8) g = (uint64_t)L.sm_count * 8;
+#define SQS_AC(KW_, AT_)                                                              \
+  k_apply_compact<KW_, AT_>                                                           \
+      <<<(int)g, kStreamThreads, 0, L.stream>>>(ctl, in, in_slot, out, out_slot, ops, \
+                                                L.seq)
+  SQS_DISPATCH(kw, amp32, SQS_AC);
 #undef SQS_AC
   return cudaGetLastError();
 }
 
 cudaError_t launch_partition(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
-                             const OpList& ops, const Gate1& g, Buckets bk, Arr out,
-                             int out_slot) {
-  const int grid = stream_grid(L, 256);
-#define SQS_PT(KW_, AT_)                                                                    \
-  k_partition<KW_, AT_><<<grid, 256, 0, L.stream>>>(ctl, in, in_slot, ops, g, bk, out, out_slot, \
-                                                    L.seq)
-  if (kw == 1) {
-    if (amp32) SQS_PT(1, float2);
-    else SQS_PT(1, double2);
-  } else {
-    if (amp32) SQS_PT(2, float2);
-    else SQS_PT(2, double2);
-  }
+                             const OpList& ops, const Gate1& g, Arr bk) {
+  const int grid = stream_grid(L, kStreamThreads);
+#define SQS_PT(KW_, AT_)                                                                \
+  k_partition<KW_, AT_><<<grid, kStreamThreads, 0, L.stream>>>(ctl, in, in_slot, ops, g, \
+                                                               bk, L.seq)
+  SQS_DISPATCH(kw, amp32, SQS_PT);
 #undef SQS_PT
   return cudaGetLastError();
 }
 
-int pair_capacity(int kw, bool amp32) {
+int pair_log2_capacity(int kw, bool amp32) {
   (void)kw;
   (void)amp32;
-  return 2048;
+  return 11;  // 2048 branches per bucket
 }
 
 size_t pair_smem_bytes(int kw, bool amp32) {
-  const size_t C = (size_t)pair_capacity(kw, amp32);
-  const size_t woff = ((C + kPairThreads - 1) / kPairThreads) * (kPairThreads / 32) + 1;
-  return C * (kw == 1 ? 8 : 16) + C * (amp32 ? 8 : 16) + 2 * C * 4 + C * 4 + woff * 8;
+  const size_t C = (size_t)1 << pair_log2_capacity(kw, amp32);
+  return C * (kw == 1 ? 8 : 16) + C * (amp32 ? 8 : 16) + 2 * C * 4 + C * 4;
 }
 
 template <int KW, class AT>
-static cudaError_t pair_t(const Launch& L, Ctl* ctl, const Gate1& g, Buckets bk, Arr out,
+static cudaError_t pair_t(const Launch& L, Ctl* ctl, const Gate1& g, Arr bk, Arr out,
                           int out_slot) {
   const size_t smem = pair_smem_bytes(KW, sizeof(AT) == 8);
   // The opt-in to more than 48 KB of dynamic shared memory is per device.
@@ -629,14 +736,15 @@ static cudaError_t pair_t(const Launch& L, Ctl* ctl, const Gate1& g, Buckets bk,
     if (e != cudaSuccess) return e;
     configured |= 1ull << dev;
   }
-  k_pair<KW, AT><<<bk.B, kPairThreads, smem, L.stream>>>(ctl, g, bk, out, out_slot, L.seq);
+  k_pair<KW, AT><<<bk.n_seg, kPairThreads, smem, L.stream>>>(ctl, g, bk, out, out_slot, L.seq);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pair(const Launch& L, int kw, bool amp32, Ctl* ctl, const Gate1& g,
-                        Buckets bk, Arr out, int out_slot) {
-  if (kw == 1) return amp32 ? pair_t<1, float2>(L, ctl, g, bk, out, out_slot)
-                            : pair_t<1, double2>(L, ctl, g, bk, out, out_slot);
+cudaError_t launch_pair(const Launch& L, int kw, bool amp32, Ctl* ctl, const Gate1& g, Arr bk,
+                        Arr out, int out_slot) {
+  if (kw == 1)
+    return amp32 ? pair_t<1, float2>(L, ctl, g, bk, out, out_slot)
+                 : pair_t<1, double2>(L, ctl, g, bk, out, out_slot);
   return amp32 ? pair_t<2, float2>(L, ctl, g, bk, out, out_slot)
                : pair_t<2, double2>(L, ctl, g, bk, out, out_slot);
 }
@@ -646,14 +754,17 @@ cudaError_t launch_probabilities(const Launch& L, int kw, bool amp32, Ctl* ctl, 
   const int g = stream_grid(L, kProbThreads);
 #define SQS_PR(KW_, AT_) \
   k_probabilities<KW_, AT_><<<g, kProbThreads, 0, L.stream>>>(ctl, a, slot, off, w, probs, nrm)
-  if (kw == 1) {
-    if (amp32) SQS_PR(1, float2);
-    else SQS_PR(1, double2);
-  } else {
-    if (amp32) SQS_PR(2, float2);
-    else SQS_PR(2, double2);
-  }
+  SQS_DISPATCH(kw, amp32, SQS_PR);
 #undef SQS_PR
+  return cudaGetLastError();
+}
+
+cudaError_t launch_densify(const Launch& L, int kw, bool amp32, Arr in, const uint64_t* offsets,
+                           Arr out) {
+  if (in.n_seg == 0) return cudaSuccess;
+#define SQS_DN(KW_, AT_) k_densify<KW_, AT_><<<in.n_seg, 256, 0, L.stream>>>(in, offsets, out)
+  SQS_DISPATCH(kw, amp32, SQS_DN);
+#undef SQS_DN
   return cudaGetLastError();
 }
 

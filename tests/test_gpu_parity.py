@@ -304,3 +304,22 @@ def test_deterministic_as_a_set(sqs):
     a = sqs.run_circuit(circ).to_dict()
     b = sqs.run_circuit(circ).to_dict()
     assert a == b  # bitwise: each output is a sum of at most two products
+
+
+@pytest.mark.parametrize("then_branch", [False, True])
+def test_long_fused_runs(sqs, then_branch):
+    """Hundreds of queued non-interference operations: the runtime splits them
+    into launch-sized lists and folds the amplitude factors into tables."""
+    rng = np.random.default_rng(77)
+    kinds = ("x", "cx", "ccx", "phase", "cphase", "diag", "adiag", "add", "sub", "swap")
+    circ = W.random_circuit(W64, 400, 77, kinds=kinds)
+    lo, hi, amps = W.random_state(W64, 9000, seed=78)
+    gs, os_ = _pair(sqs, W64, lo, hi, amps)
+    gates = list(circ["gates"])
+    if then_branch:
+        gates.append(("h", 1, 1, ()))
+    for g in gates:
+        gs.apply(g)
+        os_.apply(g)
+    _check(gs, os_)
+    assert rng is not None
