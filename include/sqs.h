@@ -262,6 +262,50 @@ const char* sqs_last_error(const sqs_state* st);
 /* Library version string. */
 const char* sqs_version(void);
 
+/* ---- no-allocation variant --------------------------------------------------
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory: code embedded in a host framework that owns
+ * every byte of device memory through its own pre-planned arena or budget,
+ * and latency-bound callers that cannot afford the device-wide
+ * synchronisation that cudaMalloc and cudaFree may perform.  Such a caller
+ * keeps its state in its own device buffers and passes them in and out.
+ *
+ * sqs_apply_u1q_noalloc applies the single-qubit matrix m (layout as in
+ * sqs_apply_u1q) on bit `bit` of register `reg`, under the controls, to the
+ * n_in branches in keys_lo_in / keys_hi_in / amps_in and writes the merged,
+ * pruned (|a| < eps removed) result to keys_lo_out / keys_hi_out / amps_out:
+ *   keys_lo_*: key bits 0..63, one uint64 per branch (device memory);
+ *   keys_hi_*: key bits 64..127 (device memory; ignored, may be NULL, when
+ *              sum(reg_widths) <= 64);
+ *   amps_*:    (re, im) FP64 pairs, one per branch (device memory);
+ *   n_out:     device pointer receiving the output count, or all ones when a
+ *              device-side check failed.
+ * Keys must be distinct.  The output order carries no meaning.  It never
+ * allocates: its scratch space (buckets, output segments, offsets, a control
+ * block) is one static device array of sqs_noalloc_scratch_bytes() bytes
+ * (about 8.1 MiB), which every GPU that loads the library holds until the
+ * process exits.  Inputs larger than SQS_NOALLOC_MAX_BRANCHES branches, or an
+ * out_cap below 2 * n_in, are rejected with SQS_ERR_ARG before anything is
+ * enqueued; sqs_noalloc_last_error() gives the reason.  The first call on a
+ * device looks up the array's device address (set-up, once per device, with
+ * that device current); make that first call before any stream capture.  All
+ * calls share the one array and each clears what it needs at its start:
+ * calls whose work overlaps on the GPU (other streams, or the same stream
+ * from concurrent host threads) race and corrupt each other's results.
+ * Enqueued on `stream`; returns without waiting. */
+#define SQS_NOALLOC_MAX_BRANCHES 65536u
+sqs_status sqs_apply_u1q_noalloc(const uint32_t* reg_widths, uint32_t n_regs, uint32_t reg,
+                                 uint32_t bit, const double m[8], const sqs_ctrl* ctrl,
+                                 uint32_t n_ctrl, double eps, const uint64_t* keys_lo_in,
+                                 const uint64_t* keys_hi_in, const double* amps_in,
+                                 uint64_t n_in, uint64_t* keys_lo_out, uint64_t* keys_hi_out,
+                                 double* amps_out, uint64_t out_cap, uint64_t* n_out,
+                                 void* stream);
+/* Reason for the last SQS_ERR_* from sqs_apply_u1q_noalloc on this thread. */
+const char* sqs_noalloc_last_error(void);
+/* Size in bytes of the static scratch array of sqs_apply_u1q_noalloc. */
+uint64_t sqs_noalloc_scratch_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

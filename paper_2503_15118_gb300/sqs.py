@@ -92,6 +92,10 @@ SIGNATURES = {
     "sqs_trace_read": (_S, [_P, ctypes.POINTER(TraceRecord), _u32, ctypes.POINTER(_u32)]),
     "sqs_last_error": (ctypes.c_char_p, [_P]),
     "sqs_version": (ctypes.c_char_p, []),
+    "sqs_apply_u1q_noalloc": (_S, [ctypes.POINTER(_u32), _u32, _u32, _u32, _DP, _CP, _u32, _dbl,
+                                   _P, _P, _P, _u64, _P, _P, _P, _u64, _P, _P]),
+    "sqs_noalloc_last_error": (ctypes.c_char_p, []),
+    "sqs_noalloc_scratch_bytes": (_u64, []),
 }
 
 _lib = None
