@@ -125,6 +125,73 @@ def cpu_baseline(circ, budget_nnz=1 << 16):
                       f"(inputs <= {budget_nnz} branches), {units} updates in {dt:.2f} s"}, dt
 
 
+def _timed_steps(st, step, flush, stream, steps):
+    import torch
+    ms = []
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.mean(ms)
+
+
+def variants(circ, widths, stream, probs, norm, flush, args, st64):
+    """The FP32-storage / learned-sizing form against the plain FP64 form on
+    the same workload: updates/s of each and the fidelity of the FP32 result
+    to the FP64 one."""
+    import numpy as np
+
+    from paper_2503_15118_gb300 import predictor, sqs
+    units = None
+    pred, loss, (X, _) = predictor.trained_predictor(seed=0)
+    out = {"predictor": {"train_records": int(X.shape[0]), "train_mse": loss}}
+    ref = None
+    for name, amp32, learned in (("f64_exact", False, False), ("f32_exact", True, False),
+                                 ("f32_learned", True, True), ("f64_learned", False, True)):
+        st = sqs.State(widths, amp32=amp32, learned=learned, capacity_hint=1 << 25,
+                       stream=stream.cuda_stream, eps=circ["eps"])
+        if learned:
+            st.set_predictor(pred)
+
+        def step():
+            st.reset()
+            st.run(circ)
+            st.probabilities_device(PROB_REG, probs.data_ptr(), norm.data_ptr())
+
+        for _ in range(args.warmup):
+            step()
+        st.sync()
+        w0 = st.stats()["host_waits"]
+        ms = _timed_steps(st, step, flush, stream, args.steps)
+        waits = (st.stats()["host_waits"] - w0) / args.steps
+        lo, hi, a = st.export()
+        d = dict(zip(lo.tolist(), a.tolist()))
+        if units is None:
+            units = BENCH_UNITS[0]
+        entry = {"value": units / (ms / 1e3), "ms_per_step": ms,
+                 "host_waits_per_step": waits, "bytes_peak": st.stats()["bytes_peak"],
+                 "overflow_reruns": st.stats()["overflow_reruns"]}
+        if ref is None:
+            ref = d
+        else:
+            ov = sum(np.conj(v) * d.get(k, 0) for k, v in ref.items())
+            n1 = sum(abs(v) ** 2 for v in ref.values())
+            n2 = sum(abs(v) ** 2 for v in d.values())
+            entry["fidelity_vs_f64"] = float(abs(ov) ** 2 / (n1 * n2))
+        out[name] = entry
+        st.close()
+    pred.close()
+    return out
+
+
+BENCH_UNITS = [0]
+
+
 def run_reference(args, rank):
     if rank != 0:
         return 0
@@ -159,6 +226,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--amp32", action="store_true", help="FP32 amplitude storage")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP32-storage / learned-sizing comparison")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -206,6 +275,7 @@ def main():
     n_final = st.nnz()
     peak = st.peak_nnz()
     units += n_final  # the probability reduction reads every branch once
+    BENCH_UNITS[0] = units
 
     # Timed region: per-step events on the state's stream; L2 flushed between steps.
     st.trace_enable(64 * (args.steps + 1) * 8)
@@ -299,6 +369,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if not args.no_variants:
+        line["variants"] = variants(circ, widths, stream, probs, norm, flush, args, st)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, _ = cpu_baseline(circ)
         line["cpu_baseline"] = cb

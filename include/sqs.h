@@ -262,6 +262,59 @@ const char* sqs_last_error(const sqs_state* st);
 /* Library version string. */
 const char* sqs_version(void);
 
+/* ---- learned capacity predictor ------------------------------------------
+ * The paper sizes nothing in advance: its std::vector grows branch by branch
+ * (Sec. II.C).  A device state must be sized before a merge runs.  In exact
+ * mode the runtime uses the bound "an interference step at most doubles the
+ * branches it acts on" and reads the exact count back when that bound would
+ * outgrow the buffers.  In learned mode (SQS_SIZING_LEARNED plus an attached
+ * predictor) interference steps are queued until the next flush; their
+ * structural features go through one batched inference of this MLP, which
+ * predicts log2(branches after / branches before) of each step; the merge
+ * buckets are sized from the predicted counts; an undersized bucket is
+ * detected on the device (no write goes out of bounds) and the step and
+ * everything after it re-run at the exact size before the flush returns.
+ *
+ * Network: SQS_PRED_FEATURES inputs -> SQS_PRED_HIDDEN tanh -> SQS_PRED_HIDDEN
+ * tanh -> 1, FP32.  Parameters (SQS_PRED_PARAMS floats) in the order W1[H][F],
+ * b1[H], W2[H][H], b2[H], w3[H], b3.  Training minimises the mean squared
+ * error with Adam, all on the device. */
+#define SQS_PRED_FEATURES 16
+#define SQS_PRED_HIDDEN 32
+#define SQS_PRED_PARAMS 1633
+typedef struct sqs_predictor sqs_predictor;
+/* Deterministic initialisation from seed; work goes on cuda_stream. */
+sqs_status sqs_predictor_create(uint64_t seed, void* cuda_stream, sqs_predictor** out);
+void sqs_predictor_destroy(sqs_predictor* p);
+sqs_status sqs_predictor_get_params(const sqs_predictor* p, float* out);
+sqs_status sqs_predictor_set_params(sqs_predictor* p, const float* in);
+/* Y[i] = net(X[i]) for n samples of SQS_PRED_FEATURES floats (host arrays). */
+sqs_status sqs_predictor_predict(sqs_predictor* p, const float* X, uint32_t n, float* Y);
+/* Gradient of the mean squared error over the n samples (host arrays). */
+sqs_status sqs_predictor_gradient(sqs_predictor* p, const float* X, const float* T, uint32_t n,
+                                  float* grad, float* loss);
+/* Adam over `epochs` passes of mini-batches of `batch` samples. */
+sqs_status sqs_predictor_train(sqs_predictor* p, const float* X, const float* T, uint32_t n,
+                               uint32_t epochs, uint32_t batch, float lr, float* final_loss);
+/* Attaches a predictor (owned by the caller) used when the state was created
+ * with SQS_SIZING_LEARNED; NULL detaches. */
+sqs_status sqs_state_set_predictor(sqs_state* st, sqs_predictor* p);
+/* Records, for every interference step from now on, its feature vector and
+ * the measured log2(branches after / branches before) (training traces). */
+sqs_status sqs_state_record(sqs_state* st, uint32_t enable);
+/* Waits, copies up to cap records (X: cap * SQS_PRED_FEATURES floats, y: cap
+ * floats), writes the number available to *n and clears the records. */
+sqs_status sqs_state_read_records(sqs_state* st, float* X, float* y, uint32_t cap, uint32_t* n);
+
+typedef struct {
+  uint64_t host_waits;       /* times the host read the device counts         */
+  uint64_t overflow_reruns;  /* learned-mode steps re-run at the exact size    */
+  uint64_t learned_steps;    /* steps sized from a prediction                  */
+  uint64_t bytes_live;       /* device bytes currently held by the state       */
+  uint64_t bytes_peak;       /* largest bytes_live since creation              */
+} sqs_stats;
+sqs_status sqs_state_stats(const sqs_state* st, sqs_stats* out);
+
 /* ---- no-allocation variant --------------------------------------------------
  * The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory: code embedded in a host framework that owns

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/sqs.h"
@@ -119,6 +120,36 @@ struct sqs_state {
   std::vector<sqs_trace_record> trace;  // kernel / call of each used pair
   uint32_t trace_dropped = 0;
   uint32_t call = 0;                    // API call counter
+
+  // Structural history per key bit: the features of the learned predictor.
+  std::vector<int64_t> last_branch;  // index of the last interference step on the bit, -1: none
+  std::vector<uint32_t> writes_since, reads_since;  // operations since that step
+  std::vector<uint8_t> arith_since;  // the bit's register was an arithmetic destination since
+  std::vector<int8_t> const_val;     // value when the bit is known constant, else -1
+  int64_t n_branch = 0;
+  int64_t last_target = -1;
+
+  // Training traces: features and (in, out) counts of every interference step.
+  bool recording = false;
+  std::vector<float> rec_x;
+  unsigned long long* rec_dev = nullptr;
+  uint32_t rec_cap = 0;
+
+  // Learned sizing: queued interference steps (with the operations before
+  // each), sized at the next flush from one batched inference.
+  sqs_predictor* predictor = nullptr;
+  struct Lazy {
+    Gate1 g;
+    std::vector<HostOp> ops;
+    float x[SQS_PRED_FEATURES];
+  };
+  std::vector<Lazy> lazy;
+  bool defer_frees = false;
+  std::vector<void*> graveyard;
+  uint64_t grow_hint_b = 0;  // learned mode: buckets at the predicted peak (growth target)
+
+  sqs_stats stats{};
+  std::unordered_map<void*, size_t> sizes;
 };
 
 namespace {
@@ -149,15 +180,35 @@ void* dalloc(sqs_state* st, size_t bytes) {
     cudaGetLastError();
     p = nullptr;
   }
+  if (p) {
+    st->sizes[p] = bytes;
+    st->stats.bytes_live += bytes;
+    st->stats.bytes_peak = std::max(st->stats.bytes_peak, st->stats.bytes_live);
+  }
   return p;
 }
 
-void dfree(sqs_state* st, void* p) {
+void dfree_now(sqs_state* st, void* p) {
   if (!p) return;
+  auto it = st->sizes.find(p);
+  if (it != st->sizes.end()) {
+    st->stats.bytes_live -= it->second;
+    st->sizes.erase(it);
+  }
   if (st->has_alloc)
     st->alloc.free(st->alloc.ctx, p, (void*)st->stream);
   else
     cudaFreeAsync(p, st->stream);
+}
+
+// While a learned-sizing flush may still re-run a step, buffers that held
+// its input are kept alive instead of being freed.
+void dfree(sqs_state* st, void* p) {
+  if (!p) return;
+  if (st->defer_frees)
+    st->graveyard.push_back(p);
+  else
+    dfree_now(st, p);
 }
 
 size_t amp_bytes(const sqs_state* st) { return st->amp32 ? 8 : 16; }
@@ -247,12 +298,15 @@ bool encode_ctrls(sqs_state* st, const sqs_ctrl* c, uint32_t n, uint64_t mask[2]
 bool ctrl_touches(const uint64_t mask[2], uint32_t q) { return (mask[q >> 6] >> (q & 63)) & 1; }
 
 // Reads the control block (waits for the stream) and converts device errors.
-sqs_status sync_ctl(sqs_state* st) {
+// With report_only, a device error is returned without becoming sticky.
+sqs_status sync_ctl(sqs_state* st, bool report_only = false) {
   cudaError_t e = cudaMemcpyAsync(st->ctl_host, st->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
                                   st->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
   if (e != cudaSuccess) return cuda_fail(st, e, "synchronize");
+  st->stats.host_waits++;
   const Ctl& c = *st->ctl_host;
+  if (c.err && report_only) return SQS_ERR_CAPACITY;
   if (c.err) {
     st->sticky = (c.err & sqs::kErrProbe) ? SQS_ERR_TIMEOUT : SQS_ERR_CAPACITY;
     return fail(st, st->sticky,
@@ -307,7 +361,7 @@ size_t pack_ops(const std::vector<HostOp>& ops, size_t from, OpList& L) {
   L.touches_keys = L.touches_amps = L.drops = 0;
   Group g;
   size_t i = from;
-  constexpr uint32_t kGroupBits = 8;
+  constexpr uint32_t kGroupBits = 10;
   for (; i < ops.size(); ++i) {
     const HostOp& h = ops[i];
     const uint32_t kind = h.d.kind;
@@ -395,22 +449,30 @@ sqs_status run_pending(sqs_state* st, bool keep_tail) {
   return SQS_OK;
 }
 
-// One interference step: fused pending run + partition + pair.
-sqs_status run_branching(sqs_state* st, const Gate1& g) {
+// One interference step: fused pending run + partition + pair.  est_in < 0:
+// buckets sized from the hard bound st->ub (exact mode); otherwise from the
+// predicted input count est_in with a 20% margin (learned mode).
+sqs_status run_branching(sqs_state* st, const Gate1& g, double est_in = -1.0,
+                         int64_t rec_idx = -1) {
   sqs_status s = run_pending(st, true);  // leaves the fused tail in ops_buf
   if (s != SQS_OK) return st->sticky = s;
   const OpList& L = st->ops_buf;
   const uint64_t C = 1ull << kBucketLog2;
   const uint64_t target = C * 3 / 4;  // mean bucket fill: overflow is ~18 sigma away
-  uint64_t B = std::max<uint64_t>(1, (st->ub + target - 1) / target);
-  if ((B << kSegLog2) > st->alt.cap && st->ub > 1) {
+  const uint64_t want =
+      est_in < 0 ? st->ub : std::min<uint64_t>(st->ub, (uint64_t)(est_in * 1.2) + 1);
+  uint64_t B = std::max<uint64_t>(1, (want + target - 1) / target);
+  if (est_in < 0 && (B << kSegLog2) > st->alt.cap && st->ub > 1) {
     // The bound outgrew the allocation: learn the exact count first.
     s = sync_ctl(st);
     if (s != SQS_OK) return s;
     B = std::max<uint64_t>(1, (st->ub + target - 1) / target);
   }
   if (B > 0x7fffffffull) return st->sticky = fail(st, SQS_ERR_CAPACITY, "too many buckets");
-  if (!ensure_store(st, st->bk, B << kBucketLog2) || !ensure_store(st, st->alt, B << kSegLog2))
+  // Learned mode grows buffers straight to the predicted peak (grow_hint_b).
+  const uint64_t Bcap = std::max(B, st->grow_hint_b);
+  if ((st->bk.cap < (B << kBucketLog2) && !ensure_store(st, st->bk, Bcap << kBucketLog2)) ||
+      (st->alt.cap < (B << kSegLog2) && !ensure_store(st, st->alt, Bcap << kSegLog2)))
     return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate %llu branches",
                              (unsigned long long)(B << kSegLog2));
   st->bk.set_segments(kBucketLog2, (uint32_t)B);
@@ -431,6 +493,11 @@ sqs_status run_branching(sqs_state* st, const Gate1& g) {
                          st->alt.view(), out_slot);
   }
   if (e != cudaSuccess) return cuda_fail(st, e, "pair launch");
+  if (rec_idx >= 0) {
+    e = sqs::launch_record(launch_of(st, 1), st->ctl, st->cur_slot, out_slot,
+                           st->rec_dev + 2 * (size_t)rec_idx);
+    if (e != cudaSuccess) return cuda_fail(st, e, "record launch");
+  }
   std::swap(st->cur, st->alt);
   st->cur_slot = out_slot;
   st->ub = std::min(max_branches(st), 2 * st->ub);
@@ -438,6 +505,251 @@ sqs_status run_branching(sqs_state* st, const Gate1& g) {
 }
 
 bool is_zero(double re, double im) { return re == 0.0 && im == 0.0; }
+
+// ---- structural history (features of the learned predictor) ---------------
+void history_reset(sqs_state* st, bool known_zero) {
+  const uint32_t n = st->total_bits;
+  st->last_branch.assign(n, -1);
+  st->writes_since.assign(n, 0);
+  st->reads_since.assign(n, 0);
+  st->arith_since.assign(n, 0);
+  st->const_val.assign(n, known_zero ? 0 : -1);
+  st->n_branch = 0;
+  st->last_target = -1;
+}
+
+template <class F>
+void for_bits(const uint64_t m[2], uint32_t nbits, F f) {
+  for (uint32_t q = 0; q < nbits; ++q)
+    if ((m[q >> 6] >> (q & 63)) & 1ull) f(q);
+}
+
+// Every predicate bit known constant and equal to the required value?
+// 1: always holds, 0: never holds, -1: unknown.
+int predicate_known(const sqs_state* st, const uint64_t pm[2], const uint64_t pv[2]) {
+  int res = 1;
+  for (uint32_t q = 0; q < st->total_bits; ++q) {
+    if (!((pm[q >> 6] >> (q & 63)) & 1ull)) continue;
+    const int want = (int)((pv[q >> 6] >> (q & 63)) & 1ull);
+    if (st->const_val[q] < 0) res = res == 0 ? 0 : -1;
+    else if (st->const_val[q] != want) res = 0;
+  }
+  return res;
+}
+
+void note_field_write(sqs_state* st, uint32_t off, uint32_t w, bool arith) {
+  for (uint32_t b = 0; b < w; ++b) {
+    st->writes_since[off + b]++;
+    st->const_val[off + b] = -1;
+    if (arith) st->arith_since[off + b] = 1;
+  }
+}
+
+void note_field_read(sqs_state* st, uint32_t off, uint32_t w) {
+  for (uint32_t b = 0; b < w; ++b) st->reads_since[off + b]++;
+}
+
+// Updates the history for a queued non-interference operation.
+void note_op(sqs_state* st, const HostOp& h) {
+  const DevOp& d = h.d;
+  for_bits(d.pmask, st->total_bits, [&](uint32_t q) { st->reads_since[q]++; });
+  switch (d.kind) {
+    case sqs::OP_XOR:
+    case sqs::OP_MUL_XOR: {
+      const int known = predicate_known(st, d.pmask, d.pval);
+      for_bits(d.xmask, st->total_bits, [&](uint32_t q) {
+        st->writes_since[q]++;
+        if (st->const_val[q] >= 0) {
+          if (known == 1) st->const_val[q] ^= 1;
+          else if (known < 0) st->const_val[q] = -1;
+        }
+      });
+      if (d.kind == sqs::OP_MUL_XOR && d.sel_bit < 128) st->reads_since[d.sel_bit]++;
+      break;
+    }
+    case sqs::OP_ADD_REG:
+    case sqs::OP_SUB_REG:
+      note_field_read(st, d.src_off, d.src_w);
+      note_field_write(st, d.dst_off, d.dst_w, true);
+      break;
+    case sqs::OP_ADD_CONST:
+      note_field_write(st, d.dst_off, d.dst_w, true);
+      break;
+    case sqs::OP_SWAP:
+      note_field_write(st, d.dst_off, d.dst_w, true);
+      note_field_write(st, d.src_off, d.src_w, true);
+      break;
+    case sqs::OP_QRAM:
+      note_field_read(st, d.src_off, d.src_w);
+      note_field_write(st, d.dst_off, d.dst_w, true);
+      break;
+    case sqs::OP_MUL:
+      if (d.sel_bit < 128) st->reads_since[d.sel_bit]++;
+      break;
+    default:
+      break;
+  }
+}
+
+void push_op(sqs_state* st, const HostOp& h) {
+  note_op(st, h);
+  st->pending.push_back(h);
+}
+
+// Feature vector of an interference step on key bit t (before it runs).
+void features(const sqs_state* st, const Gate1& g, uint32_t n_ctrl, float* x) {
+  const uint32_t t = g.t;
+  const double lg = 1.0 / 4.0;
+  int n_const = 0;
+  for (uint32_t q = 0; q < st->total_bits; ++q) n_const += st->const_val[q] >= 0;
+  bool ctrl_unknown = false;
+  for_bits(g.cmask, st->total_bits, [&](uint32_t q) { ctrl_unknown |= st->const_val[q] < 0; });
+  const bool branched = st->last_branch[t] >= 0;
+  x[0] = (g.reuse & 0xfu) == (1u | 2u | 8u) ? 1.f : 0.f;  // H-like structure
+  x[1] = g.mode == 2 ? 1.f : 0.f;
+  x[2] = g.mode == 1 ? 1.f : 0.f;
+  x[3] = g.mode == 0 ? 1.f : 0.f;
+  x[4] = (float)n_ctrl / 4.f;
+  x[5] = st->const_val[t] >= 0 ? 1.f : 0.f;
+  x[6] = branched ? 1.f : 0.f;
+  x[7] = branched && st->writes_since[t] == 0 && st->reads_since[t] == 0 ? 1.f : 0.f;
+  x[8] = (float)(std::log2(1.0 + st->writes_since[t]) * lg);
+  x[9] = (float)(std::log2(1.0 + st->reads_since[t]) * lg);
+  x[10] = branched ? (float)(std::log2(1.0 + (double)(st->n_branch - st->last_branch[t])) * lg)
+                   : 1.f;
+  x[11] = st->total_bits ? (float)n_const / (float)st->total_bits : 0.f;
+  x[12] = st->last_target == (int64_t)t ? 1.f : 0.f;
+  x[13] = ctrl_unknown ? 1.f : 0.f;
+  x[14] = st->arith_since[t] ? 1.f : 0.f;
+  x[15] = 1.f;
+}
+
+void note_branch(sqs_state* st, const Gate1& g) {
+  for_bits(g.cmask, st->total_bits, [&](uint32_t q) { st->reads_since[q]++; });
+  const uint32_t t = g.t;
+  st->last_branch[t] = st->n_branch++;
+  st->writes_since[t] = st->reads_since[t] = 0;
+  st->arith_since[t] = 0;
+  st->const_val[t] = -1;
+  st->last_target = t;
+}
+
+// Queues (learned mode) or runs (exact mode) one interference step.
+sqs_status issue_branching(sqs_state* st, const Gate1& g, uint32_t n_ctrl) {
+  float x[SQS_PRED_FEATURES];
+  features(st, g, n_ctrl, x);
+  note_branch(st, g);
+  if ((st->flags & SQS_SIZING_LEARNED) && st->predictor) {
+    sqs_state::Lazy q;
+    q.g = g;
+    q.ops.swap(st->pending);
+    std::memcpy(q.x, x, sizeof(x));
+    st->lazy.push_back(std::move(q));
+    return SQS_OK;
+  }
+  int64_t rec = -1;
+  if (st->recording && st->rec_x.size() / SQS_PRED_FEATURES < st->rec_cap) {
+    rec = (int64_t)(st->rec_x.size() / SQS_PRED_FEATURES);
+    st->rec_x.insert(st->rec_x.end(), x, x + SQS_PRED_FEATURES);
+  }
+  return run_branching(st, g, -1.0, rec);
+}
+
+// Growth factor used for sizing from a predicted log2 ratio: a quarter of a
+// bit above the prediction, and never above the doubling bound, so that the
+// estimates chained from step to step do not drift below the true counts.
+double grow_factor(float y) {
+  return std::exp2(std::min(1.0, std::max(-8.0, (double)y + 0.25)));
+}
+
+// Executes the queued interference steps of learned mode: one batched
+// inference predicts every step's growth; buckets are sized from the
+// predicted counts; a device-side bucket overflow rolls back to the failed
+// step, whose input buffers were kept alive, and re-runs it and the steps
+// after it at the exact size.
+sqs_status run_lazy(sqs_state* st) {
+  if (st->lazy.empty()) return SQS_OK;
+  const size_t n = st->lazy.size();
+  std::vector<float> X(n * SQS_PRED_FEATURES), Y(n);
+  for (size_t i = 0; i < n; ++i)
+    std::memcpy(&X[i * SQS_PRED_FEATURES], st->lazy[i].x, sizeof(st->lazy[i].x));
+  sqs_status s = sqs_predictor_predict(st->predictor, X.data(), (uint32_t)n, Y.data());
+  if (s != SQS_OK) return st->sticky = fail(st, s, "predictor inference failed");
+  s = sync_ctl(st);  // exact count entering the first queued step
+  if (s != SQS_OK) return s;
+  std::vector<HostOp> tail;
+  tail.swap(st->pending);  // operations queued after the last step
+
+  struct Snap {
+    Store cur, alt, bk;
+    int cur_slot;
+    uint32_t seq;
+  };
+  std::vector<Snap> snaps(n);
+  st->defer_frees = true;
+  double est = (double)st->ub;
+  {
+    // Buffers that must grow during the flush grow once, to the predicted
+    // peak, so that few of them wait in the graveyard.
+    double e = est, peak = est;
+    for (size_t i = 0; i < n; ++i) {
+      const double r = grow_factor(Y[i]);
+      e = std::min(2.0 * e, std::max(1.0, e * r));
+      peak = std::max(peak, e);
+    }
+    st->grow_hint_b = (uint64_t)(peak * 1.2 / 1536.0) + 1;
+  }
+  for (size_t i = 0; i < n && s == SQS_OK; ++i) {
+    snaps[i] = Snap{st->cur, st->alt, st->bk, st->cur_slot, st->seq};
+    st->pending = st->lazy[i].ops;
+    s = run_branching(st, st->lazy[i].g, est);
+    const double r = grow_factor(Y[i]);
+    est = std::min(2.0 * est, std::max(1.0, est * r));
+  }
+  st->stats.learned_steps += n;
+  if (s == SQS_OK) s = sync_ctl(st, true);
+  if (s == SQS_ERR_CAPACITY && (st->ctl_host->err & ~sqs::kErrBucket) == 0) {
+    // Roll back to the first step whose launches include the failing one.
+    const uint32_t where = st->ctl_host->err_where;
+    size_t f = 0;
+    while (f + 1 < n && snaps[f + 1].seq < where) ++f;
+    for (Store* x : {&st->cur, &st->alt, &st->bk})
+      for (void* ptr : {(void*)x->k0, (void*)x->k1, x->amp, (void*)x->segs})
+        if (ptr) st->graveyard.push_back(ptr);
+    st->cur = snaps[f].cur;
+    st->alt = snaps[f].alt;
+    st->bk = snaps[f].bk;
+    st->cur_slot = snaps[f].cur_slot;
+    Ctl* c = st->ctl;
+    cudaMemsetAsync(&c->err, 0, sizeof(c->err) + sizeof(c->err_where), st->stream);
+    cudaMemsetAsync(&c->need, 0, sizeof(c->need), st->stream);
+    if (st->bk.segs)
+      cudaMemsetAsync(st->bk.segs, 0, ((st->bk.cap >> kBucketLog2) + 1) * 4, st->stream);
+    s = sync_ctl(st);  // exact input count of the failed step
+    for (size_t i = f; i < n && s == SQS_OK; ++i) {
+      st->pending = st->lazy[i].ops;
+      s = run_branching(st, st->lazy[i].g);
+      st->stats.overflow_reruns++;
+    }
+    if (s == SQS_OK) s = sync_ctl(st);
+  } else if (s == SQS_ERR_CAPACITY) {
+    s = sync_ctl(st);  // any other device error is sticky
+  }
+  st->defer_frees = false;
+  st->grow_hint_b = 0;
+  std::vector<void*> live;
+  for (Store* x : {&st->cur, &st->alt, &st->bk})
+    for (void* ptr : {(void*)x->k0, (void*)x->k1, x->amp, (void*)x->segs}) live.push_back(ptr);
+  std::sort(st->graveyard.begin(), st->graveyard.end());
+  st->graveyard.erase(std::unique(st->graveyard.begin(), st->graveyard.end()),
+                      st->graveyard.end());
+  for (void* p : st->graveyard)
+    if (std::find(live.begin(), live.end(), p) == live.end()) dfree_now(st, p);
+  st->graveyard.clear();
+  st->lazy.clear();
+  st->pending.swap(tail);
+  return s;
+}
 
 HostOp blank_op(uint32_t kind) {
   HostOp o;
@@ -477,7 +789,7 @@ sqs_status apply_1q(sqs_state* st, uint32_t reg, uint32_t bit, const double* m,
     o.d.sel_bit = t;
     o.c0 = std::complex<double>(m[0], m[1]);
     o.c1 = std::complex<double>(m[6], m[7]);
-    st->pending.push_back(o);
+    push_op(st, o);
     push_prune(st, st->eps);
     return SQS_OK;
   }
@@ -490,7 +802,7 @@ sqs_status apply_1q(sqs_state* st, uint32_t reg, uint32_t bit, const double* m,
     o.c0 = std::complex<double>(m[4], m[5]);
     o.c1 = std::complex<double>(m[2], m[3]);
     o.d.xmask[t >> 6] = 1ull << (t & 63);
-    st->pending.push_back(o);
+    push_op(st, o);
     push_prune(st, st->eps);
     return SQS_OK;
   }
@@ -520,11 +832,13 @@ sqs_status apply_1q(sqs_state* st, uint32_t reg, uint32_t bit, const double* m,
   g.eps = st->eps;
   g.eps2 = st->eps * st->eps;
   g.epsf = (float)st->eps;
-  return run_branching(st, g);
+  return issue_branching(st, g, n_ctrl);
 }
 
 sqs_status flush_all(sqs_state* st) {
   sqs_status s = check_usable(st);
+  if (s != SQS_OK) return s;
+  s = run_lazy(st);
   if (s != SQS_OK) return s;
   return run_pending(st, false);
 }
@@ -637,6 +951,7 @@ void sqs_state_destroy(sqs_state* st) {
   free_store(st, st->cur);
   free_store(st, st->alt);
   free_store(st, st->bk);
+  dfree(st, st->rec_dev);
   dfree(st, st->ctl);
   dfree(st, st->scratch);
   for (sqs_table* t : st->tables) {
@@ -653,10 +968,12 @@ void sqs_state_destroy(sqs_state* st) {
 sqs_status sqs_state_reset(sqs_state* st) {
   if (!st) return SQS_ERR_ARG;
   st->pending.clear();
+  st->lazy.clear();
   st->sticky = SQS_OK;
   st->err.clear();
   st->cur_slot = 0;
   st->ub = 1;
+  history_reset(st, true);
   if (st->bk.segs)
     cudaMemsetAsync(st->bk.segs, 0, ((st->bk.cap >> kBucketLog2) + 1) * 4, st->stream);
   st->cur.set_dense();
@@ -770,7 +1087,7 @@ sqs_status sqs_apply_perm(sqs_state* st, const sqs_perm_op* ops, uint32_t n_ops)
     }
     add.push_back(h);
   }
-  st->pending.insert(st->pending.end(), add.begin(), add.end());
+  for (const HostOp& h : add) push_op(st, h);
   return SQS_OK;
 }
 
@@ -784,7 +1101,7 @@ sqs_status sqs_apply_phase(sqs_state* st, const sqs_ctrl* pred, uint32_t n_pred,
   HostOp o = blank_op(sqs::OP_MUL);
   o.d.pmask[0] = cm[0], o.d.pmask[1] = cm[1], o.d.pval[0] = cv[0], o.d.pval[1] = cv[1];
   o.c0 = std::complex<double>(std::cos(phi), std::sin(phi));
-  st->pending.push_back(o);
+  push_op(st, o);
   return SQS_OK;
 }
 
@@ -837,7 +1154,7 @@ static sqs_status qram(sqs_state* st, uint32_t addr_reg, uint32_t data_reg, cons
   o.d.table = t->dev;
   o.d.n_entries = t->n;
   o.d.constant = t->bytes;
-  st->pending.push_back(o);
+  push_op(st, o);
   return SQS_OK;
 }
 
@@ -1026,6 +1343,8 @@ sqs_status sqs_import(sqs_state* st, const uint64_t* keys, const double* amps, u
   st->cur_slot = 0;
   st->ub = n;
   st->sticky = SQS_OK;
+  st->lazy.clear();
+  history_reset(st, false);
   return SQS_OK;
 }
 
@@ -1071,6 +1390,61 @@ sqs_status sqs_trace_read(sqs_state* st, sqs_trace_record* out, uint32_t cap, ui
   st->trace.clear();
   st->trace_dropped = 0;
   st->call = 0;
+  return SQS_OK;
+}
+
+sqs_status sqs_state_set_predictor(sqs_state* st, sqs_predictor* p) {
+  if (!st) return SQS_ERR_ARG;
+  sqs_status s = flush_all(st);  // steps queued under the old setting run first
+  if (s != SQS_OK) return s;
+  st->predictor = p;
+  return SQS_OK;
+}
+
+sqs_status sqs_state_record(sqs_state* st, uint32_t enable) {
+  sqs_status s = check_usable(st);
+  if (s != SQS_OK) return s;
+  if (enable && !st->rec_dev) {
+    st->rec_cap = 1u << 16;
+    st->rec_dev = (unsigned long long*)dalloc(st, (size_t)st->rec_cap * 16);
+    if (!st->rec_dev) return fail(st, SQS_ERR_OOM, "cannot allocate the record buffer");
+  }
+  st->recording = enable != 0;
+  return SQS_OK;
+}
+
+sqs_status sqs_state_read_records(sqs_state* st, float* X, float* y, uint32_t cap, uint32_t* n) {
+  if (!st || !n || (cap && (!X || !y))) return SQS_ERR_ARG;
+  sqs_status s = flush_all(st);
+  if (s != SQS_OK) return s;
+  const size_t nrec = st->rec_x.size() / SQS_PRED_FEATURES;
+  std::vector<unsigned long long> cnt(2 * std::max<size_t>(nrec, 1));
+  if (nrec) {
+    cudaError_t e = cudaMemcpyAsync(cnt.data(), st->rec_dev, nrec * 16, cudaMemcpyDeviceToHost,
+                                    st->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+    if (e != cudaSuccess) return cuda_fail(st, e, "records");
+  }
+  // Steps whose input was empty carry no ratio and are skipped.
+  uint32_t w = 0;
+  for (size_t i = 0; i < nrec; ++i) {
+    const unsigned long long a = cnt[2 * i], b = cnt[2 * i + 1];
+    if (a == 0) continue;
+    if (w < cap) {
+      std::memcpy(X + (size_t)w * SQS_PRED_FEATURES, &st->rec_x[i * SQS_PRED_FEATURES],
+                  SQS_PRED_FEATURES * sizeof(float));
+      y[w] = (float)std::log2((double)std::max<unsigned long long>(b, 1) / (double)a);
+    }
+    ++w;
+  }
+  *n = w;
+  st->rec_x.clear();
+  return SQS_OK;
+}
+
+sqs_status sqs_state_stats(const sqs_state* st, sqs_stats* out) {
+  if (!st || !out) return SQS_ERR_ARG;
+  *out = st->stats;
   return SQS_OK;
 }
 

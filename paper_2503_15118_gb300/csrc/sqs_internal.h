@@ -48,7 +48,7 @@ struct DevOp {
 };
 
 constexpr int kMaxOps = 64;      // fused operations per launch
-constexpr int kTabEntries = 512;  // folded factor entries per launch
+constexpr int kTabEntries = 1024;  // folded factor entries per launch
 
 struct OpList {
   uint32_t n;
@@ -141,6 +141,9 @@ cudaError_t launch_probabilities(const Launch& L, int kw, bool amp32, Ctl* ctl, 
 cudaError_t launch_densify(const Launch& L, int kw, bool amp32, Arr in, const uint64_t* offsets,
                            Arr out);
 cudaError_t launch_to_f64(const Launch& L, Ctl* ctl, Arr a, int slot, double* out);
+// rec[0] = cnt[in_slot], rec[1] = cnt[out_slot] (one interference step's counts).
+cudaError_t launch_record(const Launch& L, const Ctl* ctl, int in_slot, int out_slot,
+                          unsigned long long* rec);
 cudaError_t launch_from_f64(const Launch& L, Ctl* ctl, Arr a, const double* in, uint64_t n);
 
 int pair_log2_capacity(int kw, bool amp32);  // log2 branches per bucket

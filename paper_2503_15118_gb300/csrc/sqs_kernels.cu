@@ -88,15 +88,31 @@ __device__ __forceinline__ uint64_t khash(u128 k) {
 // FP32 (the FP32 pipe is 64x wider than the FP64 pipe here).  Two-term sums
 // of FP32 products are single FP32 roundings of the exact sum, which is the
 // value an FP64 accumulation rounded to the FP32 store would give.
+// Complex product with one product fused into the sum (two instructions per
+// component): one rounding fewer than the host's complex<double> product.
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  // Each product rounded, then one rounded sum: the operations of a
-  // complex<double> product on the host, up to commutation.
-  return make_double2(__dsub_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)),
-                      __dadd_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x)));
+  return make_double2(__fma_rn(a.x, b.x, -__dmul_rn(a.y, b.y)),
+                      __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x)));
 }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(__fsub_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)),
-                     __fadd_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+  return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)),
+                     __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
+// u * a + p (real u), fused per component.
+__device__ __forceinline__ double2 rfma(double u, double2 a, double2 p) {
+  return make_double2(__fma_rn(u, a.x, p.x), __fma_rn(u, a.y, p.y));
+}
+__device__ __forceinline__ float2 rfma(float u, float2 a, float2 p) {
+  return make_float2(__fmaf_rn(u, a.x, p.x), __fmaf_rn(u, a.y, p.y));
+}
+// c * a + p (complex c), fused.
+__device__ __forceinline__ double2 cfma(double2 c, double2 a, double2 p) {
+  return make_double2(__fma_rn(c.x, a.x, __fma_rn(-c.y, a.y, p.x)),
+                      __fma_rn(c.x, a.y, __fma_rn(c.y, a.x, p.y)));
+}
+__device__ __forceinline__ float2 cfma(float2 c, float2 a, float2 p) {
+  return make_float2(__fmaf_rn(c.x, a.x, __fmaf_rn(-c.y, a.y, p.x)),
+                     __fmaf_rn(c.x, a.y, __fmaf_rn(c.y, a.x, p.y)));
 }
 // Real coefficient: (u + 0i)(a.x + i a.y) evaluated as above is exactly these
 // two products.
@@ -138,6 +154,7 @@ __device__ __forceinline__ bool keep_amp(double2 a, double eps, float, double ep
   const unsigned long long ay =
       (unsigned long long)__double_as_longlong(a.y) & 0x7fffffffffffffffull;
   if (ax >= e || ay >= e) return true;
+  if ((ax | ay) == 0ull) return e == 0ull;  // exact zero: kept only when eps = 0
   return !(norm2(a) < eps2);
 }
 __device__ __forceinline__ bool keep_amp(float2 a, double, float epsf, double eps2) {
@@ -145,6 +162,7 @@ __device__ __forceinline__ bool keep_amp(float2 a, double, float epsf, double ep
   const unsigned int ax = (unsigned int)__float_as_int(a.x) & 0x7fffffffu;
   const unsigned int ay = (unsigned int)__float_as_int(a.y) & 0x7fffffffu;
   if (ax >= e || ay >= e) return true;
+  if ((ax | ay) == 0u) return eps2 == 0.0;
   return !(norm2(a) < eps2);
 }
 __device__ __forceinline__ void to_amp(double2& out, double2 v) { out = v; }
@@ -177,6 +195,8 @@ __device__ __forceinline__ bool slot_live(const Arr& a, uint64_t i) {
 
 // Calls f(i) for every live slot: grid-stride over a dense array, or CTA per
 // segment (live branches are a prefix of each segment).
+// Calls f(i) for every live slot: grid-stride over a dense array, or CTA per
+// segment (live branches are a prefix of each segment).
 template <class F>
 __device__ __forceinline__ void for_each_live(const Arr& a, uint64_t n_dense, F f) {
   if (!a.seg_cnt) {
@@ -202,13 +222,13 @@ __device__ __forceinline__ void raise_err(Ctl* ctl, unsigned int bit, uint32_t s
 // ---- fused operation run ---------------------------------------------------------
 // tab: the folded factors in the storage type (shared-memory copy).
 template <int KW, class AT>
-__device__ __forceinline__ bool apply_ops(const OpList& L, const AT* tab, typename KT<KW>::T& k,
-                                          AT& a) {
+__device__ __forceinline__ bool apply_ops(uint32_t n_ops, const DevOp* ops, const AT* tab,
+                                          typename KT<KW>::T& k, AT& a) {
   typedef typename KT<KW>::T K;
   uint32_t idx = 0;
 #pragma unroll 1
-  for (uint32_t o = 0; o < L.n; ++o) {
-    const DevOp& op = L.op[o];
+  for (uint32_t o = 0; o < n_ops; ++o) {
+    const DevOp& op = ops[o];
     const uint32_t kind = op.kind;
     const bool on = (k & mk<KW>(op.pmask[0], op.pmask[1])) == mk<KW>(op.pval[0], op.pval[1]);
     if (kind == OP_XOR) {
@@ -255,8 +275,16 @@ __device__ __forceinline__ bool apply_ops(const OpList& L, const AT* tab, typena
   return true;
 }
 
+// Copies the launch's operations and factor table into shared memory: the
+// per-branch loop then reads them with broadcast shared loads instead of
+// indexed parameter-space loads.
 template <class AT>
-__device__ __forceinline__ void load_tab(const OpList& L, AT* tab) {
+__device__ __forceinline__ void load_ops(const OpList& L, DevOp* ops, AT* tab) {
+  static_assert(sizeof(DevOp) % 8 == 0, "DevOp copied as 8-byte words");
+  const uint64_t* src = (const uint64_t*)L.op;
+  uint64_t* dst = (uint64_t*)ops;
+  const uint32_t words = L.n * (uint32_t)(sizeof(DevOp) / 8);
+  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
   for (uint32_t i = threadIdx.x; i < L.n_tab; i += blockDim.x) to_amp(tab[i], L.tab[i]);
   __syncthreads();
 }
@@ -284,14 +312,15 @@ template <int KW, class AT, bool TK, bool TA>
 __global__ void __launch_bounds__(kStreamThreads)
     k_apply_inplace(Ctl* ctl, Arr a, int slot, const __grid_constant__ OpList ops, uint32_t seq) {
   __shared__ AT tab[kTabEntries];
+  __shared__ DevOp sops[kMaxOps];
   if (ctl->err) return;
-  load_tab(ops, tab);
+  load_ops(ops, sops, tab);
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, ctl->cnt[slot]);
   for_each_live(a, ctl->cnt[slot], [&](uint64_t i) {
     typename KT<KW>::T k = ld_key<KW>(a, i);
     AT v;
     if (TA) v = ((const AT*)a.amp)[i];
-    apply_ops<KW, AT>(ops, tab, k, v);
+    apply_ops<KW, AT>(ops.n, sops, tab, k, v);
     if (TK) st_key<KW>(a, i, k);
     if (TA) ((AT*)a.amp)[i] = v;
   });
@@ -304,9 +333,10 @@ __global__ void __launch_bounds__(kStreamThreads)
     k_apply_compact(Ctl* ctl, Arr in, int in_slot, Arr out, int out_slot,
                     const __grid_constant__ OpList ops, uint32_t seq) {
   __shared__ AT tab[kTabEntries];
+  __shared__ DevOp sops[kMaxOps];
   __shared__ unsigned int seg_fill;
   if (ctl->err) return;
-  load_tab(ops, tab);
+  load_ops(ops, sops, tab);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->cnt[(out_slot + 1) & 3] = 0;
     atomicMax(&ctl->peak, ctl->cnt[in_slot]);
@@ -333,7 +363,7 @@ __global__ void __launch_bounds__(kStreamThreads)
       if (r + threadIdx.x < cnt) {
         k = ld_key<KW>(in, i);
         v = ((const AT*)in.amp)[i];
-        keep = apply_ops<KW, AT>(ops, tab, k, v);
+        keep = apply_ops<KW, AT>(ops.n, sops, tab, k, v);
       }
       const unsigned int ball = __ballot_sync(0xffffffffu, keep);
       unsigned int wbase = 0;
@@ -354,32 +384,83 @@ __global__ void __launch_bounds__(kStreamThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Each thread carries kPartILP branches at once, so their loads and their
+// bucket-counter atomics overlap instead of forming one long chain.
+constexpr int kPartILP = 4;
+
 template <int KW, class AT>
 __global__ void __launch_bounds__(kStreamThreads)
     k_partition(Ctl* ctl, Arr in, int in_slot, const __grid_constant__ OpList ops, Gate1 g,
                 Arr bk, uint32_t seq) {
   typedef typename KT<KW>::T K;
   __shared__ AT tab[kTabEntries];
+  __shared__ DevOp sops[kMaxOps];
   if (ctl->err) return;
-  load_tab(ops, tab);
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, ctl->cnt[in_slot]);
+  load_ops(ops, sops, tab);
+  const uint64_t n_dense = ctl->cnt[in_slot];
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, n_dense);
   const K bmask = ((K)1) << g.t;
   const uint32_t C = 1u << bk.seg_log2;
-  for_each_live(in, ctl->cnt[in_slot], [&](uint64_t i) {
-    K k = ld_key<KW>(in, i);
-    AT v = ((const AT*)in.amp)[i];
-    if (!apply_ops<KW, AT>(ops, tab, k, v)) return;
-    const uint64_t h = khash(k & ~bmask);
-    const uint32_t b = (uint32_t)(((h >> 32) * (uint64_t)bk.n_seg) >> 32);
-    const unsigned int pos = atomicAdd(&bk.seg_cnt[b], 1u);
-    if (pos < C) {
-      const uint64_t j = ((uint64_t)b << bk.seg_log2) + pos;
-      st_key<KW>(bk, j, k);
-      ((AT*)bk.amp)[j] = v;
+  // Units of kPartILP * blockDim slots: a slice of a segment, or of the dense
+  // array.
+  const uint32_t unit = kPartILP * blockDim.x;
+  uint32_t per_seg = 1;
+  uint64_t units;
+  if (in.seg_cnt) {
+    per_seg = ((1u << in.seg_log2) + unit - 1) / unit;
+    units = (uint64_t)in.n_seg * per_seg;
+  } else {
+    units = (n_dense + unit - 1) / unit;
+  }
+  for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    uint64_t base;
+    uint32_t lim;
+    if (in.seg_cnt) {
+      const uint32_t sg = (uint32_t)(u / per_seg);
+      const uint32_t off = (uint32_t)(u - (uint64_t)sg * per_seg) * unit;
+      const uint32_t cnt = in.seg_cnt[sg];
+      if (off >= cnt) continue;
+      base = ((uint64_t)sg << in.seg_log2) + off;
+      lim = cnt - off < unit ? cnt - off : unit;
     } else {
-      raise_err(ctl, kErrBucket, seq, (unsigned long long)pos + 1);
+      base = u * unit;
+      lim = (uint32_t)(n_dense - base < unit ? n_dense - base : unit);
     }
-  });
+    K k[kPartILP];
+    AT v[kPartILP];
+    bool live[kPartILP];
+#pragma unroll
+    for (int q = 0; q < kPartILP; ++q) {
+      const uint32_t j = q * blockDim.x + threadIdx.x;
+      live[q] = j < lim;
+      if (live[q]) {
+        k[q] = ld_key<KW>(in, base + j);
+        v[q] = ((const AT*)in.amp)[base + j];
+      }
+    }
+    unsigned int pos[kPartILP];
+    uint32_t bkt[kPartILP];
+#pragma unroll
+    for (int q = 0; q < kPartILP; ++q) {
+      if (live[q]) live[q] = apply_ops<KW, AT>(ops.n, sops, tab, k[q], v[q]);
+      if (live[q]) {
+        const uint64_t h = khash(k[q] & ~bmask);
+        bkt[q] = (uint32_t)(((h >> 32) * (uint64_t)bk.n_seg) >> 32);
+        pos[q] = atomicAdd(&bk.seg_cnt[bkt[q]], 1u);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kPartILP; ++q) {
+      if (!live[q]) continue;
+      if (pos[q] < C) {
+        const uint64_t j = ((uint64_t)bkt[q] << bk.seg_log2) + pos[q];
+        st_key<KW>(bk, j, k[q]);
+        ((AT*)bk.amp)[j] = v[q];
+      } else {
+        raise_err(ctl, kErrBucket, seq, (unsigned long long)pos[q] + 1);
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -406,7 +487,8 @@ template <class AT>
 __device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, bool has0, AT a0,
                                          bool has1, AT a1, AT& o0, AT& o1) {
   typedef typename Coef<AT>::S S;
-  AT p00, p10, p01, p11;  // row r, column s: U[r][s] * a_s
+  const bool same0 = g.reuse & 1u, neg0 = g.reuse & 4u;  // U10 = +-U00
+  const bool same1 = g.reuse & 2u, neg1 = g.reuse & 8u;  // U11 = +-U01
   if (g.mode == 2 || g.mode == 1) {
     S u00, u01, u10, u11;
     if (g.mode == 1) {
@@ -418,33 +500,33 @@ __device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, b
       u00 = Coef<AT>::r(g, 0), u01 = Coef<AT>::r(g, 1), u10 = Coef<AT>::r(g, 2),
       u11 = Coef<AT>::r(g, 3);
     }
-    if (has0) {
-      p00 = rmul(u00, a0);
-      p10 = (g.reuse & 1u) ? ((g.reuse & 4u) ? cneg(p00) : p00) : rmul(u10, a0);
-    }
-    if (has1) {
-      p01 = rmul(u01, a1);
-      p11 = (g.reuse & 2u) ? ((g.reuse & 8u) ? cneg(p01) : p01) : rmul(u11, a1);
+    if (has0 && has1) {
+      const AT p01 = rmul(u01, a1);
+      const AT p11 = same1 ? (neg1 ? cneg(p01) : p01) : rmul(u11, a1);
+      o0 = rfma(u00, a0, p01);
+      o1 = rfma(u10, a0, p11);
+    } else if (has0) {
+      o0 = rmul(u00, a0);
+      o1 = same0 ? (neg0 ? cneg(o0) : o0) : rmul(u10, a0);
+    } else {
+      o0 = rmul(u01, a1);
+      o1 = same1 ? (neg1 ? cneg(o0) : o0) : rmul(u11, a1);
     }
   } else {
-    if (has0) {
-      p00 = cmul(Coef<AT>::c(g, 0), a0);
-      p10 = (g.reuse & 1u) ? ((g.reuse & 4u) ? cneg(p00) : p00) : cmul(Coef<AT>::c(g, 2), a0);
+    const AT U00 = Coef<AT>::c(g, 0), U01 = Coef<AT>::c(g, 1);
+    const AT U10 = Coef<AT>::c(g, 2), U11 = Coef<AT>::c(g, 3);
+    if (has0 && has1) {
+      const AT p01 = cmul(U01, a1);
+      const AT p11 = same1 ? (neg1 ? cneg(p01) : p01) : cmul(U11, a1);
+      o0 = cfma(U00, a0, p01);
+      o1 = cfma(U10, a0, p11);
+    } else if (has0) {
+      o0 = cmul(U00, a0);
+      o1 = same0 ? (neg0 ? cneg(o0) : o0) : cmul(U10, a0);
+    } else {
+      o0 = cmul(U01, a1);
+      o1 = same1 ? (neg1 ? cneg(o0) : o0) : cmul(U11, a1);
     }
-    if (has1) {
-      p01 = cmul(Coef<AT>::c(g, 1), a1);
-      p11 = (g.reuse & 2u) ? ((g.reuse & 8u) ? cneg(p01) : p01) : cmul(Coef<AT>::c(g, 3), a1);
-    }
-  }
-  if (has0 && has1) {
-    o0 = cadd(p00, p01);
-    o1 = cadd(p10, p11);
-  } else if (has0) {
-    o0 = p00;
-    o1 = p10;
-  } else {
-    o0 = p01;
-    o1 = p11;
   }
 }
 
@@ -508,16 +590,42 @@ __global__ void __launch_bounds__(kPairThreads)
   }
   __syncthreads();
 
-  const uint64_t obase = (uint64_t)b << out.seg_log2;
+  // Emitters: branches the controls leave alone, unpaired branches and the
+  // bit-0 member of each pair.  Listing them first (in the probe table, which
+  // is free now) keeps every lane of the arithmetic below busy.
+  unsigned int* emit = slot;
   const uint32_t lane = threadIdx.x & 31u;
   const unsigned int lt = (1u << lane) - 1u;
-  const uint32_t rounds = (n + blockDim.x - 1u) / blockDim.x;
-  for (uint32_t r = 0; r < rounds; ++r) {
+  if (threadIdx.x == 0) fill = 0;
+  __shared__ unsigned int n_emit;
+  if (threadIdx.x == 0) n_emit = 0;
+  __syncthreads();
+  const uint32_t rounds_in = (n + blockDim.x - 1u) / blockDim.x;
+  for (uint32_t r = 0; r < rounds_in; ++r) {
     const uint32_t i = r * blockDim.x + threadIdx.x;
+    bool e = false;
+    if (i < n) {
+      const K k = skey[i];
+      e = (k & cmask) != cval || !((k & bmask) != (K)0 && partner[i] >= 0);
+    }
+    const unsigned int ball = __ballot_sync(0xffffffffu, e);
+    unsigned int wb = 0;
+    if (lane == 0 && ball) wb = atomicAdd(&n_emit, (unsigned int)__popc(ball));
+    wb = __shfl_sync(0xffffffffu, wb, 0);
+    if (e) emit[wb + __popc(ball & lt)] = i;
+  }
+  __syncthreads();
+  const uint32_t ne = n_emit;
+
+  const uint64_t obase = (uint64_t)b << out.seg_log2;
+  const uint32_t rounds = (ne + blockDim.x - 1u) / blockDim.x;
+  for (uint32_t r = 0; r < rounds; ++r) {
+    const uint32_t q = r * blockDim.x + threadIdx.x;
     bool keep0 = false, keep1 = false;
     K k0 = 0, k1 = 0;
     AT o0, o1;
-    if (i < n) {
+    if (q < ne) {
+      const uint32_t i = emit[q];
       const K k = skey[i];
       const AT ai = samp[i];
       if ((k & cmask) != cval) {
@@ -527,17 +635,15 @@ __global__ void __launch_bounds__(kPairThreads)
       } else {
         const bool kt = (k & bmask) != (K)0;
         const int j = partner[i];
-        if (!(kt && j >= 0)) {  // the bit-1 member of a pair is emitted by its partner
-          k0 = k & ~bmask;
-          k1 = k | bmask;
-          const uint64_t av = g.mode == 1 ? get_field(k0, g.ang_off, g.ang_w) : 0ull;
-          if (!kt)
-            children<AT>(g, av, true, ai, j >= 0, j >= 0 ? samp[j] : ai, o0, o1);
-          else
-            children<AT>(g, av, false, ai, true, ai, o0, o1);
-          keep0 = keep_amp(o0, g.eps, g.epsf, g.eps2);
-          keep1 = keep_amp(o1, g.eps, g.epsf, g.eps2);
-        }
+        k0 = k & ~bmask;
+        k1 = k | bmask;
+        const uint64_t av = g.mode == 1 ? get_field(k0, g.ang_off, g.ang_w) : 0ull;
+        if (!kt)
+          children<AT>(g, av, true, ai, j >= 0, j >= 0 ? samp[j] : ai, o0, o1);
+        else
+          children<AT>(g, av, false, ai, true, ai, o0, o1);
+        keep0 = keep_amp(o0, g.eps, g.epsf, g.eps2);
+        keep1 = keep_amp(o1, g.eps, g.epsf, g.eps2);
       }
     }
     const unsigned int b0 = __ballot_sync(0xffffffffu, keep0);
@@ -765,6 +871,19 @@ cudaError_t launch_densify(const Launch& L, int kw, bool amp32, Arr in, const ui
 #define SQS_DN(KW_, AT_) k_densify<KW_, AT_><<<in.n_seg, 256, 0, L.stream>>>(in, offsets, out)
   SQS_DISPATCH(kw, amp32, SQS_DN);
 #undef SQS_DN
+  return cudaGetLastError();
+}
+
+__global__ void k_record(const Ctl* ctl, int in_slot, int out_slot, unsigned long long* rec) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    rec[0] = ctl->cnt[in_slot];
+    rec[1] = ctl->cnt[out_slot];
+  }
+}
+
+cudaError_t launch_record(const Launch& L, const Ctl* ctl, int in_slot, int out_slot,
+                          unsigned long long* rec) {
+  k_record<<<1, 32, 0, L.stream>>>(ctl, in_slot, out_slot, rec);
   return cudaGetLastError();
 }
 

@@ -39,6 +39,15 @@ class PermOp(ctypes.Structure):
                 ("n_ctrl", ctypes.c_uint32), ("ctrl", Ctrl * MAX_CTRL)]
 
 
+class Stats(ctypes.Structure):
+    _fields_ = [("host_waits", ctypes.c_uint64), ("overflow_reruns", ctypes.c_uint64),
+                ("learned_steps", ctypes.c_uint64), ("bytes_live", ctypes.c_uint64),
+                ("bytes_peak", ctypes.c_uint64)]
+
+
+PRED_FEATURES, PRED_HIDDEN, PRED_PARAMS = 16, 32, 1633
+
+
 class TraceRecord(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_uint32), ("call", ctypes.c_uint32), ("ms", ctypes.c_float),
                 ("pad", ctypes.c_uint32)]
@@ -62,6 +71,7 @@ _S = ctypes.c_int
 _CP = ctypes.POINTER(Ctrl)
 _DP = ctypes.POINTER(ctypes.c_double)
 _UP = ctypes.POINTER(ctypes.c_uint64)
+_FP = ctypes.POINTER(ctypes.c_float)
 SIGNATURES = {
     "sqs_state_create": (_S, [ctypes.POINTER(_u32), _u32, _u32, _u64,
                               ctypes.POINTER(Allocator), _P, ctypes.POINTER(_P)]),
@@ -96,6 +106,17 @@ SIGNATURES = {
                                    _P, _P, _P, _u64, _P, _P, _P, _u64, _P, _P]),
     "sqs_noalloc_last_error": (ctypes.c_char_p, []),
     "sqs_noalloc_scratch_bytes": (_u64, []),
+    "sqs_predictor_create": (_S, [_u64, _P, ctypes.POINTER(_P)]),
+    "sqs_predictor_destroy": (None, [_P]),
+    "sqs_predictor_get_params": (_S, [_P, _FP]),
+    "sqs_predictor_set_params": (_S, [_P, _FP]),
+    "sqs_predictor_predict": (_S, [_P, _FP, _u32, _FP]),
+    "sqs_predictor_gradient": (_S, [_P, _FP, _FP, _u32, _FP, _FP]),
+    "sqs_predictor_train": (_S, [_P, _FP, _FP, _u32, _u32, _u32, ctypes.c_float, _FP]),
+    "sqs_state_set_predictor": (_S, [_P, _P]),
+    "sqs_state_record": (_S, [_P, _u32]),
+    "sqs_state_read_records": (_S, [_P, _FP, _FP, _u32, ctypes.POINTER(_u32)]),
+    "sqs_state_stats": (_S, [_P, ctypes.POINTER(Stats)]),
 }
 
 _lib = None
@@ -290,6 +311,27 @@ class State:
     def launch_count(self):
         return int(self.lib.sqs_launch_count(self.h))
 
+    def set_predictor(self, pred):
+        self._pred = pred
+        self._chk(self.lib.sqs_state_set_predictor(self.h, pred.h if pred is not None else None))
+
+    def record(self, enable=True):
+        self._chk(self.lib.sqs_state_record(self.h, 1 if enable else 0))
+
+    def read_records(self, cap=1 << 16):
+        X = np.zeros((cap, PRED_FEATURES), np.float32)
+        y = np.zeros(cap, np.float32)
+        n = ctypes.c_uint32()
+        self._chk(self.lib.sqs_state_read_records(self.h, X.ctypes.data_as(_FP),
+                                                  y.ctypes.data_as(_FP), cap, ctypes.byref(n)))
+        k = min(int(n.value), cap)
+        return X[:k], y[:k]
+
+    def stats(self):
+        s = Stats()
+        self._chk(self.lib.sqs_state_stats(self.h, ctypes.byref(s)))
+        return {f: int(getattr(s, f)) for f, _ in Stats._fields_}
+
     def trace_enable(self, max_records):
         self._chk(self.lib.sqs_trace_enable(self.h, int(max_records)))
 
@@ -388,9 +430,79 @@ class State:
         return self
 
 
-def run_circuit(circ, amp32=False, learned=False, merge=MERGE_AUTO, capacity_hint=0, upto=None):
+class Predictor:
+    """The learned capacity predictor (include/sqs.h, sqs_predictor_*)."""
+
+    def __init__(self, seed=0, stream=None):
+        self.lib = load()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = ctypes.c_void_p()
+        st = self.lib.sqs_predictor_create(int(seed), ctypes.c_void_p(int(stream or 0)),
+                                           ctypes.byref(h))
+        if st != OK:
+            raise SqsError(st, "sqs_predictor_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sqs_predictor_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        w = np.zeros(PRED_PARAMS, np.float32)
+        self._chk(self.lib.sqs_predictor_get_params(self.h, w.ctypes.data_as(_FP)))
+        return w
+
+    def set_params(self, w):
+        w = np.ascontiguousarray(w, np.float32)
+        assert w.shape == (PRED_PARAMS,)
+        self._chk(self.lib.sqs_predictor_set_params(self.h, w.ctypes.data_as(_FP)))
+
+    def predict(self, X):
+        X = np.ascontiguousarray(X, np.float32).reshape(-1, PRED_FEATURES)
+        Y = np.zeros(X.shape[0], np.float32)
+        self._chk(self.lib.sqs_predictor_predict(self.h, X.ctypes.data_as(_FP), X.shape[0],
+                                                 Y.ctypes.data_as(_FP)))
+        return Y
+
+    def gradient(self, X, T):
+        X = np.ascontiguousarray(X, np.float32).reshape(-1, PRED_FEATURES)
+        T = np.ascontiguousarray(T, np.float32)
+        g = np.zeros(PRED_PARAMS, np.float32)
+        loss = ctypes.c_float()
+        self._chk(self.lib.sqs_predictor_gradient(self.h, X.ctypes.data_as(_FP),
+                                                  T.ctypes.data_as(_FP), X.shape[0],
+                                                  g.ctypes.data_as(_FP), ctypes.byref(loss)))
+        return g, float(loss.value)
+
+    def train(self, X, T, epochs=200, batch=256, lr=3e-3):
+        X = np.ascontiguousarray(X, np.float32).reshape(-1, PRED_FEATURES)
+        T = np.ascontiguousarray(T, np.float32)
+        loss = ctypes.c_float()
+        self._chk(self.lib.sqs_predictor_train(self.h, X.ctypes.data_as(_FP),
+                                               T.ctypes.data_as(_FP), X.shape[0], epochs, batch,
+                                               float(lr), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def _chk(self, status):
+        if status != OK:
+            raise SqsError(status, "predictor call failed")
+
+
+def run_circuit(circ, amp32=False, learned=False, merge=MERGE_AUTO, capacity_hint=0, upto=None,
+                predictor=None):
     st = State(circ["widths"], amp32=amp32, learned=learned, merge=merge,
                capacity_hint=capacity_hint, eps=circ.get("eps", 1e-14))
+    if predictor is not None:
+        st.set_predictor(predictor)
     return st.run(circ, upto=upto)
 
 

@@ -309,3 +309,30 @@ def test_reflection_R_matches_definition():
     got = st.to_dict()
     for i in range(16):
         assert abs(got.get(i, 0) - want[i]) < 1e-14
+
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    """Pins the reference network's analytic gradient against central
+    differences of its forward pass (FP64)."""
+    from oracle import mlp
+    rng = np.random.default_rng(4)
+    p = rng.normal(scale=0.3, size=mlp.N_PARAMS)
+    X = rng.normal(size=(7, mlp.F))
+    T = rng.normal(size=7)
+    g = mlp.gradient(p, X, T)
+    h = 1e-6
+    idx = rng.choice(mlp.N_PARAMS, size=60, replace=False)
+    for i in list(idx) + [mlp.N_PARAMS - 1, 0]:
+        e = np.zeros_like(p)
+        e[i] = h
+        num = (mlp.loss(p + e, X, T) - mlp.loss(p - e, X, T)) / (2 * h)
+        assert abs(num - g[i]) <= 1e-6 * max(1.0, abs(num)), (i, num, g[i])
+
+
+def test_mlp_oracle_forward_closed_form():
+    """Zero weights: the output is the output bias whatever the input."""
+    from oracle import mlp
+    p = np.zeros(mlp.N_PARAMS)
+    p[-1] = 0.37
+    y, _, _ = mlp.forward(p, np.ones((3, mlp.F)))
+    assert np.allclose(y, 0.37)
