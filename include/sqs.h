@@ -57,9 +57,10 @@ typedef enum {
 #define SQS_SIZING_LEARNED 2u     /* sized by the learned capacity predictor;
                                      an overflow is detected on the device and
                                      the operation re-run at the exact size     */
-#define SQS_MERGE_AUTO 0u         /* merge path chosen per step by measurement  */
-#define SQS_MERGE_HASH 4u         /* force the bucketed hash merge              */
+#define SQS_MERGE_AUTO 0u         /* default merge path (per-CTA buckets)       */
+#define SQS_MERGE_HASH 4u         /* force the per-CTA bucket merge             */
 #define SQS_MERGE_SORT 8u         /* force the radix-sort merge                 */
+#define SQS_MERGE_CLUSTER 16u     /* force the cluster (binned) merge           */
 
 /*
  * One control (or predicate) qubit: bit `bit` of register `reg` must equal

@@ -449,6 +449,49 @@ sqs_status run_pending(sqs_state* st, bool keep_tail) {
   return SQS_OK;
 }
 
+// One interference step on the binned cluster path: k_bin then
+// k_pair_cluster.  The fused run is already packed in st->ops_buf.
+sqs_status run_binned(sqs_state* st, const Gate1& g, uint64_t B1, int64_t rec_idx) {
+  const OpList& L = st->ops_buf;
+  const uint32_t bin_log2 = (uint32_t)sqs::cluster_bin_log2();
+  const uint32_t seg_log2 = (uint32_t)sqs::cluster_out_seg_log2();
+  const uint64_t ctas = (uint64_t)sqs::cluster_ctas();
+  const uint64_t Bcap = std::max<uint64_t>(B1, (st->grow_hint_b * 1536) >> bin_log2);
+  // One extra slice of padding: a bulk copy rounds its size up to 16 bytes.
+  const uint64_t bin_need = (B1 << bin_log2) + 4096;
+  const uint64_t out_need = (B1 * ctas) << seg_log2;
+  if ((st->bk.cap < bin_need && !ensure_store(st, st->bk, ((Bcap << bin_log2) + 4096))) ||
+      (st->alt.cap < out_need && !ensure_store(st, st->alt, (Bcap * ctas) << seg_log2)))
+    return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate %llu branches",
+                             (unsigned long long)out_need);
+  st->bk.set_segments(bin_log2, (uint32_t)B1);
+  st->alt.set_segments(seg_log2, (uint32_t)(B1 * ctas));
+  const uint64_t in_slots = st->cur.slots(st->ub);
+  const int out_slot = (st->cur_slot + 1) & 3;
+  cudaError_t e;
+  {
+    Traced tr(st, SQS_K_PARTITION);
+    e = sqs::launch_bin(launch_of(st, in_slots), st->kw, st->amp32, st->ctl, st->cur.view(),
+                        st->cur_slot, L, g, st->bk.view());
+  }
+  if (e != cudaSuccess) return cuda_fail(st, e, "bin launch");
+  {
+    Traced tr(st, SQS_K_PAIR);
+    e = sqs::launch_pair_cluster(launch_of(st, in_slots), st->kw, st->amp32, st->ctl, g,
+                                 st->bk.view(), st->alt.view(), out_slot);
+  }
+  if (e != cudaSuccess) return cuda_fail(st, e, "cluster pair launch");
+  if (rec_idx >= 0) {
+    e = sqs::launch_record(launch_of(st, 1), st->ctl, st->cur_slot, out_slot,
+                           st->rec_dev + 2 * (size_t)rec_idx);
+    if (e != cudaSuccess) return cuda_fail(st, e, "record launch");
+  }
+  std::swap(st->cur, st->alt);
+  st->cur_slot = out_slot;
+  st->ub = std::min(max_branches(st), 2 * st->ub);
+  return SQS_OK;
+}
+
 // One interference step: fused pending run + partition + pair.  est_in < 0:
 // buckets sized from the hard bound st->ub (exact mode); otherwise from the
 // predicted input count est_in with a 20% margin (learned mode).
@@ -459,16 +502,31 @@ sqs_status run_branching(sqs_state* st, const Gate1& g, double est_in = -1.0,
   const OpList& L = st->ops_buf;
   const uint64_t C = 1ull << kBucketLog2;
   const uint64_t target = C * 3 / 4;  // mean bucket fill: overflow is ~18 sigma away
-  const uint64_t want =
+  uint64_t want =
       est_in < 0 ? st->ub : std::min<uint64_t>(st->ub, (uint64_t)(est_in * 1.2) + 1);
-  uint64_t B = std::max<uint64_t>(1, (want + target - 1) / target);
-  if (est_in < 0 && (B << kSegLog2) > st->alt.cap && st->ub > 1) {
+  // The per-CTA bucket merge is the default (measured faster at every size
+  // of the benchmark workload); the binned cluster merge runs when requested
+  // and the state fits the bins one launch carries.
+  const uint64_t bin_target = (3ull << sqs::cluster_bin_log2()) / 4;
+  auto plan = [&](uint64_t w, uint64_t& B, uint64_t& B1) {
+    B = std::max<uint64_t>(1, (w + target - 1) / target);
+    B1 = std::max<uint64_t>(1, (w + bin_target - 1) / bin_target);
+    const bool binned = (st->flags & SQS_MERGE_CLUSTER) && B1 <= (uint64_t)sqs::kMaxBins;
+    return binned ? ((B1 * sqs::cluster_ctas()) << sqs::cluster_out_seg_log2())
+                  : (B << kSegLog2);
+  };
+  uint64_t B, B1;
+  uint64_t need = plan(want, B, B1);
+  if (est_in < 0 && need > st->alt.cap && st->ub > 1) {
     // The bound outgrew the allocation: learn the exact count first.
     s = sync_ctl(st);
     if (s != SQS_OK) return s;
-    B = std::max<uint64_t>(1, (st->ub + target - 1) / target);
+    want = st->ub;
+    need = plan(want, B, B1);
   }
   if (B > 0x7fffffffull) return st->sticky = fail(st, SQS_ERR_CAPACITY, "too many buckets");
+  if ((st->flags & SQS_MERGE_CLUSTER) && B1 <= (uint64_t)sqs::kMaxBins)
+    return run_binned(st, g, B1, rec_idx);
   // Learned mode grows buffers straight to the predicted peak (grow_hint_b).
   const uint64_t Bcap = std::max(B, st->grow_hint_b);
   if ((st->bk.cap < (B << kBucketLog2) && !ensure_store(st, st->bk, Bcap << kBucketLog2)) ||
@@ -891,7 +949,8 @@ sqs_status sqs_state_create(const uint32_t* reg_widths, uint32_t n_regs, uint32_
                             uint64_t capacity_hint, const sqs_allocator* allocator,
                             void* cuda_stream, sqs_state** out) {
   if (!out || !reg_widths || n_regs == 0 || n_regs > 128) return SQS_ERR_ARG;
-  if (flags & ~(SQS_AMP_FP32 | SQS_SIZING_LEARNED | SQS_MERGE_HASH | SQS_MERGE_SORT))
+  if (flags & ~(SQS_AMP_FP32 | SQS_SIZING_LEARNED | SQS_MERGE_HASH | SQS_MERGE_SORT |
+                SQS_MERGE_CLUSTER))
     return SQS_ERR_ARG;
   uint32_t total = 0;
   for (uint32_t j = 0; j < n_regs; ++j) {

@@ -146,6 +146,18 @@ cudaError_t launch_record(const Launch& L, const Ctl* ctl, int in_slot, int out_
                           unsigned long long* rec);
 cudaError_t launch_from_f64(const Launch& L, Ctl* ctl, Arr a, const double* in, uint64_t n);
 
+// Binned merge (thread-block clusters): bins of 2^cluster_bin_log2()
+// branches, each paired by cluster_ctas() CTAs whose survivors go to output
+// segments (bin * cluster_ctas() + rank) of 2^cluster_out_seg_log2() slots.
+constexpr int kMaxBins = 2048;
+int cluster_bin_log2();
+int cluster_ctas();
+int cluster_out_seg_log2();
+cudaError_t launch_bin(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
+                       const OpList& ops, const Gate1& g, Arr bins);
+cudaError_t launch_pair_cluster(const Launch& L, int kw, bool amp32, Ctl* ctl, const Gate1& g,
+                                Arr bins, Arr out, int out_slot);
+
 int pair_log2_capacity(int kw, bool amp32);  // log2 branches per bucket
 size_t pair_smem_bytes(int kw, bool amp32);  // dynamic shared memory of one bucket CTA
 

@@ -740,6 +740,420 @@ __global__ void k_from_f64(const double2* in, uint64_t n, float2* amp) {
 }
 
 // ---------------------------------------------------------------------------
+// Binned merge: coarse bins filled in coalesced runs, paired by a cluster.
+//
+// k_bin streams the state through the fused run and sorts each tile of
+// kBinTile branches by bin in shared memory, so each tile reserves its place
+// in a bin with one global atomic per bin it touches and writes runs, not
+// single branches.  A bin holds up to kClusterCtas * kSliceCap branches.
+//
+// k_pair_cluster gives each bin to a cluster of kClusterCtas CTAs.  CTA r
+// pulls slice r of the bin into its shared memory with one TMA bulk copy per
+// array (cp.async.bulk, completion on an mbarrier), then every CTA inserts its
+// branches' pair classes into one open-addressing table spread over the
+// cluster's shared memory (distributed shared memory atomics), so a pair
+// whose members sit in different slices still meets.  Emission is as in
+// k_pair; the survivors of CTA r go to output segment (bin, r).
+// ---------------------------------------------------------------------------
+constexpr int kBinThreads = 512;
+constexpr int kBinILP = 8;
+constexpr int kBinTile = kBinThreads * kBinILP;  // 4096 branches
+constexpr int kClusterCtas = 8;
+constexpr int kSliceLog2 = 12;                   // 4096 branches per CTA
+constexpr int kSliceCap = 1 << kSliceLog2;
+constexpr int kBinLog2 = kSliceLog2 + 3;         // 32768 branches per bin
+constexpr int kSlotsPerCta = 2 * kSliceCap;      // hash slots per CTA
+constexpr int kPairCThreads = 512;
+
+template <int KW, class AT>
+struct BinSmem {
+  typename KT<KW>::T key[kBinTile];
+  AT amp[kBinTile];
+  uint16_t bin[kBinTile];
+  unsigned int hist[kMaxBins];
+  unsigned int off[kMaxBins];
+  unsigned int base[kMaxBins];
+  AT tab[kTabEntries];
+  DevOp ops[kMaxOps];
+  unsigned int scan[kBinThreads / 32];
+};
+
+template <int KW, class AT>
+__global__ void __launch_bounds__(kBinThreads)
+    k_bin(Ctl* ctl, Arr in, int in_slot, const __grid_constant__ OpList ops, Gate1 g, Arr bins,
+          uint32_t seq) {
+  typedef typename KT<KW>::T K;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BinSmem<KW, AT>& sm = *reinterpret_cast<BinSmem<KW, AT>*>(smem_raw);
+  if (ctl->err) return;
+  load_ops(ops, sm.ops, sm.tab);
+  const uint64_t n_dense = ctl->cnt[in_slot];
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, n_dense);
+  const K bmask = ((K)1) << g.t;
+  const uint32_t B = bins.n_seg;
+  const uint32_t cap = 1u << bins.seg_log2;
+  uint32_t per_seg = 1;
+  uint64_t units;
+  if (in.seg_cnt) {
+    per_seg = ((1u << in.seg_log2) + kBinTile - 1) / kBinTile;
+    units = (uint64_t)in.n_seg * per_seg;
+  } else {
+    units = (n_dense + kBinTile - 1) / kBinTile;
+  }
+  for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) sm.hist[b] = 0u;
+  __syncthreads();
+  for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    uint64_t base;
+    uint32_t lim;
+    if (in.seg_cnt) {
+      const uint32_t sg = (uint32_t)(u / per_seg);
+      const uint32_t o = (uint32_t)(u - (uint64_t)sg * per_seg) * kBinTile;
+      const uint32_t cnt = in.seg_cnt[sg];
+      lim = o >= cnt ? 0u : (cnt - o < (uint32_t)kBinTile ? cnt - o : (uint32_t)kBinTile);
+      base = ((uint64_t)sg << in.seg_log2) + o;
+    } else {
+      base = u * kBinTile;
+      lim = (uint32_t)(n_dense - base < (uint64_t)kBinTile ? n_dense - base : kBinTile);
+    }
+    if (lim == 0) continue;  // uniform across the CTA
+    // 1. Load, apply the run, bin, rank within the tile's bin.
+    K k[kBinILP];
+    AT v[kBinILP];
+    int bn[kBinILP];
+    unsigned int rk[kBinILP];
+#pragma unroll
+    for (int q = 0; q < kBinILP; ++q) {
+      const uint32_t j = q * blockDim.x + threadIdx.x;
+      bn[q] = -1;
+      if (j < lim) {
+        k[q] = ld_key<KW>(in, base + j);
+        v[q] = ((const AT*)in.amp)[base + j];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kBinILP; ++q) {
+      const uint32_t j = q * blockDim.x + threadIdx.x;
+      if (j < lim && apply_ops<KW, AT>(ops.n, sm.ops, sm.tab, k[q], v[q])) {
+        const uint64_t h = khash(k[q] & ~bmask);
+        bn[q] = (int)(((h >> 32) * (uint64_t)B) >> 32);
+        rk[q] = atomicAdd(&sm.hist[bn[q]], 1u);
+      }
+    }
+    __syncthreads();
+    // 2. Exclusive scan of the histogram (block-wide), global reservation.
+    const uint32_t per_t = (B + blockDim.x - 1) / blockDim.x;
+    const uint32_t b0 = threadIdx.x * per_t;
+    uint32_t local = 0;
+    for (uint32_t b = b0; b < b0 + per_t && b < B; ++b) local += sm.hist[b];
+    uint32_t incl = local;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) sm.scan[warp] = incl;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (uint32_t w = 0; w < warp; ++w) wpre += sm.scan[w];
+    uint32_t run = wpre + incl - local;
+    for (uint32_t b = b0; b < b0 + per_t && b < B; ++b) {
+      const uint32_t c = sm.hist[b];
+      sm.off[b] = run;
+      run += c;
+      sm.base[b] = c ? atomicAdd(&bins.seg_cnt[b], c) : 0u;
+    }
+    __syncthreads();
+    // 3. Stage the tile sorted by bin.
+#pragma unroll
+    for (int q = 0; q < kBinILP; ++q) {
+      if (bn[q] >= 0) {
+        const uint32_t at = sm.off[bn[q]] + rk[q];
+        sm.key[at] = k[q];
+        sm.amp[at] = v[q];
+        sm.bin[at] = (uint16_t)bn[q];
+      }
+    }
+    __syncthreads();
+    // 4. Coalesced write-out: consecutive threads, consecutive slots of a run.
+    const uint32_t total = sm.off[B - 1] + sm.hist[B - 1];
+    for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
+      const uint32_t b = sm.bin[i];
+      const uint32_t pos = sm.base[b] + (i - sm.off[b]);
+      if (pos < cap) {
+        const uint64_t j = ((uint64_t)b << bins.seg_log2) + pos;
+        st_key<KW>(bins, j, sm.key[i]);
+        ((AT*)bins.amp)[j] = sm.amp[i];
+      } else {
+        raise_err(ctl, kErrBucket, seq, (unsigned long long)pos + 1);
+      }
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) sm.hist[b] = 0u;
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+// Address of the same shared variable in CTA `rank` of the cluster (generic).
+template <class T>
+__device__ __forceinline__ T* map_rank(T* p, uint32_t rank) {
+  uint64_t out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"((uint64_t)p), "r"(rank));
+  return (T*)out;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+
+// Slot tag: (CTA rank << 12 | index) + 1; 0 marks an empty slot.
+__device__ __forceinline__ uint32_t ctag(uint32_t r, uint32_t i) { return ((r << kSliceLog2) | i) + 1u; }
+
+constexpr uint32_t kWaitLimit = 1u << 26;  // bounded mbarrier wait (try_wait loop)
+
+template <int KW, class AT>
+size_t pair_cluster_smem_bytes_t() {
+  typedef typename KT<KW>::T K;
+  return 128 + (size_t)kSliceCap * (sizeof(K) + sizeof(AT) + 4) + (size_t)kSlotsPerCta * 4 + 64;
+}
+
+template <int KW, class AT>
+__global__ void __launch_bounds__(kPairCThreads)
+    k_pair_cluster(Ctl* ctl, Gate1 g, Arr bins, Arr out, int out_slot, uint32_t seq) {
+  typedef typename KT<KW>::T K;
+  extern __shared__ __align__(128) unsigned char smem_pc[];
+  uint64_t* bar = (uint64_t*)smem_pc;
+  unsigned int* meta = (unsigned int*)(smem_pc + 16);  // [0] fill, [1] n_emit, [2] abort
+  K* skey = (K*)(smem_pc + 128);
+  AT* samp = (AT*)((unsigned char*)skey + (size_t)kSliceCap * sizeof(K));
+  int* partner = (int*)((unsigned char*)samp + (size_t)kSliceCap * sizeof(AT));
+  unsigned int* slot = (unsigned int*)((unsigned char*)partner + (size_t)kSliceCap * 4);
+
+  const uint32_t r = cluster_rank();
+  const uint32_t b = blockIdx.x / kClusterCtas;
+  // Every CTA of the cluster must reach every cluster barrier: an early exit
+  // is taken only after the last one.
+  const bool dead = ctl->err != 0u;
+  const uint32_t n_bin = dead ? 0u : bins.seg_cnt[b];
+  const uint32_t lo = r * kSliceCap;
+  const uint32_t n = n_bin > lo ? (n_bin - lo < (uint32_t)kSliceCap ? n_bin - lo : kSliceCap) : 0u;
+  const uint64_t src = ((uint64_t)b << bins.seg_log2) + lo;
+  if (threadIdx.x == 0) {
+    meta[0] = meta[1] = meta[2] = 0u;
+    if (b == 0 && r == 0 && !dead) ctl->cnt[(out_slot + 1) & 3] = 0;
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (uint32_t i = threadIdx.x; i < kSlotsPerCta; i += blockDim.x) slot[i] = 0u;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) partner[i] = -1;
+  __syncthreads();
+  // Slice r of the bin -> shared memory (both arrays start 16-byte aligned:
+  // slices begin at multiples of 4096 branches; sizes round up to 16 bytes
+  // inside the bin's capacity).
+  if (threadIdx.x == 0 && n > 0) {
+    const uint32_t kb = (uint32_t)(((size_t)n * 8 + 15) & ~(size_t)15);
+    const uint32_t ab = (uint32_t)(((size_t)n * sizeof(AT) + 15) & ~(size_t)15);
+    const uint32_t total = kb * (KW == 2 ? 2u : 1u) + ab;
+    mbar_expect_tx(bar, total);
+    if (KW == 1) {
+      bulk_g2s(skey, bins.k0 + src, kb, bar);
+    } else {
+      // Two-word keys are interleaved in shared memory: stage both words
+      // into the partner/slot area first would cost space; load them into
+      // skey as two halves and interleave below.
+      bulk_g2s(skey, bins.k0 + src, kb, bar);
+      bulk_g2s((unsigned char*)skey + (size_t)kSliceCap * 8, bins.k1 + src, kb, bar);
+    }
+    bulk_g2s(samp, (const AT*)bins.amp + src, ab, bar);
+  }
+  if (n > 0) {
+    uint32_t it = 0;
+    while (!mbar_try_wait(bar, 0) && ++it < kWaitLimit) {
+    }
+    if (it >= kWaitLimit && threadIdx.x == 0) {
+      raise_err(ctl, kErrProbe, seq, 0);
+      atomicOr(&meta[2], 1u);
+      // Let the copies land before the CTA leaves (bounded again).
+      uint32_t it2 = 0;
+      while (!mbar_try_wait(bar, 0) && ++it2 < kWaitLimit) {
+      }
+    }
+  }
+  __syncthreads();
+  if (KW == 2 && n > 0) {
+    // skey holds low words [0, n) and high words at byte offset 8 * kSliceCap:
+    // rebuild 128-bit keys in place from the top down (each slot i reads
+    // low[i] and high[i], which live at or above where key i lands only for
+    // i >= n / 2; a copy through registers in two passes keeps it safe).
+    uint64_t* w = (uint64_t*)skey;
+    uint64_t lo_w[kSliceCap / kPairCThreads], hi_w[kSliceCap / kPairCThreads];
+#pragma unroll
+    for (int q = 0; q < kSliceCap / kPairCThreads; ++q) {
+      const uint32_t i = q * blockDim.x + threadIdx.x;
+      lo_w[q] = i < n ? w[i] : 0ull;
+      hi_w[q] = i < n ? w[kSliceCap + i] : 0ull;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kSliceCap / kPairCThreads; ++q) {
+      const uint32_t i = q * blockDim.x + threadIdx.x;
+      if (i < n) skey[i] = mk<KW>(lo_w[q], hi_w[q]);
+    }
+  }
+  cluster_sync_all();  // every slot array of the cluster is cleared and loaded
+
+  const K bmask = ((K)1) << g.t;
+  const K cmask = mk<KW>(g.cmask[0], g.cmask[1]);
+  const K cval = mk<KW>(g.cval[0], g.cval[1]);
+  constexpr uint32_t kSlotsAll = kSlotsPerCta * kClusterCtas;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const K k = skey[i];
+    if ((k & cmask) != cval) continue;  // passes through unchanged
+    const K p = k & ~bmask;
+    uint32_t h = (uint32_t)khash(p) & (kSlotsAll - 1u);
+    const uint32_t me = ctag(r, i);
+    uint32_t probe = 0;
+    for (; probe < kSlotsAll; ++probe) {
+      unsigned int* s = map_rank(slot, h / kSlotsPerCta) + (h % kSlotsPerCta);
+      const unsigned int old = atomicCAS(s, 0u, me);
+      if (old == 0u) break;
+      const uint32_t orank = (old - 1u) >> kSliceLog2, oidx = (old - 1u) & (kSliceCap - 1u);
+      const K ok = *map_rank(skey + oidx, orank);
+      if ((ok & ~bmask) == p) {
+        partner[i] = (int)old;
+        *map_rank(partner + oidx, orank) = (int)me;
+        break;
+      }
+      h = (h + 1u) & (kSlotsAll - 1u);
+    }
+    if (probe == kSlotsAll) raise_err(ctl, kErrProbe, seq, 0);
+  }
+  cluster_sync_all();  // all pairs linked
+
+  // Emitters first (as in k_pair), then children, then warp-ballot appends
+  // into this CTA's output segment.
+  unsigned int* emit = slot;  // own slots are no longer read by anyone...
+  // ...only after every CTA has finished reading them: the barrier above.
+  const uint32_t lane = threadIdx.x & 31u;
+  const unsigned int lt = (1u << lane) - 1u;
+  const uint32_t rounds_in = (n + blockDim.x - 1u) / blockDim.x;
+  __syncthreads();
+  for (uint32_t rr = 0; rr < rounds_in; ++rr) {
+    const uint32_t i = rr * blockDim.x + threadIdx.x;
+    bool e = false;
+    if (i < n) {
+      const K k = skey[i];
+      e = (k & cmask) != cval || !((k & bmask) != (K)0 && partner[i] >= 0);
+    }
+    const unsigned int ball = __ballot_sync(0xffffffffu, e);
+    unsigned int wb = 0;
+    if (lane == 0 && ball) wb = atomicAdd(&meta[1], (unsigned int)__popc(ball));
+    wb = __shfl_sync(0xffffffffu, wb, 0);
+    if (e) emit[wb + __popc(ball & lt)] = i;
+  }
+  __syncthreads();
+  const uint32_t ne = meta[1];
+  const uint64_t oseg = (uint64_t)b * kClusterCtas + r;
+  const uint64_t obase = oseg << out.seg_log2;
+  const uint32_t rounds = (ne + blockDim.x - 1u) / blockDim.x;
+  for (uint32_t rr = 0; rr < rounds; ++rr) {
+    const uint32_t q = rr * blockDim.x + threadIdx.x;
+    bool keep0 = false, keep1 = false;
+    K k0 = 0, k1 = 0;
+    AT o0, o1;
+    if (q < ne) {
+      const uint32_t i = emit[q];
+      const K k = skey[i];
+      const AT ai = samp[i];
+      if ((k & cmask) != cval) {
+        keep0 = true;
+        k0 = k;
+        o0 = ai;
+      } else {
+        const bool kt = (k & bmask) != (K)0;
+        const int pj = partner[i];
+        k0 = k & ~bmask;
+        k1 = k | bmask;
+        AT aj = ai;
+        if (pj >= 0) {
+          const uint32_t orank = ((uint32_t)pj - 1u) >> kSliceLog2;
+          const uint32_t oidx = ((uint32_t)pj - 1u) & (kSliceCap - 1u);
+          aj = *map_rank(samp + oidx, orank);
+        }
+        const uint64_t av = g.mode == 1 ? get_field(k0, g.ang_off, g.ang_w) : 0ull;
+        if (!kt)
+          children<AT>(g, av, true, ai, pj >= 0, aj, o0, o1);
+        else
+          children<AT>(g, av, false, ai, true, ai, o0, o1);
+        keep0 = keep_amp(o0, g.eps, g.epsf, g.eps2);
+        keep1 = keep_amp(o1, g.eps, g.epsf, g.eps2);
+      }
+    }
+    const unsigned int b0 = __ballot_sync(0xffffffffu, keep0);
+    const unsigned int b1 = __ballot_sync(0xffffffffu, keep1);
+    const unsigned int tot = __popc(b0) + __popc(b1);
+    unsigned int wbase = 0;
+    if (lane == 0 && tot) wbase = atomicAdd(&meta[0], tot);
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    if (keep0) {
+      const uint64_t pos = obase + wbase + __popc(b0 & lt);
+      st_key<KW>(out, pos, k0);
+      ((AT*)out.amp)[pos] = o0;
+    }
+    if (keep1) {
+      const uint64_t pos = obase + wbase + __popc(b0) + __popc(b1 & lt);
+      st_key<KW>(out, pos, k1);
+      ((AT*)out.amp)[pos] = o1;
+    }
+  }
+  // Partners read this CTA's keys and amplitudes remotely until every CTA is
+  // past its emission: keep the shared memory alive until then.
+  cluster_sync_all();
+  if (threadIdx.x == 0) {
+    const unsigned int fill = meta[0];
+    if (!dead) {
+      out.seg_cnt[oseg] = fill;
+      if (fill) atomicAdd(&ctl->cnt[out_slot], (unsigned long long)fill);
+      if (r == 0) bins.seg_cnt[b] = 0u;  // bin counter clean for the next use
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 static int stream_grid(const Launch& L, int threads) {
@@ -897,6 +1311,80 @@ cudaError_t launch_from_f64(const Launch& L, Ctl* ctl, Arr a, const double* in, 
   (void)ctl;
   k_from_f64<<<stream_grid(L, 256), 256, 0, L.stream>>>((const double2*)in, n, (float2*)a.amp);
   return cudaGetLastError();
+}
+
+
+// ---- binned merge launchers -------------------------------------------------
+int cluster_bin_log2() { return kBinLog2; }
+int cluster_ctas() { return kClusterCtas; }
+int cluster_out_seg_log2() { return kSliceLog2 + 1; }
+
+template <int KW, class AT>
+static cudaError_t bin_t(const Launch& L, Ctl* ctl, Arr in, int in_slot, const OpList& ops,
+                         const Gate1& g, Arr bins) {
+  const size_t smem = sizeof(BinSmem<KW, AT>);
+  static unsigned long long configured = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !(configured & (1ull << dev))) {
+    cudaError_t e = cudaFuncSetAttribute(k_bin<KW, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured |= 1ull << dev;
+  }
+  uint64_t tiles = (L.n_hint + kBinTile - 1) / kBinTile;
+  if (tiles < 1) tiles = 1;
+  const uint64_t cap = (uint64_t)L.sm_count * 2;
+  const int grid = (int)(tiles < cap ? tiles : cap);
+  k_bin<KW, AT><<<grid, kBinThreads, smem, L.stream>>>(ctl, in, in_slot, ops, g, bins, L.seq);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
+                       const OpList& ops, const Gate1& g, Arr bins) {
+  if (bins.n_seg > (uint32_t)kMaxBins) return cudaErrorInvalidValue;
+  if (kw == 1)
+    return amp32 ? bin_t<1, float2>(L, ctl, in, in_slot, ops, g, bins)
+                 : bin_t<1, double2>(L, ctl, in, in_slot, ops, g, bins);
+  return amp32 ? bin_t<2, float2>(L, ctl, in, in_slot, ops, g, bins)
+               : bin_t<2, double2>(L, ctl, in, in_slot, ops, g, bins);
+}
+
+template <int KW, class AT>
+static cudaError_t pair_cluster_t(const Launch& L, Ctl* ctl, const Gate1& g, Arr bins, Arr out,
+                                  int out_slot) {
+  const size_t smem = pair_cluster_smem_bytes_t<KW, AT>();
+  static unsigned long long configured = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !(configured & (1ull << dev))) {
+    cudaError_t e = cudaFuncSetAttribute(k_pair_cluster<KW, AT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured |= 1ull << dev;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(bins.n_seg * kClusterCtas);
+  cfg.blockDim = dim3(kPairCThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = L.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_pair_cluster<KW, AT>, ctl, g, bins, out, out_slot, L.seq);
+}
+
+cudaError_t launch_pair_cluster(const Launch& L, int kw, bool amp32, Ctl* ctl, const Gate1& g,
+                                Arr bins, Arr out, int out_slot) {
+  if (kw == 1)
+    return amp32 ? pair_cluster_t<1, float2>(L, ctl, g, bins, out, out_slot)
+                 : pair_cluster_t<1, double2>(L, ctl, g, bins, out, out_slot);
+  return amp32 ? pair_cluster_t<2, float2>(L, ctl, g, bins, out, out_slot)
+               : pair_cluster_t<2, double2>(L, ctl, g, bins, out, out_slot);
 }
 
 }  // namespace sqs

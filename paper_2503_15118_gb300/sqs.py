@@ -18,7 +18,7 @@ from . import build as _build
 OK, ERR_ARG, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 AMP_FP64, AMP_FP32 = 0, 1
 SIZING_EXACT, SIZING_LEARNED = 0, 2
-MERGE_AUTO, MERGE_HASH, MERGE_SORT = 0, 4, 8
+MERGE_AUTO, MERGE_HASH, MERGE_SORT, MERGE_CLUSTER = 0, 4, 8, 16
 PERM_X, PERM_ADD_REG, PERM_SUB_REG, PERM_ADD_CONST, PERM_SUB_CONST, PERM_SWAP = range(6)
 MAX_CTRL = 8
 

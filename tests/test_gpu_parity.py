@@ -31,8 +31,8 @@ def sqs():
     return S
 
 
-def _pair(sqs, widths, lo, hi, amps, amp32=False, eps=1e-14):
-    g = sqs.State(widths, amp32=amp32, eps=eps)
+def _pair(sqs, widths, lo, hi, amps, amp32=False, eps=1e-14, merge=0):
+    g = sqs.State(widths, amp32=amp32, eps=eps, merge=merge)
     g.import_(lo, hi, amps)
     o = oracle.OracleState(widths, eps=eps)
     o.import_(lo, hi, amps)
@@ -70,23 +70,28 @@ GATES_64 = [
 ]
 
 
+MERGES = {"cluster": 16, "bucket": 0}
+
+
+@pytest.mark.parametrize("merge", ["cluster", "bucket"])
 @pytest.mark.parametrize("n", [1, 33, 2049, 70001])
 @pytest.mark.parametrize("gi", range(len(GATES_64)))
-def test_single_gate_64bit_keys(sqs, n, gi):
+def test_single_gate_64bit_keys(sqs, n, gi, merge):
     g = GATES_64[gi]
     target = (g[1], g[2]) if g[0] in ("h", "ry", "u1q", "ry_reg") else None
     lo, hi, amps = W.random_state(W64, n, seed=100 + n + gi, pair_fraction=0.5, target=target)
-    gs, os_ = _pair(sqs, W64, lo, hi, amps)
+    gs, os_ = _pair(sqs, W64, lo, hi, amps, merge=MERGES[merge])
     gs.apply(g)
     os_.apply(g)
     _check(gs, os_)
 
 
+@pytest.mark.parametrize("merge", ["cluster", "bucket"])
 @pytest.mark.parametrize("pair_fraction", [0.0, 1.0])
-@pytest.mark.parametrize("n", [5, 4096, 30000])
-def test_h_pairing_extremes(sqs, n, pair_fraction):
+@pytest.mark.parametrize("n", [5, 4096, 30000, 300000])
+def test_h_pairing_extremes(sqs, n, pair_fraction, merge):
     lo, hi, amps = W.random_state(W64, n, seed=7 * n, pair_fraction=pair_fraction, target=(1, 6))
-    gs, os_ = _pair(sqs, W64, lo, hi, amps)
+    gs, os_ = _pair(sqs, W64, lo, hi, amps, merge=MERGES[merge])
     gs.h_gate(1, 6)
     os_.h_gate(1, 6)
     _check(gs, os_)
@@ -107,16 +112,17 @@ GATES_128 = [
 ]
 
 
+@pytest.mark.parametrize("merge", ["cluster", "bucket"])
 @pytest.mark.parametrize("amp32", [False, True])
 @pytest.mark.parametrize("n", [3, 2049, 40000])
 @pytest.mark.parametrize("gi", range(len(GATES_128)))
-def test_single_gate_128bit_keys(sqs, n, gi, amp32):
+def test_single_gate_128bit_keys(sqs, n, gi, amp32, merge):
     g = GATES_128[gi]
     target = (g[1], g[2]) if g[0] in ("h", "ry", "u1q", "ry_reg") else None
     lo, hi, amps = W.random_state(W128, n, seed=300 + n + gi, pair_fraction=0.5, target=target)
     if amp32:
         amps = amps.astype(np.complex64).astype(np.complex128)  # representable input
-    gs, os_ = _pair(sqs, W128, lo, hi, amps, amp32=amp32)
+    gs, os_ = _pair(sqs, W128, lo, hi, amps, amp32=amp32, merge=MERGES[merge])
     gs.apply(g)
     os_.apply(g)
     _check(gs, os_, amp32=amp32)
@@ -189,11 +195,12 @@ def test_config1_fp32(sqs):
     assert compare_states(g.to_dict(), o.to_dict(), atol=1e-5, band=1e-5) >= 1 - 1e-6
 
 
-def test_config2_reduced(sqs):
+@pytest.mark.parametrize("merge", ["cluster", "bucket"])
+def test_config2_reduced(sqs, merge):
     circ = W.config2(seed=2, n_branch=16, n_perm=300, n_cancel=6)
     n_main = len(circ["gates"]) - 6
     o = oracle.run_circuit(circ, upto=n_main)
-    g = sqs.run_circuit(circ, upto=n_main)
+    g = sqs.run_circuit(circ, upto=n_main, merge=MERGES[merge])
     assert g.nnz() == o.nnz() == 2 ** 16
     _check(g, o)
     for i, gate in enumerate(circ["gates"][n_main:]):

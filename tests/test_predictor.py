@@ -89,7 +89,7 @@ def test_overflow_falls_back_to_exact(S):
     w = np.zeros(S.PRED_PARAMS, np.float32)
     w[-1] = -8.0
     bad.set_params(w)
-    c = W.config2(seed=3, n_branch=15, n_perm=200, n_cancel=4)
+    c = W.config2(seed=3, n_branch=17, n_perm=200, n_cancel=4)
     o = oracle.run_circuit(c)
     g = S.State(c["widths"], learned=True)
     g.set_predictor(bad)
