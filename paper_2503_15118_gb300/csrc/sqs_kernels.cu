@@ -483,6 +483,17 @@ struct Coef<float2> {
   __device__ static float r(const Gate1& g, int e) { return g.uf[2 * e]; }
 };
 
+// FP32 storage: a two-term sum that lands below the rounding noise of its
+// terms (2^-21 of their size, a few units in the last place) is a
+// cancellation that FP64 arithmetic would have made (near) exact; it is
+// flushed to zero so that the pruning step removes it.  FP64 states keep
+// their results as computed.
+__device__ __forceinline__ void flush_residue(double2&, double2, double2) {}
+__device__ __forceinline__ void flush_residue(float2& o, float2 a0, float2 a1) {
+  const float size = fabsf(a0.x) + fabsf(a0.y) + fabsf(a1.x) + fabsf(a1.y);
+  if (fabsf(o.x) + fabsf(o.y) <= size * 4.76837158e-7f) o = make_float2(0.f, 0.f);
+}
+
 template <class AT>
 __device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, bool has0, AT a0,
                                          bool has1, AT a1, AT& o0, AT& o1) {
@@ -505,6 +516,8 @@ __device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, b
       const AT p11 = same1 ? (neg1 ? cneg(p01) : p01) : rmul(u11, a1);
       o0 = rfma(u00, a0, p01);
       o1 = rfma(u10, a0, p11);
+      flush_residue(o0, a0, a1);
+      flush_residue(o1, a0, a1);
     } else if (has0) {
       o0 = rmul(u00, a0);
       o1 = same0 ? (neg0 ? cneg(o0) : o0) : rmul(u10, a0);
@@ -520,6 +533,8 @@ __device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, b
       const AT p11 = same1 ? (neg1 ? cneg(p01) : p01) : cmul(U11, a1);
       o0 = cfma(U00, a0, p01);
       o1 = cfma(U10, a0, p11);
+      flush_residue(o0, a0, a1);
+      flush_residue(o1, a0, a1);
     } else if (has0) {
       o0 = cmul(U00, a0);
       o1 = same0 ? (neg0 ? cneg(o0) : o0) : cmul(U10, a0);

@@ -298,8 +298,11 @@ def random_state(widths, n, seed, pair_fraction=0.5, target=None):
                 hi &= ~np.uint64(1 << (bpos - 64))
         lo = np.concatenate([base_lo, lo])
         hi = np.concatenate([base_hi, hi])
-        both = np.stack([hi, lo], axis=1)
-        _, first = np.unique(both, axis=0, return_index=True)
+        if words == 1:
+            _, first = np.unique(lo, return_index=True)
+        else:
+            both = np.stack([hi, lo], axis=1)
+            _, first = np.unique(both, axis=0, return_index=True)
         first = np.sort(first)
         base_lo, base_hi = lo[first], hi[first]
     base_lo, base_hi = base_lo[:n_base], base_hi[:n_base]
