@@ -243,6 +243,9 @@ uint64_t sqs_launch_count(const sqs_state* st);
 #define SQS_K_PAIR 4u       /* pair, 2x2, prune, compact (one CTA / bucket) */
 #define SQS_K_PROB 5u       /* probabilities / norm                         */
 #define SQS_K_CONVERT 6u    /* FP32 <-> FP64 staging for export / import    */
+#define SQS_K_EXPAND 7u     /* constant target bit: children without merge  */
+#define SQS_K_BIN 8u        /* cluster merge: coarse binning                */
+#define SQS_K_PAIR_CLUSTER 9u /* cluster merge: pairing in a thread-block cluster */
 typedef struct {
   uint32_t kernel; /* SQS_K_*                          */
   uint32_t call;   /* API call index since enabling     */

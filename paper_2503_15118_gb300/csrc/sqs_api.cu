@@ -449,6 +449,47 @@ sqs_status run_pending(sqs_state* st, bool keep_tail) {
   return SQS_OK;
 }
 
+sqs_status densify(sqs_state* st);
+
+// One interference step whose target bit is constant over the state: no
+// pair exists, so k_expand writes both children of every controlled branch
+// in one pass (the constant-bit path of the merge).
+sqs_status run_expand(sqs_state* st, const Gate1& g, int64_t rec_idx) {
+  const OpList& L = st->ops_buf;
+  constexpr uint32_t kChunkLog2 = 12;  // chunk of input slots per output segment
+  // Expansion doubles the slots of the layout; a sparse segmented state is
+  // packed densely first so that slots track branches, not capacity.
+  if (st->cur.segmented && st->cur.slots(st->ub) > 4 * std::max<uint64_t>(st->ub, 4096)) {
+    sqs_status s = densify(st);
+    if (s != SQS_OK) return st->sticky = s;
+  }
+  const uint64_t in_slots = st->cur.slots(st->ub);
+  const uint64_t nseg = std::max<uint64_t>(1, (in_slots + (1ull << kChunkLog2) - 1) >> kChunkLog2);
+  if (nseg > 0xffffffffull) return st->sticky = fail(st, SQS_ERR_CAPACITY, "state too large");
+  const uint64_t need = nseg << (kChunkLog2 + 1);
+  if (st->alt.cap < need && !ensure_store(st, st->alt, need))
+    return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate %llu branches",
+                             (unsigned long long)need);
+  st->alt.set_segments(kChunkLog2 + 1, (uint32_t)nseg);
+  const int out_slot = (st->cur_slot + 1) & 3;
+  cudaError_t e;
+  {
+    Traced tr(st, SQS_K_EXPAND);
+    e = sqs::launch_expand(launch_of(st, in_slots), st->kw, st->amp32, st->ctl, st->cur.view(),
+                           st->cur_slot, L, g, st->alt.view(), out_slot);
+  }
+  if (e != cudaSuccess) return cuda_fail(st, e, "expand launch");
+  if (rec_idx >= 0) {
+    e = sqs::launch_record(launch_of(st, 1), st->ctl, st->cur_slot, out_slot,
+                           st->rec_dev + 2 * (size_t)rec_idx);
+    if (e != cudaSuccess) return cuda_fail(st, e, "record launch");
+  }
+  std::swap(st->cur, st->alt);
+  st->cur_slot = out_slot;
+  st->ub = std::min(max_branches(st), 2 * st->ub);
+  return SQS_OK;
+}
+
 // One interference step on the binned cluster path: k_bin then
 // k_pair_cluster.  The fused run is already packed in st->ops_buf.
 sqs_status run_binned(sqs_state* st, const Gate1& g, uint64_t B1, int64_t rec_idx) {
@@ -470,13 +511,13 @@ sqs_status run_binned(sqs_state* st, const Gate1& g, uint64_t B1, int64_t rec_id
   const int out_slot = (st->cur_slot + 1) & 3;
   cudaError_t e;
   {
-    Traced tr(st, SQS_K_PARTITION);
+    Traced tr(st, SQS_K_BIN);
     e = sqs::launch_bin(launch_of(st, in_slots), st->kw, st->amp32, st->ctl, st->cur.view(),
                         st->cur_slot, L, g, st->bk.view());
   }
   if (e != cudaSuccess) return cuda_fail(st, e, "bin launch");
   {
-    Traced tr(st, SQS_K_PAIR);
+    Traced tr(st, SQS_K_PAIR_CLUSTER);
     e = sqs::launch_pair_cluster(launch_of(st, in_slots), st->kw, st->amp32, st->ctl, g,
                                  st->bk.view(), st->alt.view(), out_slot);
   }
@@ -500,6 +541,7 @@ sqs_status run_branching(sqs_state* st, const Gate1& g, double est_in = -1.0,
   sqs_status s = run_pending(st, true);  // leaves the fused tail in ops_buf
   if (s != SQS_OK) return st->sticky = s;
   const OpList& L = st->ops_buf;
+  if (g.no_partners) return run_expand(st, g, rec_idx);
   const uint64_t C = 1ull << kBucketLog2;
   const uint64_t target = C * 3 / 4;  // mean bucket fill: overflow is ~18 sigma away
   uint64_t want =
@@ -693,9 +735,12 @@ void note_branch(sqs_state* st, const Gate1& g) {
 }
 
 // Queues (learned mode) or runs (exact mode) one interference step.
-sqs_status issue_branching(sqs_state* st, const Gate1& g, uint32_t n_ctrl) {
+sqs_status issue_branching(sqs_state* st, const Gate1& g_in, uint32_t n_ctrl) {
   float x[SQS_PRED_FEATURES];
+  Gate1 g = g_in;
   features(st, g, n_ctrl, x);
+  // A target bit known constant over the whole state has no partner anywhere.
+  g.no_partners = (st->const_val[g.t] >= 0) ? 1u : 0u;
   note_branch(st, g);
   if ((st->flags & SQS_SIZING_LEARNED) && st->predictor) {
     sqs_state::Lazy q;

@@ -108,6 +108,7 @@ struct Gate1 {            // the interference operation of one merge step
   double scale, offset;        // mode 1: theta = scale * value + offset
   double eps, eps2;       // pruning threshold and its square (|a| < eps removes)
   float epsf;             // eps rounded to FP32
+  uint32_t no_partners;   // the target bit is constant over the state: expand only
 };
 
 struct Launch {
@@ -135,6 +136,11 @@ cudaError_t launch_partition(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr 
 // bucket counters.
 cudaError_t launch_pair(const Launch& L, int kw, bool amp32, Ctl* ctl, const Gate1& g, Arr bk,
                         Arr out, int out_slot);
+// Interference step whose target bit is constant over the state (no pair can
+// exist): the fused run, then both children of every controlled branch, into
+// output segment c for input chunk c (segments twice the chunk size).
+cudaError_t launch_expand(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
+                          const OpList& ops, const Gate1& g, Arr out, int out_slot);
 cudaError_t launch_probabilities(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr a, int slot,
                                  uint32_t off, uint32_t w, double* probs, double* norm2);
 // Copies a segmented array into a dense one given exclusive segment offsets.

@@ -686,6 +686,102 @@ __global__ void __launch_bounds__(kPairThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Constant target bit: no branch has a partner, so each controlled branch
+// expands into its two children directly (no partition, no pairing).  The
+// input is walked in chunks of kExpandChunk slots (a dense range, or a slice
+// of one segment); chunk c becomes output segment c, of twice the size.
+constexpr uint32_t kExpandChunkLog2 = 12;
+
+template <int KW, class AT>
+__global__ void __launch_bounds__(kStreamThreads)
+    k_expand(Ctl* ctl, Arr in, int in_slot, Arr out, int out_slot,
+             const __grid_constant__ OpList ops, Gate1 g, uint32_t seq) {
+  typedef typename KT<KW>::T K;
+  __shared__ AT tab[kTabEntries];
+  __shared__ DevOp sops[kMaxOps];
+  __shared__ unsigned int seg_fill;
+  if (ctl->err) return;
+  load_ops(ops, sops, tab);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->cnt[(out_slot + 1) & 3] = 0;
+    atomicMax(&ctl->peak, ctl->cnt[in_slot]);
+  }
+  const uint64_t n_dense = ctl->cnt[in_slot];
+  const uint64_t chunk = 1ull << kExpandChunkLog2;
+  // Chunks per input segment (segments are at least one chunk long).
+  const uint32_t cps_log2 = in.seg_cnt ? in.seg_log2 - kExpandChunkLog2 : 0u;
+  const K bmask = ((K)1) << g.t;
+  const K cmask = mk<KW>(g.cmask[0], g.cmask[1]);
+  const K cval = mk<KW>(g.cval[0], g.cval[1]);
+  const unsigned int lane = threadIdx.x & 31u;
+  const unsigned int lt = (1u << lane) - 1u;
+  for (uint64_t c = blockIdx.x; c < out.n_seg; c += gridDim.x) {
+    if (threadIdx.x == 0) seg_fill = 0;
+    __syncthreads();
+    uint64_t ibase, cnt;
+    if (in.seg_cnt) {
+      const uint64_t sg = c >> cps_log2;
+      const uint64_t off = (c & ((1ull << cps_log2) - 1ull)) << kExpandChunkLog2;
+      const uint64_t n_sg = sg < in.n_seg ? in.seg_cnt[sg] : 0;
+      ibase = (sg << in.seg_log2) + off;
+      cnt = n_sg > off ? (n_sg - off < chunk ? n_sg - off : chunk) : 0;
+    } else {
+      ibase = c << kExpandChunkLog2;
+      cnt = ibase >= n_dense ? 0 : (n_dense - ibase < chunk ? n_dense - ibase : chunk);
+    }
+    const uint64_t obase = c << out.seg_log2;
+    for (uint64_t r = 0; r < cnt; r += blockDim.x) {
+      bool keep0 = false, keep1 = false;
+      K k0 = 0, k1 = 0;
+      AT o0, o1;
+      if (r + threadIdx.x < cnt) {
+        K k = ld_key<KW>(in, ibase + r + threadIdx.x);
+        AT v = ((const AT*)in.amp)[ibase + r + threadIdx.x];
+        if (apply_ops<KW, AT>(ops.n, sops, tab, k, v)) {
+          if ((k & cmask) != cval) {
+            keep0 = true;
+            k0 = k;
+            o0 = v;
+          } else {
+            const bool kt = (k & bmask) != (K)0;
+            k0 = k & ~bmask;
+            k1 = k | bmask;
+            const uint64_t av = g.mode == 1 ? get_field(k0, g.ang_off, g.ang_w) : 0ull;
+            if (!kt)
+              children<AT>(g, av, true, v, false, v, o0, o1);
+            else
+              children<AT>(g, av, false, v, true, v, o0, o1);
+            keep0 = keep_amp(o0, g.eps, g.epsf, g.eps2);
+            keep1 = keep_amp(o1, g.eps, g.epsf, g.eps2);
+          }
+        }
+      }
+      const unsigned int b0 = __ballot_sync(0xffffffffu, keep0);
+      const unsigned int b1 = __ballot_sync(0xffffffffu, keep1);
+      const unsigned int tot = __popc(b0) + __popc(b1);
+      unsigned int wbase = 0;
+      if (lane == 0 && tot) wbase = atomicAdd(&seg_fill, tot);
+      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      if (keep0) {
+        const uint64_t pos = obase + wbase + __popc(b0 & lt);
+        st_key<KW>(out, pos, k0);
+        ((AT*)out.amp)[pos] = o0;
+      }
+      if (keep1) {
+        const uint64_t pos = obase + wbase + __popc(b0) + __popc(b1 & lt);
+        st_key<KW>(out, pos, k1);
+        ((AT*)out.amp)[pos] = o1;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      out.seg_cnt[c] = seg_fill;
+      if (seg_fill) atomicAdd(&ctl->cnt[out_slot], (unsigned long long)seg_fill);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 constexpr int kProbThreads = 256;
 constexpr uint32_t kSmemBinsLog2 = 11;
 
@@ -1232,6 +1328,18 @@ cudaError_t launch_apply_compact(const Launch& L, int kw, bool amp32, Ctl* ctl, 
                                                 L.seq)
   SQS_DISPATCH(kw, amp32, SQS_AC);
 #undef SQS_AC
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
+                          const OpList& ops, const Gate1& g, Arr out, int out_slot) {
+  uint64_t grid = out.n_seg < 1 ? 1 : out.n_seg;
+  if (grid > (uint64_t)L.sm_count * 8) grid = (uint64_t)L.sm_count * 8;
+#define SQS_EX(KW_, AT_)                                                                 \
+  k_expand<KW_, AT_><<<(int)grid, kStreamThreads, 0, L.stream>>>(ctl, in, in_slot, out, \
+                                                                 out_slot, ops, g, L.seq)
+  SQS_DISPATCH(kw, amp32, SQS_EX);
+#undef SQS_EX
   return cudaGetLastError();
 }
 

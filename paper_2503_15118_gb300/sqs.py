@@ -54,7 +54,8 @@ class TraceRecord(ctypes.Structure):
 
 
 KERNEL_NAMES = {0: "k_init", 1: "k_apply_inplace", 2: "k_apply_compact", 3: "k_partition",
-                4: "k_pair", 5: "k_probabilities", 6: "k_convert"}
+                4: "k_pair", 5: "k_probabilities", 6: "k_convert", 7: "k_expand", 8: "k_bin",
+                9: "k_pair_cluster"}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)

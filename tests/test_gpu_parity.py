@@ -330,3 +330,32 @@ def test_long_fused_runs(sqs, then_branch):
         os_.apply(g)
     _check(gs, os_)
     assert rng is not None
+
+
+@pytest.mark.parametrize("merge", ["cluster", "bucket"])
+def test_constant_target_expand_path(sqs, merge):
+    """Targets whose bit the runtime can prove constant (never touched, or
+    flipped by X / CNOT whose controls are themselves constant) take the
+    expand-only path; targets made non-constant by a superposed control take
+    the merge.  Both must match the oracle."""
+    widths = [6, 6, 4]
+    gates = [
+        ("h", 0, 0, ()), ("h", 0, 1, ()),                  # fresh bits: constant
+        ("x", 1, 0, ()), ("h", 1, 0, ()),                  # constant after X (value 1)
+        ("x", 1, 1, ((1, 2, 1),)), ("h", 1, 1, ()),        # control constant 0: unchanged
+        ("x", 2, 0, ((0, 0, 1),)), ("h", 2, 0, ()),        # control superposed: merge path
+        ("h", 0, 0, ()),                                   # re-applied H: pairs, merge path
+        ("add", 2, 0, 0, ()), ("h", 2, 3, ()),             # arithmetic destination: merge
+        ("ry", 1, 5, 0.7, ((0, 1, 1),)),                   # controlled, constant target
+    ]
+    circ = {"widths": widths, "eps": 1e-14, "tables": [], "gates": gates}
+    o = oracle.run_circuit(circ)
+    g = sqs.State(widths, merge=MERGES[merge])
+    g.trace_enable(4096)
+    g.run(circ)
+    recs, _ = g.trace_read()
+    names = [r[0] for r in recs]
+    assert names.count("k_expand") == 5
+    got, ref = g.to_dict(), o.to_dict()
+    assert compare_states(got, ref) > 1 - 1e-12
+    assert set(got) == set(ref)
