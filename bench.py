@@ -48,7 +48,7 @@ L2_FLUSH_BYTES = 512 << 20
 def kernel_source_sha():
     import hashlib
     h = hashlib.sha256()
-    for f in ("sqs_kernels.cu", "sqs_internal.h"):
+    for f in ("sqs_kernels.cu", "sqs_device.cuh", "sqs_sort.cu", "sqs_internal.h"):
         with open(os.path.join(ROOT, "paper_2503_15118_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -59,8 +59,21 @@ typedef enum {
                                      the operation re-run at the exact size     */
 #define SQS_MERGE_AUTO 0u         /* default merge path (per-CTA buckets)       */
 #define SQS_MERGE_HASH 4u         /* force the per-CTA bucket merge             */
-#define SQS_MERGE_SORT 8u         /* force the radix-sort merge                 */
+#define SQS_MERGE_SORT 8u         /* force the radix-sort merge: LSD passes of
+                                     8-bit digits over the pair-class key (the
+                                     key without the target bit), windows
+                                     skipping bits known constant, then one
+                                     pass combining neighbours; states of 2^32
+                                     or more branches use the bucket merge    */
 #define SQS_MERGE_CLUSTER 16u     /* force the cluster (binned) merge           */
+#define SQS_MERGE_TUNED 32u       /* measured choice per step: the first steps
+                                     of each size class (log2 of the count
+                                     bound, sort pass count) time the bucket
+                                     and the sort merge with CUDA events; later
+                                     steps of the class take the faster one.
+                                     Both give bit-identical states.  A step
+                                     whose target bit is known constant always
+                                     takes the expansion path (no merge).     */
 
 /*
  * One control (or predicate) qubit: bit `bit` of register `reg` must equal
@@ -246,6 +259,8 @@ uint64_t sqs_launch_count(const sqs_state* st);
 #define SQS_K_EXPAND 7u     /* constant target bit: children without merge  */
 #define SQS_K_BIN 8u        /* cluster merge: coarse binning                */
 #define SQS_K_PAIR_CLUSTER 9u /* cluster merge: pairing in a thread-block cluster */
+#define SQS_K_SORT 10u      /* radix-sort merge: one LSD pass (histogram, scan, scatter) */
+#define SQS_K_SORT_MERGE 11u /* radix-sort merge: neighbours combined, 2x2, prune */
 typedef struct {
   uint32_t kernel; /* SQS_K_*                          */
   uint32_t call;   /* API call index since enabling     */
@@ -316,6 +331,10 @@ typedef struct {
   uint64_t learned_steps;    /* steps sized from a prediction                  */
   uint64_t bytes_live;       /* device bytes currently held by the state       */
   uint64_t bytes_peak;       /* largest bytes_live since creation              */
+  uint64_t steps_expand;     /* interference steps by path: constant target   */
+  uint64_t steps_hash;       /*   per-CTA bucket merge                         */
+  uint64_t steps_sort;       /*   radix-sort merge                             */
+  uint64_t steps_cluster;    /*   binned cluster merge                         */
 } sqs_stats;
 sqs_status sqs_state_stats(const sqs_state* st, sqs_stats* out);
 

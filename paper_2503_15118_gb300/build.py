@@ -38,7 +38,7 @@ def sources():
 
 
 def _newest_input():
-    files = sources() + glob.glob(os.path.join(CSRC, "*.h")) + \
+    files = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         [os.path.join(ROOT, "include", "sqs.h"), os.path.abspath(__file__)]
     return max(os.path.getmtime(f) for f in files)
 

@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -147,6 +148,18 @@ struct sqs_state {
   bool defer_frees = false;
   std::vector<void*> graveyard;
   uint64_t grow_hint_b = 0;  // learned mode: buckets at the predicted peak (growth target)
+
+  // Radix-sort merge scratch: digit histograms, scan partials, count.
+  unsigned char* sort_buf = nullptr;
+  size_t sort_bytes = 0;
+  // Measured merge choice (SQS_MERGE_TUNED), per size class.
+  struct Tune {
+    float us_per_slot[2] = {-1.f, -1.f};  // bucket merge, sort merge
+    int pending = -1;                     // path whose events are in flight
+    uint64_t slots = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+  };
+  std::map<uint32_t, Tune> tune;
 
   sqs_stats stats{};
   std::unordered_map<void*, size_t> sizes;
@@ -402,12 +415,18 @@ sqs_status run_list(sqs_state* st, const OpList& L) {
   cudaError_t e = cudaSuccess;
   const uint64_t in_slots = st->cur.slots(st->ub);
   if (L.drops) {
-    const uint64_t chunks = std::max<uint64_t>(1, (in_slots + (1ull << kSegLog2) - 1) >> kSegLog2);
+    // Output segment c holds what survives of input segment c (segmented
+    // input, segments of any size) or of dense chunk c.
+    const uint32_t seg_log2 =
+        st->cur.segmented ? std::max<uint32_t>(kSegLog2, st->cur.seg_log2) : kSegLog2;
+    const uint64_t chunks =
+        st->cur.segmented ? std::max<uint64_t>(1, st->cur.n_seg)
+                          : std::max<uint64_t>(1, (in_slots + (1ull << kSegLog2) - 1) >> kSegLog2);
     if (chunks > 0xffffffffull) return st->sticky = fail(st, SQS_ERR_CAPACITY, "state too large");
-    if (!ensure_store(st, st->alt, chunks << kSegLog2))
+    if (!ensure_store(st, st->alt, chunks << seg_log2))
       return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate %llu branches",
-                               (unsigned long long)(chunks << kSegLog2));
-    st->alt.set_segments(kSegLog2, (uint32_t)chunks);
+                               (unsigned long long)(chunks << seg_log2));
+    st->alt.set_segments(seg_log2, (uint32_t)chunks);
     const int out_slot = (st->cur_slot + 1) & 3;
     {
       Traced tr(st, SQS_K_COMPACT);
@@ -536,12 +555,12 @@ sqs_status run_binned(sqs_state* st, const Gate1& g, uint64_t B1, int64_t rec_id
 // One interference step: fused pending run + partition + pair.  est_in < 0:
 // buckets sized from the hard bound st->ub (exact mode); otherwise from the
 // predicted input count est_in with a 20% margin (learned mode).
-sqs_status run_branching(sqs_state* st, const Gate1& g, double est_in = -1.0,
-                         int64_t rec_idx = -1) {
-  sqs_status s = run_pending(st, true);  // leaves the fused tail in ops_buf
-  if (s != SQS_OK) return st->sticky = s;
+// One interference step on the per-CTA bucket merge (k_partition, k_pair),
+// or on the binned cluster merge when requested.  The fused run is already
+// packed in st->ops_buf.
+sqs_status run_hashed(sqs_state* st, const Gate1& g, double est_in, int64_t rec_idx) {
+  sqs_status s;
   const OpList& L = st->ops_buf;
-  if (g.no_partners) return run_expand(st, g, rec_idx);
   const uint64_t C = 1ull << kBucketLog2;
   const uint64_t target = C * 3 / 4;  // mean bucket fill: overflow is ~18 sigma away
   uint64_t want =
@@ -567,8 +586,11 @@ sqs_status run_branching(sqs_state* st, const Gate1& g, double est_in = -1.0,
     need = plan(want, B, B1);
   }
   if (B > 0x7fffffffull) return st->sticky = fail(st, SQS_ERR_CAPACITY, "too many buckets");
-  if ((st->flags & SQS_MERGE_CLUSTER) && B1 <= (uint64_t)sqs::kMaxBins)
+  if ((st->flags & SQS_MERGE_CLUSTER) && B1 <= (uint64_t)sqs::kMaxBins) {
+    st->stats.steps_cluster++;
     return run_binned(st, g, B1, rec_idx);
+  }
+  st->stats.steps_hash++;
   // Learned mode grows buffers straight to the predicted peak (grow_hint_b).
   const uint64_t Bcap = std::max(B, st->grow_hint_b);
   if ((st->bk.cap < (B << kBucketLog2) && !ensure_store(st, st->bk, Bcap << kBucketLog2)) ||
@@ -602,6 +624,181 @@ sqs_status run_branching(sqs_state* st, const Gate1& g, double est_in = -1.0,
   st->cur_slot = out_slot;
   st->ub = std::min(max_branches(st), 2 * st->ub);
   return SQS_OK;
+}
+
+// Digit windows of the radix-sort merge: start positions (in the pair-class
+// key, the key with bit t deleted) of 8-bit digits covering every bit not
+// known constant.  Known-constant bits order nothing and are skipped.
+std::vector<uint32_t> sort_shifts(const sqs_state* st, const Gate1& g) {
+  const uint32_t nb = st->total_bits;  // the class key has nb - 1 bits
+  const uint32_t D = (uint32_t)sqs::sort_radix_bits();
+  auto varying = [&](uint32_t q) {  // bit q of the class key
+    const uint32_t kb = q < g.t ? q : q + 1;
+    return ((g.vary[kb >> 6] >> (kb & 63)) & 1ull) != 0ull;
+  };
+  std::vector<uint32_t> shifts;
+  for (uint32_t q = 0; q + 1 < nb;) {
+    if (!varying(q)) {
+      ++q;
+      continue;
+    }
+    shifts.push_back(q);
+    q += D;
+  }
+  if (shifts.empty()) shifts.push_back(0);  // one pass still applies the fused run
+  return shifts;
+}
+
+// One interference step on the radix-sort merge: LSD passes ping-pong
+// between the two scratch stores so that the sorted array always ends in
+// st->bk, whose segment counters stay untouched (zero) for the bucket merge;
+// the merge writes st->alt, which becomes the state.
+sqs_status run_sorted(sqs_state* st, const Gate1& g, int64_t rec_idx) {
+  const OpList& L = st->ops_buf;
+  const std::vector<uint32_t> shifts = sort_shifts(st, g);
+  const uint32_t npass = (uint32_t)shifts.size();
+  const uint64_t tile = (uint64_t)sqs::sort_tile();
+  const uint64_t in_slots = st->cur.slots(st->ub);
+  uint32_t per_seg = 1;
+  uint64_t tiles0;
+  if (st->cur.segmented) {
+    per_seg = (uint32_t)std::max<uint64_t>(1, ((1ull << st->cur.seg_log2) + tile - 1) / tile);
+    tiles0 = std::max<uint64_t>(1, (uint64_t)st->cur.n_seg * per_seg);
+  } else {
+    tiles0 = std::max<uint64_t>(1, (st->ub + tile - 1) / tile);
+  }
+  const uint64_t tilesN = std::max<uint64_t>(1, (st->ub + tile - 1) / tile);
+  const uint64_t radix = 1ull << sqs::sort_radix_bits();
+  const size_t hist_bytes = (size_t)(radix * std::max(tiles0, tilesN) * 4 + 255) & ~(size_t)255;
+  const size_t part_bytes = (sqs::sort_part_entries() * 4 + 255) & ~(size_t)255;
+  const size_t bytes = hist_bytes + part_bytes + 256;
+  if (st->sort_bytes < bytes) {
+    dfree(st, st->sort_buf);
+    st->sort_buf = (unsigned char*)dalloc(st, bytes);
+    st->sort_bytes = st->sort_buf ? bytes : 0;
+    if (!st->sort_buf) return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate sort scratch");
+  }
+  unsigned int* hist = (unsigned int*)st->sort_buf;
+  unsigned int* part = (unsigned int*)(st->sort_buf + hist_bytes);
+  unsigned long long* n_dev = (unsigned long long*)(st->sort_buf + hist_bytes + part_bytes);
+  const uint32_t chunk_log2 = sqs::sort_merge_chunk_log2();
+  const uint64_t nseg_out = std::max<uint64_t>(1, (st->ub + (1ull << chunk_log2) - 1) >> chunk_log2);
+  if (nseg_out > 0xffffffffull) return st->sticky = fail(st, SQS_ERR_CAPACITY, "state too large");
+  const uint64_t out_need = nseg_out << (chunk_log2 + 1);
+  if ((st->bk.cap < st->ub && !ensure_store(st, st->bk, st->ub)) ||
+      (st->alt.cap < std::max(out_need, st->ub) &&
+       !ensure_store(st, st->alt, std::max(out_need, st->ub))))
+    return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate %llu branches",
+                             (unsigned long long)out_need);
+  // Pass p writes buf[p & 1]; the last pass lands in bk.
+  Store* buf[2];
+  buf[0] = (npass & 1) ? &st->bk : &st->alt;
+  buf[1] = (npass & 1) ? &st->alt : &st->bk;
+  const unsigned long long* n_ptr = &st->ctl->cnt[st->cur_slot];
+  Arr src = st->cur.view();
+  cudaError_t e = cudaSuccess;
+  for (uint32_t p = 0; p < npass && e == cudaSuccess; ++p) {
+    Store& dst = *buf[p & 1];
+    dst.set_dense();
+    Traced tr(st, SQS_K_SORT);
+    e = sqs::launch_rsort_pass(launch_of(st, in_slots), st->kw, st->amp32, st->ctl, src, n_ptr,
+                               p == 0 ? per_seg : 1u, p == 0 ? tiles0 : tilesN,
+                               p == 0 ? &L : nullptr, g.t, shifts[p], hist, part, n_dev,
+                               dst.view());
+    st->launches += 3;  // a pass is four kernels: histogram, two scan steps, scatter
+    src = dst.view();
+    n_ptr = n_dev;
+  }
+  if (e != cudaSuccess) return cuda_fail(st, e, "sort pass launch");
+  const int out_slot = (st->cur_slot + 1) & 3;
+  st->alt.set_segments(chunk_log2 + 1, (uint32_t)nseg_out);
+  {
+    Traced tr(st, SQS_K_SORT_MERGE);
+    e = sqs::launch_rsort_merge(launch_of(st, in_slots), st->kw, st->amp32, st->ctl,
+                                st->bk.view(), n_dev, g, st->alt.view(), out_slot);
+  }
+  if (e != cudaSuccess) return cuda_fail(st, e, "sort merge launch");
+  st->bk.set_dense();
+  if (rec_idx >= 0) {
+    e = sqs::launch_record(launch_of(st, 1), st->ctl, st->cur_slot, out_slot,
+                           st->rec_dev + 2 * (size_t)rec_idx);
+    if (e != cudaSuccess) return cuda_fail(st, e, "record launch");
+  }
+  std::swap(st->cur, st->alt);
+  st->cur_slot = out_slot;
+  st->ub = std::min(max_branches(st), 2 * st->ub);
+  return SQS_OK;
+}
+
+// SQS_MERGE_TUNED: which merge this step takes, and whether it is timed.
+// A size class is the log2 of the count bound with the sort pass count;
+// its first steps time each path once (CUDA events, per slot visited),
+// the rest take the faster.  A pending measurement is read only when its
+// events have completed, so the choice never waits on the device.
+int tuned_path(sqs_state* st, uint32_t key, bool& timed) {
+  sqs_state::Tune& T = st->tune[key];
+  timed = false;
+  if (T.pending >= 0) {
+    if (cudaEventQuery(T.ev[1]) != cudaSuccess) {
+      cudaGetLastError();  // not ready: no new measurement this step
+      return T.us_per_slot[1] >= 0.f && T.us_per_slot[1] < T.us_per_slot[0] ? 1 : 0;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, T.ev[0], T.ev[1]);
+    T.us_per_slot[T.pending] = 1e3f * ms / (float)std::max<uint64_t>(1, T.slots);
+    T.pending = -1;
+  }
+  for (int p = 0; p < 2; ++p) {
+    if (T.us_per_slot[p] < 0.f) {
+      if (!T.ev[0] && (cudaEventCreate(&T.ev[0]) != cudaSuccess ||
+                       cudaEventCreate(&T.ev[1]) != cudaSuccess)) {
+        cudaGetLastError();
+        return 0;
+      }
+      timed = true;
+      return p;
+    }
+  }
+  return T.us_per_slot[1] < T.us_per_slot[0] ? 1 : 0;
+}
+
+sqs_status run_branching(sqs_state* st, const Gate1& g, double est_in = -1.0,
+                         int64_t rec_idx = -1) {
+  sqs_status s = run_pending(st, true);  // leaves the fused tail in ops_buf
+  if (s != SQS_OK) return st->sticky = s;
+  if (g.no_partners) {
+    st->stats.steps_expand++;
+    return run_expand(st, g, rec_idx);
+  }
+  const bool sort_ok = st->ub < (1ull << 31) && !(st->flags & SQS_MERGE_CLUSTER);
+  int path = 0;
+  bool timed = false;
+  uint32_t key = 0;
+  if (sort_ok && (st->flags & SQS_MERGE_SORT)) {
+    path = 1;
+  } else if (sort_ok && (st->flags & SQS_MERGE_TUNED)) {
+    uint32_t lg = 0;
+    while (lg < 63 && (1ull << lg) < st->ub) ++lg;
+    key = lg | ((uint32_t)sort_shifts(st, g).size() << 8);
+    path = tuned_path(st, key, timed);
+  }
+  if (timed) {
+    sqs_state::Tune& T = st->tune[key];
+    T.slots = st->cur.slots(st->ub);
+    cudaEventRecord(T.ev[0], st->stream);
+  }
+  if (path == 1) {
+    st->stats.steps_sort++;
+    s = run_sorted(st, g, rec_idx);
+  } else {
+    s = run_hashed(st, g, est_in, rec_idx);
+  }
+  if (timed && s == SQS_OK) {
+    sqs_state::Tune& T = st->tune[key];
+    cudaEventRecord(T.ev[1], st->stream);
+    T.pending = path;
+  }
+  return s;
 }
 
 bool is_zero(double re, double im) { return re == 0.0 && im == 0.0; }
@@ -741,6 +938,9 @@ sqs_status issue_branching(sqs_state* st, const Gate1& g_in, uint32_t n_ctrl) {
   features(st, g, n_ctrl, x);
   // A target bit known constant over the whole state has no partner anywhere.
   g.no_partners = (st->const_val[g.t] >= 0) ? 1u : 0u;
+  g.vary[0] = g.vary[1] = 0ull;
+  for (uint32_t q = 0; q < st->total_bits; ++q)
+    if (st->const_val[q] < 0) g.vary[q >> 6] |= 1ull << (q & 63);
   note_branch(st, g);
   if ((st->flags & SQS_SIZING_LEARNED) && st->predictor) {
     sqs_state::Lazy q;
@@ -995,7 +1195,7 @@ sqs_status sqs_state_create(const uint32_t* reg_widths, uint32_t n_regs, uint32_
                             void* cuda_stream, sqs_state** out) {
   if (!out || !reg_widths || n_regs == 0 || n_regs > 128) return SQS_ERR_ARG;
   if (flags & ~(SQS_AMP_FP32 | SQS_SIZING_LEARNED | SQS_MERGE_HASH | SQS_MERGE_SORT |
-                SQS_MERGE_CLUSTER))
+                SQS_MERGE_CLUSTER | SQS_MERGE_TUNED))
     return SQS_ERR_ARG;
   uint32_t total = 0;
   for (uint32_t j = 0; j < n_regs; ++j) {
@@ -1058,6 +1258,10 @@ void sqs_state_destroy(sqs_state* st) {
   dfree(st, st->rec_dev);
   dfree(st, st->ctl);
   dfree(st, st->scratch);
+  dfree(st, st->sort_buf);
+  for (auto& kv : st->tune)
+    for (cudaEvent_t e : kv.second.ev)
+      if (e) cudaEventDestroy(e);
   for (sqs_table* t : st->tables) {
     dfree(st, t->dev);
     delete t;

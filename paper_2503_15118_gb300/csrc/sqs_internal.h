@@ -109,6 +109,7 @@ struct Gate1 {            // the interference operation of one merge step
   double eps, eps2;       // pruning threshold and its square (|a| < eps removes)
   float epsf;             // eps rounded to FP32
   uint32_t no_partners;   // the target bit is constant over the state: expand only
+  uint64_t vary[2];       // key bits not known constant over the state (sort digits)
 };
 
 struct Launch {
@@ -131,6 +132,27 @@ cudaError_t launch_apply_compact(const Launch& L, int kw, bool amp32, Ctl* ctl, 
 // bk.n_seg buckets of 2^bk.seg_log2 slots, counters zero on entry.
 cudaError_t launch_partition(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
                              const OpList& ops, const Gate1& g, Arr bk);
+// Radix-sort merge (sqs_sort.cu).  One LSD pass: digit `shift` of the
+// pair-class key (key with bit t deleted) of `in` -> `out` (dense), stable.
+// With first_ops the fused run is applied on the way (in is the state as it
+// lies, n_ptr its count); later passes read the dense count *n_ptr.  hist
+// holds 2^8 * n_tiles counters, part sort_part_entries(); the pass stores the
+// number of branches written in *n_dev.
+int sort_tile();
+int sort_radix_bits();
+uint32_t sort_merge_chunk_log2();
+size_t sort_part_entries();
+cudaError_t launch_rsort_pass(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in,
+                              const unsigned long long* n_ptr, uint32_t per_seg,
+                              uint64_t n_tiles, const OpList* first_ops, uint32_t t,
+                              uint32_t shift, unsigned int* hist, unsigned int* part,
+                              unsigned long long* n_dev, Arr out);
+// Combines neighbours of the sorted array `in` (*n_ptr branches): chunk c of
+// 2^sort_merge_chunk_log2() branches becomes segment c of `out` (twice the
+// size).  Adds the count into cnt[out_slot], clears cnt[(out_slot + 1) & 3].
+cudaError_t launch_rsort_merge(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in,
+                               const unsigned long long* n_ptr, const Gate1& g, Arr out,
+                               int out_slot);
 // One CTA per bucket: pair, apply the 2x2, prune; bucket b's survivors become
 // segment b of `out` (segment capacity 2 x bucket capacity).  Resets the
 // bucket counters.

@@ -24,270 +24,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sqs_device.cuh"
 #include "sqs_internal.h"
 
 namespace sqs {
-
-typedef unsigned __int128 u128;
-
-template <int KW>
-struct KT;
-template <>
-struct KT<1> {
-  typedef uint64_t T;
-};
-template <>
-struct KT<2> {
-  typedef u128 T;
-};
-
-template <int KW>
-__device__ __forceinline__ typename KT<KW>::T mk(uint64_t lo, uint64_t hi);
-template <>
-__device__ __forceinline__ uint64_t mk<1>(uint64_t lo, uint64_t) {
-  return lo;
-}
-template <>
-__device__ __forceinline__ u128 mk<2>(uint64_t lo, uint64_t hi) {
-  return (((u128)hi) << 64) | (u128)lo;
-}
-
-__device__ __forceinline__ uint64_t lo64(uint64_t k) { return k; }
-__device__ __forceinline__ uint64_t lo64(u128 k) { return (uint64_t)k; }
-__device__ __forceinline__ uint64_t hi64(uint64_t) { return 0; }
-__device__ __forceinline__ uint64_t hi64(u128 k) { return (uint64_t)(k >> 64); }
-
-__device__ __forceinline__ uint64_t wmask(uint32_t w) {
-  return w >= 64 ? ~0ull : ((1ull << w) - 1ull);
-}
-
-template <class K>
-__device__ __forceinline__ uint64_t get_field(K k, uint32_t off, uint32_t w) {
-  return (uint64_t)(k >> off) & wmask(w);
-}
-
-template <class K>
-__device__ __forceinline__ K set_field(K k, uint32_t off, uint32_t w, uint64_t v) {
-  const K m = ((K)wmask(w)) << off;
-  return (k & ~m) | (((K)(v & wmask(w))) << off);
-}
-
-// splitmix64 finalizer (Steele, Lea, Flood 2014): a bijective 64-bit mixer.
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-  return z ^ (z >> 31);
-}
-__device__ __forceinline__ uint64_t khash(uint64_t k) { return mix64(k); }
-__device__ __forceinline__ uint64_t khash(u128 k) {
-  return mix64((uint64_t)k ^ mix64((uint64_t)(k >> 64) + 0x9e3779b97f4a7c15ull));
-}
-
-// ---- amplitudes ------------------------------------------------------------
-// Arithmetic runs in the storage type: FP64 states in FP64, FP32 states in
-// FP32 (the FP32 pipe is 64x wider than the FP64 pipe here).  Two-term sums
-// of FP32 products are single FP32 roundings of the exact sum, which is the
-// value an FP64 accumulation rounded to the FP32 store would give.
-// Complex product with one product fused into the sum (two instructions per
-// component): one rounding fewer than the host's complex<double> product.
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(__fma_rn(a.x, b.x, -__dmul_rn(a.y, b.y)),
-                      __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x)));
-}
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)),
-                     __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
-}
-// u * a + p (real u), fused per component.
-__device__ __forceinline__ double2 rfma(double u, double2 a, double2 p) {
-  return make_double2(__fma_rn(u, a.x, p.x), __fma_rn(u, a.y, p.y));
-}
-__device__ __forceinline__ float2 rfma(float u, float2 a, float2 p) {
-  return make_float2(__fmaf_rn(u, a.x, p.x), __fmaf_rn(u, a.y, p.y));
-}
-// c * a + p (complex c), fused.
-__device__ __forceinline__ double2 cfma(double2 c, double2 a, double2 p) {
-  return make_double2(__fma_rn(c.x, a.x, __fma_rn(-c.y, a.y, p.x)),
-                      __fma_rn(c.x, a.y, __fma_rn(c.y, a.x, p.y)));
-}
-__device__ __forceinline__ float2 cfma(float2 c, float2 a, float2 p) {
-  return make_float2(__fmaf_rn(c.x, a.x, __fmaf_rn(-c.y, a.y, p.x)),
-                     __fmaf_rn(c.x, a.y, __fmaf_rn(c.y, a.x, p.y)));
-}
-// Real coefficient: (u + 0i)(a.x + i a.y) evaluated as above is exactly these
-// two products.
-__device__ __forceinline__ double2 rmul(double u, double2 a) {
-  return make_double2(__dmul_rn(u, a.x), __dmul_rn(u, a.y));
-}
-__device__ __forceinline__ float2 rmul(float u, float2 a) {
-  return make_float2(__fmul_rn(u, a.x), __fmul_rn(u, a.y));
-}
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) {
-  return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
-}
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
-  return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
-}
-// Exact negation by the sign bits (no arithmetic instruction).
-__device__ __forceinline__ double2 cneg(double2 a) {
-  return make_double2(__longlong_as_double(__double_as_longlong(a.x) ^ (long long)0x8000000000000000ull),
-                      __longlong_as_double(__double_as_longlong(a.y) ^ (long long)0x8000000000000000ull));
-}
-__device__ __forceinline__ float2 cneg(float2 a) {
-  return make_float2(__int_as_float(__float_as_int(a.x) ^ (int)0x80000000u),
-                     __int_as_float(__float_as_int(a.y) ^ (int)0x80000000u));
-}
-__device__ __forceinline__ double norm2(double2 a) {
-  return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
-}
-__device__ __forceinline__ double norm2(float2 a) {
-  const double x = (double)a.x, y = (double)a.y;
-  return __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
-}
-// |a| >= eps?  Certain, without floating-point arithmetic, when one component
-// already reaches eps in magnitude (IEEE order of non-negative values is
-// integer order); otherwise |a|^2 is compared with eps^2 in FP64.
-__device__ __forceinline__ bool keep_amp(double2 a, double eps, float, double eps2) {
-  const unsigned long long e = (unsigned long long)__double_as_longlong(eps);
-  const unsigned long long ax =
-      (unsigned long long)__double_as_longlong(a.x) & 0x7fffffffffffffffull;
-  const unsigned long long ay =
-      (unsigned long long)__double_as_longlong(a.y) & 0x7fffffffffffffffull;
-  if (ax >= e || ay >= e) return true;
-  if ((ax | ay) == 0ull) return e == 0ull;  // exact zero: kept only when eps = 0
-  return !(norm2(a) < eps2);
-}
-__device__ __forceinline__ bool keep_amp(float2 a, double, float epsf, double eps2) {
-  const unsigned int e = (unsigned int)__float_as_int(epsf);
-  const unsigned int ax = (unsigned int)__float_as_int(a.x) & 0x7fffffffu;
-  const unsigned int ay = (unsigned int)__float_as_int(a.y) & 0x7fffffffu;
-  if (ax >= e || ay >= e) return true;
-  if ((ax | ay) == 0u) return eps2 == 0.0;
-  return !(norm2(a) < eps2);
-}
-__device__ __forceinline__ void to_amp(double2& out, double2 v) { out = v; }
-__device__ __forceinline__ void to_amp(float2& out, double2 v) {
-  out = make_float2((float)v.x, (float)v.y);
-}
-__device__ __forceinline__ double2 to_f64(double2 v) { return v; }
-__device__ __forceinline__ double2 to_f64(float2 v) { return make_double2(v.x, v.y); }
-
-// ---- keys --------------------------------------------------------------------
-template <int KW>
-__device__ __forceinline__ typename KT<KW>::T ld_key(const Arr& a, uint64_t i) {
-  return mk<KW>(a.k0[i], KW == 2 ? a.k1[i] : 0ull);
-}
-template <int KW>
-__device__ __forceinline__ void st_key(const Arr& a, uint64_t i, typename KT<KW>::T k) {
-  a.k0[i] = lo64(k);
-  if (KW == 2) a.k1[i] = hi64(k);
-}
-
-// ---- layout ----------------------------------------------------------------------
-// Number of slots to visit and whether slot i holds a branch.
-__device__ __forceinline__ uint64_t slots_of(const Arr& a, const Ctl* ctl, int slot) {
-  return a.seg_cnt ? ((uint64_t)a.n_seg << a.seg_log2) : ctl->cnt[slot];
-}
-__device__ __forceinline__ bool slot_live(const Arr& a, uint64_t i) {
-  if (!a.seg_cnt) return true;
-  return (uint32_t)(i & ((1ull << a.seg_log2) - 1ull)) < a.seg_cnt[i >> a.seg_log2];
-}
-
-// Calls f(i) for every live slot: grid-stride over a dense array, or CTA per
-// segment (live branches are a prefix of each segment).
-// Calls f(i) for every live slot: grid-stride over a dense array, or CTA per
-// segment (live branches are a prefix of each segment).
-template <class F>
-__device__ __forceinline__ void for_each_live(const Arr& a, uint64_t n_dense, F f) {
-  if (!a.seg_cnt) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_dense; i += stride)
-      f(i);
-  } else {
-    for (uint32_t sg = blockIdx.x; sg < a.n_seg; sg += gridDim.x) {
-      const uint32_t n = a.seg_cnt[sg];
-      const uint64_t base = (uint64_t)sg << a.seg_log2;
-      for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) f(base + j);
-    }
-  }
-}
-
-// ---- errors --------------------------------------------------------------------
-__device__ __forceinline__ void raise_err(Ctl* ctl, unsigned int bit, uint32_t seq,
-                                          unsigned long long need) {
-  if (atomicOr(&ctl->err, bit) == 0u) ctl->err_where = seq;
-  atomicMax(&ctl->need, need);
-}
-
-// ---- fused operation run ---------------------------------------------------------
-// tab: the folded factors in the storage type (shared-memory copy).
-template <int KW, class AT>
-__device__ __forceinline__ bool apply_ops(uint32_t n_ops, const DevOp* ops, const AT* tab,
-                                          typename KT<KW>::T& k, AT& a) {
-  typedef typename KT<KW>::T K;
-  uint32_t idx = 0;
-#pragma unroll 1
-  for (uint32_t o = 0; o < n_ops; ++o) {
-    const DevOp& op = ops[o];
-    const uint32_t kind = op.kind;
-    const bool on = (k & mk<KW>(op.pmask[0], op.pmask[1])) == mk<KW>(op.pval[0], op.pval[1]);
-    if (kind == OP_XOR) {
-      if (on) k ^= mk<KW>(op.xmask[0], op.xmask[1]);
-    } else if (kind == OP_MUL || kind == OP_MUL_XOR) {
-      if (on) {
-        const uint32_t one = op.sel_bit < 128 ? (uint32_t)((k >> op.sel_bit) & (K)1) : 0u;
-        idx |= (1u + one) << op.shift;
-        if (kind == OP_MUL_XOR) k ^= mk<KW>(op.xmask[0], op.xmask[1]);
-      }
-    } else if (kind == OP_ADD_REG || kind == OP_SUB_REG || kind == OP_ADD_CONST) {
-      if (on) {
-        const uint64_t d = get_field(k, op.dst_off, op.dst_w);
-        const uint64_t s = kind == OP_ADD_CONST ? op.constant : get_field(k, op.src_off, op.src_w);
-        k = set_field<K>(k, op.dst_off, op.dst_w, kind == OP_SUB_REG ? d - s : d + s);
-      }
-    } else if (kind == OP_TABLE) {
-      if (idx) a = cmul(a, tab[op.tab_off + idx]);
-      idx = 0;
-    } else if (kind == OP_QRAM) {
-      if (on) {
-        const uint64_t addr = get_field(k, op.src_off, op.src_w);
-        uint64_t d = 0;
-        if (addr < op.n_entries) {
-          switch ((uint32_t)op.constant) {
-            case 1: d = __ldg((const uint8_t*)op.table + addr); break;
-            case 2: d = __ldg((const uint16_t*)op.table + addr); break;
-            case 4: d = __ldg((const uint32_t*)op.table + addr); break;
-            default: d = __ldg((const unsigned long long*)op.table + addr); break;
-          }
-        }
-        k = set_field<K>(k, op.dst_off, op.dst_w, get_field(k, op.dst_off, op.dst_w) ^ d);
-      }
-    } else if (kind == OP_SWAP) {
-      if (on) {
-        const uint64_t v1 = get_field(k, op.dst_off, op.dst_w);
-        const uint64_t v2 = get_field(k, op.src_off, op.src_w);
-        k = set_field<K>(set_field<K>(k, op.dst_off, op.dst_w, v2), op.src_off, op.src_w, v1);
-      }
-    } else if (kind == OP_PRUNE) {
-      if (!keep_amp(a, op.eps, (float)op.eps, op.eps2)) return false;
-    }
-  }
-  return true;
-}
-
-// Copies the launch's operations and factor table into shared memory: the
-// per-branch loop then reads them with broadcast shared loads instead of
-// indexed parameter-space loads.
-template <class AT>
-__device__ __forceinline__ void load_ops(const OpList& L, DevOp* ops, AT* tab) {
-  static_assert(sizeof(DevOp) % 8 == 0, "DevOp copied as 8-byte words");
-  const uint64_t* src = (const uint64_t*)L.op;
-  uint64_t* dst = (uint64_t*)ops;
-  const uint32_t words = L.n * (uint32_t)(sizeof(DevOp) / 8);
-  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
-  for (uint32_t i = threadIdx.x; i < L.n_tab; i += blockDim.x) to_amp(tab[i], L.tab[i]);
-  __syncthreads();
-}
 
 template <class AT>
 __global__ void k_init(Ctl* ctl, Arr a, int slot) {
@@ -306,7 +46,6 @@ __global__ void k_init(Ctl* ctl, Arr a, int slot) {
 }
 
 // ---------------------------------------------------------------------------
-constexpr int kStreamThreads = 256;
 
 template <int KW, class AT, bool TK, bool TA>
 __global__ void __launch_bounds__(kStreamThreads)
@@ -349,14 +88,16 @@ __global__ void __launch_bounds__(kStreamThreads)
   for (uint64_t c = blockIdx.x; c < out.n_seg; c += gridDim.x) {
     if (threadIdx.x == 0) seg_fill = 0;
     __syncthreads();
+    // Input segment c (any size up to the output segment's) or dense chunk c.
     const uint64_t base = c << out.seg_log2;
+    const uint64_t ibase = in.seg_cnt ? (c << in.seg_log2) : base;
     uint64_t cnt;
     if (in.seg_cnt)
       cnt = c < in.n_seg ? in.seg_cnt[c] : 0;
     else
       cnt = base >= n_dense ? 0 : (n_dense - base < chunk ? n_dense - base : chunk);
     for (uint64_t r = 0; r < cnt; r += blockDim.x) {
-      const uint64_t i = base + r + threadIdx.x;
+      const uint64_t i = ibase + r + threadIdx.x;
       bool keep = false;
       typename KT<KW>::T k = 0;
       AT v;
@@ -459,88 +200,6 @@ __global__ void __launch_bounds__(kStreamThreads)
       } else {
         raise_err(ctl, kErrBucket, seq, (unsigned long long)pos[q] + 1);
       }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// The 2x2 of one merge step on a pair class: children (o0, o1) of the
-// members a0 (bit 0, present when has0) and a1 (bit 1, present when has1).
-// Coefficients in the storage type; products shared between the rows of a
-// column when the host flagged U10 = +-U00 or U11 = +-U01.
-template <class AT>
-struct Coef;
-template <>
-struct Coef<double2> {
-  typedef double S;
-  __device__ static double2 c(const Gate1& g, int e) { return make_double2(g.u[2 * e], g.u[2 * e + 1]); }
-  __device__ static double r(const Gate1& g, int e) { return g.u[2 * e]; }
-};
-template <>
-struct Coef<float2> {
-  typedef float S;
-  __device__ static float2 c(const Gate1& g, int e) { return make_float2(g.uf[2 * e], g.uf[2 * e + 1]); }
-  __device__ static float r(const Gate1& g, int e) { return g.uf[2 * e]; }
-};
-
-// FP32 storage: a two-term sum that lands below the rounding noise of its
-// terms (2^-21 of their size, a few units in the last place) is a
-// cancellation that FP64 arithmetic would have made (near) exact; it is
-// flushed to zero so that the pruning step removes it.  FP64 states keep
-// their results as computed.
-__device__ __forceinline__ void flush_residue(double2&, double2, double2) {}
-__device__ __forceinline__ void flush_residue(float2& o, float2 a0, float2 a1) {
-  const float size = fabsf(a0.x) + fabsf(a0.y) + fabsf(a1.x) + fabsf(a1.y);
-  if (fabsf(o.x) + fabsf(o.y) <= size * 4.76837158e-7f) o = make_float2(0.f, 0.f);
-}
-
-template <class AT>
-__device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, bool has0, AT a0,
-                                         bool has1, AT a1, AT& o0, AT& o1) {
-  typedef typename Coef<AT>::S S;
-  const bool same0 = g.reuse & 1u, neg0 = g.reuse & 4u;  // U10 = +-U00
-  const bool same1 = g.reuse & 2u, neg1 = g.reuse & 8u;  // U11 = +-U01
-  if (g.mode == 2 || g.mode == 1) {
-    S u00, u01, u10, u11;
-    if (g.mode == 1) {
-      const double theta = g.scale * (double)angle_value + g.offset;
-      double sn, cs;
-      sincos(theta * 0.5, &sn, &cs);
-      u00 = (S)cs, u01 = (S)-sn, u10 = (S)sn, u11 = (S)cs;
-    } else {
-      u00 = Coef<AT>::r(g, 0), u01 = Coef<AT>::r(g, 1), u10 = Coef<AT>::r(g, 2),
-      u11 = Coef<AT>::r(g, 3);
-    }
-    if (has0 && has1) {
-      const AT p01 = rmul(u01, a1);
-      const AT p11 = same1 ? (neg1 ? cneg(p01) : p01) : rmul(u11, a1);
-      o0 = rfma(u00, a0, p01);
-      o1 = rfma(u10, a0, p11);
-      flush_residue(o0, a0, a1);
-      flush_residue(o1, a0, a1);
-    } else if (has0) {
-      o0 = rmul(u00, a0);
-      o1 = same0 ? (neg0 ? cneg(o0) : o0) : rmul(u10, a0);
-    } else {
-      o0 = rmul(u01, a1);
-      o1 = same1 ? (neg1 ? cneg(o0) : o0) : rmul(u11, a1);
-    }
-  } else {
-    const AT U00 = Coef<AT>::c(g, 0), U01 = Coef<AT>::c(g, 1);
-    const AT U10 = Coef<AT>::c(g, 2), U11 = Coef<AT>::c(g, 3);
-    if (has0 && has1) {
-      const AT p01 = cmul(U01, a1);
-      const AT p11 = same1 ? (neg1 ? cneg(p01) : p01) : cmul(U11, a1);
-      o0 = cfma(U00, a0, p01);
-      o1 = cfma(U10, a0, p11);
-      flush_residue(o0, a0, a1);
-      flush_residue(o1, a0, a1);
-    } else if (has0) {
-      o0 = cmul(U00, a0);
-      o1 = same0 ? (neg0 ? cneg(o0) : o0) : cmul(U10, a0);
-    } else {
-      o0 = cmul(U01, a1);
-      o1 = same1 ? (neg1 ? cneg(o0) : o0) : cmul(U11, a1);
     }
   }
 }

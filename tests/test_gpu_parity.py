@@ -70,10 +70,10 @@ GATES_64 = [
 ]
 
 
-MERGES = {"cluster": 16, "bucket": 0}
+MERGES = {"cluster": 16, "bucket": 0, "sort": 8, "tuned": 32}
 
 
-@pytest.mark.parametrize("merge", ["cluster", "bucket"])
+@pytest.mark.parametrize("merge", list(MERGES))
 @pytest.mark.parametrize("n", [1, 33, 2049, 70001])
 @pytest.mark.parametrize("gi", range(len(GATES_64)))
 def test_single_gate_64bit_keys(sqs, n, gi, merge):
@@ -86,7 +86,7 @@ def test_single_gate_64bit_keys(sqs, n, gi, merge):
     _check(gs, os_)
 
 
-@pytest.mark.parametrize("merge", ["cluster", "bucket"])
+@pytest.mark.parametrize("merge", list(MERGES))
 @pytest.mark.parametrize("pair_fraction", [0.0, 1.0])
 @pytest.mark.parametrize("n", [5, 4096, 30000, 300000])
 def test_h_pairing_extremes(sqs, n, pair_fraction, merge):
@@ -112,7 +112,7 @@ GATES_128 = [
 ]
 
 
-@pytest.mark.parametrize("merge", ["cluster", "bucket"])
+@pytest.mark.parametrize("merge", list(MERGES))
 @pytest.mark.parametrize("amp32", [False, True])
 @pytest.mark.parametrize("n", [3, 2049, 40000])
 @pytest.mark.parametrize("gi", range(len(GATES_128)))
@@ -195,7 +195,7 @@ def test_config1_fp32(sqs):
     assert compare_states(g.to_dict(), o.to_dict(), atol=1e-5, band=1e-5) >= 1 - 1e-6
 
 
-@pytest.mark.parametrize("merge", ["cluster", "bucket"])
+@pytest.mark.parametrize("merge", list(MERGES))
 def test_config2_reduced(sqs, merge):
     circ = W.config2(seed=2, n_branch=16, n_perm=300, n_cancel=6)
     n_main = len(circ["gates"]) - 6
@@ -332,7 +332,7 @@ def test_long_fused_runs(sqs, then_branch):
     assert rng is not None
 
 
-@pytest.mark.parametrize("merge", ["cluster", "bucket"])
+@pytest.mark.parametrize("merge", list(MERGES))
 def test_constant_target_expand_path(sqs, merge):
     """Targets whose bit the runtime can prove constant (never touched, or
     flipped by X / CNOT whose controls are themselves constant) take the
@@ -359,3 +359,29 @@ def test_constant_target_expand_path(sqs, merge):
     got, ref = g.to_dict(), o.to_dict()
     assert compare_states(got, ref) > 1 - 1e-12
     assert set(got) == set(ref)
+
+
+@pytest.mark.parametrize("merge", list(MERGES))
+@pytest.mark.parametrize("last", ["expand", "merge"])
+@pytest.mark.parametrize("then", ["prune", "diag_run"])
+def test_standalone_compaction_after_wide_segments(sqs, merge, last, then):
+    """The expansion, cluster and sort merges leave segments of 2^13 slots;
+    a standalone pass that may drop branches (an explicit prune, or a run of
+    diagonal gates split over several launches) must read them as such."""
+    widths = [8, 8, 8]
+    expand = [("h", 0, b, ()) for b in range(8)] + [("h", 1, b, ()) for b in range(5)]
+    merge_step = [("x", 2, 0, ((0, 3, 1),)), ("h", 0, 3, ((2, 0, 1),))]
+    gates = expand[:8] + merge_step + expand[8:] if last == "expand" else expand + merge_step
+    if then == "prune":
+        gates += [("prune", 1e-14)]
+    else:
+        # 12 diagonal gates on distinct bits: more selector bits than one
+        # launch's factor table takes, so the first group runs on its own.
+        gates += [("u1q", r, b, np.diag([np.exp(0.1j * (b + 1)), np.exp(-0.2j * r)]), ())
+                  for r in (0, 1) for b in range(6)]
+    circ = {"widths": widths, "eps": 1e-14, "tables": [], "gates": gates}
+    o = oracle.run_circuit(circ)
+    g = sqs.run_circuit(circ, merge=MERGES[merge])
+    got, ref = g.to_dict(), o.to_dict()
+    assert set(got) == set(ref)
+    assert compare_states(got, ref) > 1 - 1e-12
