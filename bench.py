@@ -174,10 +174,14 @@ def variants(circ, widths, stream, probs, norm, flush, args, st64):
     pred, loss, (X, _) = predictor.trained_predictor(seed=0)
     out = {"predictor": {"train_records": int(X.shape[0]), "train_mse": loss}}
     ref = None
-    for name, amp32, learned in (("f64_exact", False, False), ("f32_exact", True, False),
-                                 ("f32_learned", True, True), ("f64_learned", False, True)):
+    for name, amp32, learned, merge in (
+            ("f64_exact", False, False, sqs.MERGE_AUTO), ("f32_exact", True, False, sqs.MERGE_AUTO),
+            ("f32_learned", True, True, sqs.MERGE_AUTO), ("f64_learned", False, True, sqs.MERGE_AUTO),
+            ("f64_sort_merge", False, False, sqs.MERGE_SORT),
+            ("f64_cluster_merge", False, False, sqs.MERGE_CLUSTER),
+            ("f64_tuned_merge", False, False, sqs.MERGE_TUNED)):
         st = sqs.State(widths, amp32=amp32, learned=learned, capacity_hint=1 << 25,
-                       stream=stream.cuda_stream, eps=circ["eps"])
+                       stream=stream.cuda_stream, eps=circ["eps"], merge=merge)
         if learned:
             st.set_predictor(pred)
 
@@ -189,16 +193,20 @@ def variants(circ, widths, stream, probs, norm, flush, args, st64):
         for _ in range(args.warmup):
             step()
         st.sync()
-        w0 = st.stats()["host_waits"]
+        s0 = st.stats()
         ms = _timed_steps(st, step, flush, stream, args.steps)
-        waits = (st.stats()["host_waits"] - w0) / args.steps
+        s1 = st.stats()
+        waits = (s1["host_waits"] - s0["host_waits"]) / args.steps
+        paths = {k[6:]: (s1[k] - s0[k]) / args.steps
+                 for k in ("steps_expand", "steps_hash", "steps_sort", "steps_cluster")}
         lo, hi, a = st.export()
         d = dict(zip(lo.tolist(), a.tolist()))
         if units is None:
             units = BENCH_UNITS[0]
         entry = {"value": units / (ms / 1e3), "ms_per_step": ms,
                  "host_waits_per_step": waits, "bytes_peak": st.stats()["bytes_peak"],
-                 "overflow_reruns": st.stats()["overflow_reruns"]}
+                 "overflow_reruns": st.stats()["overflow_reruns"],
+                 "interference_steps_by_path": paths}
         if ref is None:
             ref = d
         else:

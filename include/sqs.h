@@ -84,7 +84,11 @@ typedef struct {
   uint32_t reg, bit, value;
 } sqs_ctrl;
 
-#define SQS_MAX_CTRL 8
+#define SQS_MAX_CTRL 8    /* controls carried inline by one sqs_perm_op      */
+#define SQS_MAX_PRED 128  /* controls / predicates passed as an array to the
+                             sqs_apply_u1q, _h, _ry, _ry_reg and _phase calls:
+                             one entry per qubit, so a predicate over whole
+                             registers ("ancilla register = 0") fits       */
 
 /*
  * Optional device allocator.  alloc(ctx, bytes, stream) returns device memory
@@ -195,6 +199,15 @@ sqs_status sqs_qram_load(sqs_state* st, uint32_t addr_reg, uint32_t data_reg,
                          const sqs_table* table);
 sqs_status sqs_qram_unload(sqs_state* st, uint32_t addr_reg, uint32_t data_reg,
                            const sqs_table* table);
+/* The same with the address formed by n_addr_regs consecutive registers
+ * addr_reg, addr_reg + 1, ... (register addr_reg in the low bits), as the
+ * controlled state preparation of a block-encoding queries a rotation-angle
+ * tree at (column index, prepared prefix) (Supp. D, U_L).  The address is at
+ * most 64 bits wide and the data register lies outside it (SQS_ERR_ARG). */
+sqs_status sqs_qram_load_span(sqs_state* st, uint32_t addr_reg, uint32_t n_addr_regs,
+                              uint32_t data_reg, const sqs_table* table);
+sqs_status sqs_qram_unload_span(sqs_state* st, uint32_t addr_reg, uint32_t n_addr_regs,
+                                uint32_t data_reg, const sqs_table* table);
 
 /* ---- pruning, readout ---------------------------------------------------- */
 

@@ -64,6 +64,7 @@ def _bind(lib):
         "or_apply_swap": (None, [P, u32, u32, CP, u32]),
         "or_apply_phase": (None, [P, CP, u32, dbl]),
         "or_qram": (None, [P, u32, u32, P, u64, u32]),
+        "or_qram_span": (None, [P, u32, u32, u32, P, u64, u32]),
         "or_prune": (None, [P, dbl]),
         "or_export": (u64, [P, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(dbl), u64]),
         "or_import": (None, [P, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(dbl), u64]),
@@ -168,9 +169,15 @@ class OracleState:
         self.lib.or_apply_phase(self.h, c, n, float(phi))
 
     def qram(self, addr_reg, data_reg, table):
+        """addr_reg: a register, or (first, count): the address is then the
+        concatenation of consecutive registers, the first one lowest."""
         t = np.ascontiguousarray(table)
-        self.lib.or_qram(self.h, addr_reg, data_reg, t.ctypes.data_as(ctypes.c_void_p),
-                         t.shape[0], t.dtype.itemsize)
+        if isinstance(addr_reg, tuple):
+            self.lib.or_qram_span(self.h, addr_reg[0], addr_reg[1], data_reg,
+                                  t.ctypes.data_as(ctypes.c_void_p), t.shape[0], t.dtype.itemsize)
+        else:
+            self.lib.or_qram(self.h, addr_reg, data_reg, t.ctypes.data_as(ctypes.c_void_p),
+                             t.shape[0], t.dtype.itemsize)
 
     def prune(self, eps):
         self.lib.or_prune(self.h, float(eps))

@@ -238,11 +238,18 @@ void or_apply_phase(OState* s, const OCtrl* pred, uint32_t n_pred, double phi) {
 // QRAM load (Supp. C, Eq. S1): data := data XOR d_addr, d truncated to the
 // data register's word length.  The same map undoes itself, so unload calls
 // this function again.
-void or_qram(OState* s, uint32_t addr_reg, uint32_t data_reg, const void* table,
-             uint64_t n_entries, uint32_t entry_bytes) {
+// The address is the concatenation of registers addr_reg .. addr_reg +
+// n_addr - 1, register addr_reg lowest (one register when n_addr = 1).
+void or_qram_span(OState* s, uint32_t addr_reg, uint32_t n_addr, uint32_t data_reg,
+                  const void* table, uint64_t n_entries, uint32_t entry_bytes) {
   const uint64_t wmask = (uint64_t)low_mask(s->width[data_reg]);
   permute(s, [&](u128 k) {
-    const uint64_t i = get_reg(s, k, addr_reg);
+    uint64_t i = 0;
+    uint32_t shift = 0;
+    for (uint32_t r = addr_reg; r < addr_reg + n_addr; ++r) {
+      i |= get_reg(s, k, r) << shift;
+      shift += s->width[r];
+    }
     uint64_t d = 0;
     if (i < n_entries) {
       const unsigned char* p = (const unsigned char*)table + i * entry_bytes;
@@ -251,6 +258,11 @@ void or_qram(OState* s, uint32_t addr_reg, uint32_t data_reg, const void* table,
     }
     return set_reg(s, k, data_reg, get_reg(s, k, data_reg) ^ (d & wmask));
   });
+}
+
+void or_qram(OState* s, uint32_t addr_reg, uint32_t data_reg, const void* table,
+             uint64_t n_entries, uint32_t entry_bytes) {
+  or_qram_span(s, addr_reg, 1, data_reg, table, n_entries, entry_bytes);
 }
 
 void or_prune(OState* s, double eps) { prune_map(s->psi, eps); }

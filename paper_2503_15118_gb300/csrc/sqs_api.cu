@@ -297,7 +297,7 @@ sqs::Launch launch_of(sqs_state* st, uint64_t n_hint) {
 bool encode_ctrls(sqs_state* st, const sqs_ctrl* c, uint32_t n, uint64_t mask[2],
                   uint64_t val[2]) {
   mask[0] = mask[1] = val[0] = val[1] = 0;
-  if (n > SQS_MAX_CTRL || (n && !c)) return false;
+  if (n > SQS_MAX_PRED || (n && !c)) return false;
   for (uint32_t i = 0; i < n; ++i) {
     if (c[i].reg >= st->width.size() || c[i].bit >= st->width[c[i].reg] || c[i].value > 1)
       return false;
@@ -655,6 +655,16 @@ std::vector<uint32_t> sort_shifts(const sqs_state* st, const Gate1& g) {
 // the merge writes st->alt, which becomes the state.
 sqs_status run_sorted(sqs_state* st, const Gate1& g, int64_t rec_idx) {
   const OpList& L = st->ops_buf;
+  {
+    // Tiles, histograms and buffers follow the count bound: a bound that
+    // outgrew the allocation is replaced by the exact count first.
+    const uint64_t c = 1ull << sqs::sort_merge_chunk_log2();
+    const uint64_t out_need = std::max<uint64_t>(1, (st->ub + c - 1) / c) * 2 * c;
+    if (st->ub > 1 && (st->bk.cap < st->ub || st->alt.cap < std::max(out_need, st->ub))) {
+      sqs_status s = sync_ctl(st);
+      if (s != SQS_OK) return s;
+    }
+  }
   const std::vector<uint32_t> shifts = sort_shifts(st, g);
   const uint32_t npass = (uint32_t)shifts.size();
   const uint64_t tile = (uint64_t)sqs::sort_tile();
@@ -1342,7 +1352,7 @@ sqs_status sqs_apply_perm(sqs_state* st, const sqs_perm_op* ops, uint32_t n_ops)
     const sqs_perm_op& p = ops[i];
     if (p.reg >= nr) return fail(st, SQS_ERR_ARG, "op %u: bad register", i);
     uint64_t cm[2], cv[2];
-    if (!encode_ctrls(st, p.ctrl, p.n_ctrl, cm, cv))
+    if (p.n_ctrl > SQS_MAX_CTRL || !encode_ctrls(st, p.ctrl, p.n_ctrl, cm, cv))
       return fail(st, SQS_ERR_ARG, "op %u: bad controls", i);
     HostOp h = blank_op(sqs::OP_XOR);
     DevOp& o = h.d;
@@ -1444,21 +1454,26 @@ sqs_status sqs_table_create(sqs_state* st, const void* host_entries, uint64_t n_
   return SQS_OK;
 }
 
-static sqs_status qram(sqs_state* st, uint32_t addr_reg, uint32_t data_reg, const sqs_table* t) {
+static sqs_status qram(sqs_state* st, uint32_t addr_reg, uint32_t n_addr, uint32_t data_reg,
+                       const sqs_table* t) {
   sqs_status s = check_usable(st);
   if (s != SQS_OK) return s;
   st->call++;
   const uint32_t nr = (uint32_t)st->width.size();
-  if (!t || addr_reg >= nr || data_reg >= nr || addr_reg == data_reg)
+  if (!t || n_addr == 0 || addr_reg >= nr || n_addr > nr - addr_reg || data_reg >= nr ||
+      (data_reg >= addr_reg && data_reg < addr_reg + n_addr))
     return fail(st, SQS_ERR_ARG, "bad QRAM arguments");
+  uint32_t addr_w = 0;
+  for (uint32_t r = addr_reg; r < addr_reg + n_addr; ++r) addr_w += st->width[r];
+  if (addr_w > 64) return fail(st, SQS_ERR_ARG, "QRAM address wider than 64 bits");
   bool owned = false;
   for (sqs_table* x : st->tables) owned |= (x == t);
   if (!owned) return fail(st, SQS_ERR_ARG, "table belongs to another state");
   HostOp o = blank_op(sqs::OP_QRAM);
   o.d.dst_off = st->offset[data_reg];
   o.d.dst_w = st->width[data_reg];
-  o.d.src_off = st->offset[addr_reg];
-  o.d.src_w = st->width[addr_reg];
+  o.d.src_off = st->offset[addr_reg];  // registers are packed in order: one field
+  o.d.src_w = addr_w;
   o.d.table = t->dev;
   o.d.n_entries = t->n;
   o.d.constant = t->bytes;
@@ -1468,12 +1483,22 @@ static sqs_status qram(sqs_state* st, uint32_t addr_reg, uint32_t data_reg, cons
 
 sqs_status sqs_qram_load(sqs_state* st, uint32_t addr_reg, uint32_t data_reg,
                          const sqs_table* table) {
-  return qram(st, addr_reg, data_reg, table);
+  return qram(st, addr_reg, 1, data_reg, table);
 }
 
 sqs_status sqs_qram_unload(sqs_state* st, uint32_t addr_reg, uint32_t data_reg,
                            const sqs_table* table) {
-  return qram(st, addr_reg, data_reg, table);
+  return qram(st, addr_reg, 1, data_reg, table);
+}
+
+sqs_status sqs_qram_load_span(sqs_state* st, uint32_t addr_reg, uint32_t n_addr_regs,
+                              uint32_t data_reg, const sqs_table* table) {
+  return qram(st, addr_reg, n_addr_regs, data_reg, table);
+}
+
+sqs_status sqs_qram_unload_span(sqs_state* st, uint32_t addr_reg, uint32_t n_addr_regs,
+                                uint32_t data_reg, const sqs_table* table) {
+  return qram(st, addr_reg, n_addr_regs, data_reg, table);
 }
 
 sqs_status sqs_prune(sqs_state* st, double eps, uint64_t* nnz_out) {

@@ -20,7 +20,8 @@ AMP_FP64, AMP_FP32 = 0, 1
 SIZING_EXACT, SIZING_LEARNED = 0, 2
 MERGE_AUTO, MERGE_HASH, MERGE_SORT, MERGE_CLUSTER, MERGE_TUNED = 0, 4, 8, 16, 32
 PERM_X, PERM_ADD_REG, PERM_SUB_REG, PERM_ADD_CONST, PERM_SUB_CONST, PERM_SWAP = range(6)
-MAX_CTRL = 8
+MAX_CTRL = 8     # controls inline in one permutation operation
+MAX_PRED = 128   # controls / predicates passed as an array
 
 
 class SqsError(RuntimeError):
@@ -90,6 +91,8 @@ SIGNATURES = {
     "sqs_table_create": (_S, [_P, _P, _u64, _u32, ctypes.POINTER(_P)]),
     "sqs_qram_load": (_S, [_P, _u32, _u32, _P]),
     "sqs_qram_unload": (_S, [_P, _u32, _u32, _P]),
+    "sqs_qram_load_span": (_S, [_P, _u32, _u32, _u32, _P]),
+    "sqs_qram_unload_span": (_S, [_P, _u32, _u32, _u32, _P]),
     "sqs_prune": (_S, [_P, _dbl, _UP]),
     "sqs_probabilities": (_S, [_P, _u32, _DP, _DP]),
     "sqs_probabilities_device": (_S, [_P, _u32, _P, _P]),
@@ -148,7 +151,7 @@ def load(build_if_missing=True):
 
 def _ctrls(ctrls):
     ctrls = list(ctrls or ())
-    if len(ctrls) > MAX_CTRL:
+    if len(ctrls) > MAX_PRED:
         raise ValueError("too many controls")
     arr = (Ctrl * max(1, len(ctrls)))()
     for i, c in enumerate(ctrls):
@@ -284,10 +287,20 @@ class State:
         return out
 
     def qram_load(self, addr_reg, data_reg, entries):
-        self._chk(self.lib.sqs_qram_load(self.h, addr_reg, data_reg, self.table(entries)))
+        """addr_reg: a register, or (first, count) for an address spanning
+        consecutive registers."""
+        if isinstance(addr_reg, tuple):
+            self._chk(self.lib.sqs_qram_load_span(self.h, addr_reg[0], addr_reg[1], data_reg,
+                                                  self.table(entries)))
+        else:
+            self._chk(self.lib.sqs_qram_load(self.h, addr_reg, data_reg, self.table(entries)))
 
     def qram_unload(self, addr_reg, data_reg, entries):
-        self._chk(self.lib.sqs_qram_unload(self.h, addr_reg, data_reg, self.table(entries)))
+        if isinstance(addr_reg, tuple):
+            self._chk(self.lib.sqs_qram_unload_span(self.h, addr_reg[0], addr_reg[1], data_reg,
+                                                    self.table(entries)))
+        else:
+            self._chk(self.lib.sqs_qram_unload(self.h, addr_reg, data_reg, self.table(entries)))
 
     def prune(self, eps, wait=False):
         n = ctypes.c_uint64()

@@ -17,7 +17,10 @@ and each gate is a tuple:
     ("add"|"sub", dst, src_reg, const, ctrls)   dst +-= src (src_reg<0: const)
     ("swap", r1, r2, ctrls)                     register exchange
     ("phase", preds, phi)                       a *= e^{i phi} where preds hold
-    ("qload"|"qunload", addr_reg, data_reg, t)  data ^= tables[t][addr]
+    ("qload"|"qunload", addr_reg, data_reg, t)  data ^= tables[t][addr]; addr_reg
+                                                may be (first, count): the address
+                                                is then consecutive registers
+                                                concatenated, the first lowest
     ("prune", eps)
 with ctrls / preds a tuple of (reg, bit, value) triples.
 """
@@ -321,3 +324,11 @@ def random_state(widths, n, seed, pair_fraction=0.5, target=None):
     perm = rng.permutation(n)
     amps = (rng.normal(size=n) + 1j * rng.normal(size=n)) / math.sqrt(2 * max(n, 1))
     return lo[perm], hi[perm], amps
+
+
+def config4(seed=4, N=1024, half_band=8, kappa=10.0, T=2000, n_points=10):
+    """The quantum linear-system walk (Sec. III.C, Supp. D) on one seeded
+    symmetric positive-definite banded system; see qlss.config4."""
+    from . import qlss
+    return qlss.config4(seed=seed, N=N, half_band=half_band, kappa=kappa, T=T,
+                        n_points=n_points)

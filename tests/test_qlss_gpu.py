@@ -1,0 +1,97 @@
+"""The linear-system walk (Sec. III.C, Supp. D) on the CUDA path.
+
+Small systems run the whole walk on both the CUDA path and the oracle, which
+must agree element by element.  At the full size (N = 1024, half-bandwidth 8,
+2^22 branches at the peak of a walk step) the oracle is too slow for a whole
+step, so the tests check what holds at any size: the block-encoding identity
+on sampled columns against numpy's A, U_A^dag undoing U_A, the norm kept by
+every step, and the FP32-storage state against the FP64 one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_15118_gb300 import qlss as Q
+from tests.helpers import compare_states
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sqs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_15118_gb300 import sqs as S
+    S.load()
+    return S
+
+
+@pytest.mark.parametrize("merge", [0, 8])
+@pytest.mark.parametrize("amp32", [False, True])
+def test_small_walk_matches_oracle(sqs, merge, amp32):
+    cfg = Q.config4(seed=6, N=8, half_band=2, kappa=5.0, T=20)
+    circ = Q.walk_circuit(cfg)
+    o = oracle.run_circuit(circ)
+    g = sqs.run_circuit(circ, amp32=amp32, merge=merge)
+    got, ref = g.to_dict(), o.to_dict()
+    if amp32:
+        assert compare_states(got, ref, atol=1e-5, band=1e-5) >= 1 - 1e-6
+    else:
+        assert compare_states(got, ref, eps=1e-14, atol=1e-12) >= 1 - 1e-10
+        assert g.peak_nnz() == o.peak()
+
+
+def test_one_step_n256_matches_oracle(sqs):
+    cfg = Q.config4(seed=4, N=256, half_band=8, kappa=10.0, T=2000)
+    circ = Q.walk_circuit(cfg, n_steps=1)
+    o = oracle.run_circuit(circ)
+    g = sqs.run_circuit(circ)
+    assert g.nnz() == o.nnz()
+    assert compare_states(g.to_dict(), o.to_dict(), eps=1e-14, atol=1e-12) >= 1 - 1e-10
+
+
+@pytest.fixture(scope="module")
+def full():
+    return Q.config4(seed=4, N=1024, half_band=8, kappa=10.0, T=2000)
+
+
+def test_full_size_block_encoding_columns(sqs, full):
+    cfg = full
+    n, ids, N = cfg["n"], cfg["ids"], 1 << cfg["n"]
+    off = np.cumsum([0] + cfg["widths"])
+    A, nf = cfg["A"], cfg["norm_f"]
+    fwd = Q.u_a(n, ids, cfg["t_l"], cfg["t_r"], ())
+    bwd = Q.u_a(n, ids, cfg["t_l"], cfg["t_r"], (), dagger=True)
+    for j in (0, 517, N - 1):
+        st = sqs.State(cfg["widths"])
+        for b in range(n):
+            if (j >> b) & 1:
+                st.apply(("x", Q.TOP, b, ()))
+        for gate in fwd:
+            st.apply(gate, cfg["tables"])
+        d = st.to_dict()
+        col = np.array([d.get(i << int(off[Q.TOP]), 0) for i in range(N)])
+        assert np.abs(col - A[:, j] / nf).max() < 4 * n * Q.ANGLE_SCALE
+        assert abs(sum(abs(v) ** 2 for v in d.values()) - 1) < 1e-10
+        for gate in bwd:
+            st.apply(gate, cfg["tables"])
+        back = st.to_dict()
+        assert set(back) == {j << int(off[Q.TOP])}
+        st.close()
+
+
+def test_full_size_walk_steps_keep_norm_and_fp32_fidelity(sqs, full):
+    cfg = full
+    circ = Q.walk_circuit(cfg, n_steps=2)
+    g64 = sqs.run_circuit(circ)
+    g32 = sqs.run_circuit(circ, amp32=True)
+    d64, d32 = g64.to_dict(), g32.to_dict()
+    n2 = sum(abs(v) ** 2 for v in d64.values())
+    assert abs(n2 - 1) < 1e-10
+    assert g64.peak_nnz() <= 4 << (2 * cfg["n"])
+    ov = sum(np.conj(v) * d32.get(k, 0) for k, v in d64.items())
+    n32 = sum(abs(v) ** 2 for v in d32.values())
+    assert abs(ov) ** 2 / (n2 * n32) >= 1 - 1e-6

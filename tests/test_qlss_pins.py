@@ -1,0 +1,140 @@
+"""Pins of the linear-system workload (Sec. III.C, Supp. D) on the CPU oracle.
+
+The walk's gate lists are inputs, not the method, but the oracle must run
+them right, and they must be what the paper describes: the block-encoding
+identity <i|<0|<0| U_A |j>|0>|0> = A_ij / ||A||_F (Supp. D), the block of
+U_H(s) equal to H(s) / lambda, U_A^dag undoing U_A, and the walk driving the
+flagged block towards x / ||x|| for x = A^-1 b with an error that shrinks as
+the walk lengthens (Eq. of the discrete adiabatic bound, Sec. III.C).  Every
+expected value here comes from numpy linear algebra on A, independent of the
+oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_15118_gb300 import qlss as Q
+
+
+def _basis(widths, sets):
+    o = oracle.OracleState(widths)
+    for reg, val in sets:
+        for b in range(widths[reg]):
+            if (val >> b) & 1:
+                o.apply(("x", reg, b, ()))
+    return o
+
+
+def test_tree_angles_rebuild_the_vector():
+    """The product of cos / sin factors along each root-to-leaf path of the
+    angle tree is the (signed) entry of the prepared vector."""
+    rng = np.random.default_rng(0)
+    for n in (1, 3, 5):
+        x = rng.standard_normal(1 << n)
+        x[rng.integers(0, 1 << n)] = 0.0
+        x /= np.linalg.norm(x)
+        ang = Q.tree_angles(x)
+        for i in range(1 << n):
+            amp = 1.0
+            for l in range(n):
+                p = i >> (n - l)
+                bit = (i >> (n - 1 - l)) & 1
+                th = ang[l][p]
+                amp *= math.sin(th / 2) if bit else math.cos(th / 2)
+            assert abs(amp - x[i]) < 1e-12
+
+
+def test_angle_codes_round_to_the_grid():
+    th = np.array([0.0, 1e-12, math.pi, 2 * math.pi, -0.5, 4 * math.pi - 1e-12])
+    c = Q.angle_code(th).astype(np.float64) * Q.ANGLE_SCALE
+    d = np.mod(c - np.mod(th, 4 * math.pi) + 2 * math.pi, 4 * math.pi) - 2 * math.pi
+    assert np.abs(d).max() <= Q.ANGLE_SCALE / 2 + 1e-15
+
+
+@pytest.mark.parametrize("N,hb", [(4, 1), (8, 2), (16, 3)])
+def test_block_encoding_identity(N, hb):
+    """<i|<0|<0| U_A |j>|0>|0> = A_ij / ||A||_F (Supp. D), every i, j."""
+    A = Q.spd_banded(N, hb, 6.0, np.random.default_rng(N))
+    n = int(math.log2(N))
+    widths, ids = Q.registers(n)
+    t_l, t_r, nf = Q.tables_for(A)
+    tables = t_l + t_r
+    gates = Q.u_a(n, ids, list(range(n)), list(range(n, 2 * n)), ())
+    off = np.cumsum([0] + widths)
+    got = np.zeros((N, N))
+    for j in range(N):
+        o = _basis(widths, [(Q.TOP, j)])
+        for g in gates:
+            o.apply(g, tables)
+        d = o.to_dict()
+        for i in range(N):
+            got[i, j] = d.get(i << int(off[Q.TOP]), 0).real
+        # U_A^dag U_A = I: the input comes back, keys exactly
+        for g in Q.u_a(n, ids, list(range(n)), list(range(n, 2 * n)), (), dagger=True):
+            o.apply(g, tables)
+        back = o.to_dict()
+        assert set(back) == {j << int(off[Q.TOP])}
+        assert abs(back[j << int(off[Q.TOP])] - 1.0) < 1e-12
+    # 2n rotations, each within half a grid step of its angle
+    assert np.abs(got - A / nf).max() < 4 * n * Q.ANGLE_SCALE
+
+
+@pytest.mark.parametrize("f", [0.0, 0.37, 1.0])
+def test_walk_block_encodes_h_of_s(f):
+    """<0|_anc U_H(s) |0>_anc = H(s) / lambda with H(s) = [[0, A(f) Q_b],
+    [Q_b A(f), 0]] and lambda = (1 - f) + f ||A||_F."""
+    N, n = 4, 2
+    A = Q.spd_banded(N, 1, 4.0, np.random.default_rng(2))
+    widths, ids = Q.registers(n)
+    t_l, t_r, nf = Q.tables_for(A)
+    tables = t_l + t_r
+    gates = Q.u_h(n, ids, list(range(n)), list(range(n, 2 * n)), Q.lcu_angle(f, nf))
+    off = np.cumsum([0] + widths)
+
+    def key(ah, top):
+        return (ah << int(off[ids["AH"]])) | (top << int(off[Q.TOP]))
+
+    got = np.zeros((2 * N, 2 * N), np.complex128)
+    for ah in range(2):
+        for j in range(N):
+            o = _basis(widths, [(ids["AH"], ah), (Q.TOP, j)])
+            for g in gates:
+                o.apply(g, tables)
+            d = o.to_dict()
+            for ah2 in range(2):
+                for i in range(N):
+                    got[ah2 * N + i, ah * N + j] = d.get(key(ah2, i), 0)
+    b = np.full(N, N ** -0.5)
+    Qb = np.eye(N) - np.outer(b, b)
+    Af = (1 - f) * np.eye(N) + f * A
+    H = np.block([[np.zeros((N, N)), Af @ Qb], [Qb @ Af, np.zeros((N, N))]])
+    lam = (1 - f) + f * nf
+    assert np.abs(got - H / lam).max() < 1e-8
+
+
+def test_schedule_end_points_and_monotone():
+    for kappa in (2.0, 10.0, 50.0):
+        s = np.linspace(0, 1, 101)
+        f = np.array([Q.schedule(x, kappa) for x in s])
+        assert abs(f[0]) < 1e-15 and abs(f[-1] - 1) < 1e-12
+        assert np.all(np.diff(f) > 0)
+
+
+def test_walk_converges_to_the_solution():
+    """Sanity of the construction (not parity): the flagged block approaches
+    x / ||x|| and the error falls as the walk lengthens."""
+    errs = []
+    for T in (50, 200, 800):
+        cfg = Q.config4(seed=5, N=4, half_band=2, kappa=5.0, T=T)
+        circ = Q.walk_circuit(cfg)
+        o = oracle.run_circuit(circ)
+        v = Q.solution_block(o.to_dict(), cfg)
+        x = np.linalg.solve(cfg["A"], cfg["b"])
+        x /= np.linalg.norm(x)
+        p = np.vdot(v, v).real
+        errs.append(1 - abs(np.vdot(x, v)) ** 2 / p)
+        assert abs(o.norm2() - 1) < 1e-9
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[1] < 5e-3

@@ -34,7 +34,7 @@ KINDS = ("x", "cx", "ccx", "ry", "cry", "phase", "cphase", "h", "ch", "u1q", "cu
          "adiag", "add", "sub", "swap")
 
 
-@pytest.mark.parametrize("widths,seed", [([5, 5, 6], 11), ([8, 8, 8], 12), ([20, 32, 32], 13),
+@pytest.mark.parametrize("widths,seed", [([5, 5, 6], 11), ([6, 6, 6], 12), ([20, 32, 32], 13),
                                          ([16, 16, 16, 16], 14)])
 @pytest.mark.parametrize("amp32", [False, True])
 def test_sort_and_bucket_states_bit_identical(sqs, widths, seed, amp32):
