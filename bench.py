@@ -223,6 +223,39 @@ def variants(circ, widths, stream, probs, norm, flush, args, st64):
 BENCH_UNITS = [0]
 
 
+def qlss_workloads(stream, flush, args):
+    """Updates/s of the linear-system walk (one system, N = 1024) and of the
+    batched walk (256 systems of sizes 8..128), a few walk steps each."""
+    from paper_2503_15118_gb300 import qlss, sqs
+    out = {}
+    cfg4 = W.config4(seed=4)
+    cfg5 = qlss.config5(seed=5)
+    for name, circ, hint in (
+            ("qlss_walk_N1024_4steps", qlss.walk_circuit(cfg4, n_steps=4), 1 << 23),
+            ("qlss_batch256_2steps", qlss.batched_circuit(cfg5, 2), 1 << 23)):
+        st = sqs.State(circ["widths"], capacity_hint=hint, stream=stream.cuda_stream,
+                       eps=circ["eps"])
+
+        def step():
+            st.reset()
+            st.run(circ)
+
+        for _ in range(args.warmup):
+            step()
+        st.sync()
+        st.reset()
+        units = 0
+        for g in circ["gates"]:
+            units += st.nnz()
+            st.apply(g, circ["tables"])
+        ms = _timed_steps(st, step, flush, stream, max(3, args.steps // 2))
+        out[name] = {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                     "units_per_step": units, "gates": len(circ["gates"]),
+                     "peak_nnz": st.peak_nnz(), "key_words": st.kw}
+        st.close()
+    return out
+
+
 def run_reference(args, rank):
     if rank != 0:
         return 0
@@ -417,6 +450,7 @@ def main():
     }
     if not args.no_variants:
         line["variants"] = variants(circ, widths, stream, probs, norm, flush, args, st)
+        line["variants"].update(qlss_workloads(stream, flush, args))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, _ = cpu_baseline(circ)
         line["cpu_baseline"] = cb

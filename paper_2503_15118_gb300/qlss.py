@@ -270,3 +270,172 @@ def solution_block(state, cfg):
             continue
         v[(k >> top_off) & ((1 << n) - 1)] = a
     return v
+
+
+# ---- batched instances (config 5) ------------------------------------------
+#
+# Many independent systems share one state: an instance register INST (never
+# acted on) selects the system, every instance-dependent quantity is a QRAM
+# table indexed by INST, and instance i of size N_i = 2^{n_i} <= 2^n lives in
+# the low n_i bits of TOP and BOT (the higher bits stay 0: levels of the angle
+# trees above n_i carry angle 0, the identity).  A step register STEP counts
+# walk steps (one "add" per step), so that the gates of every walk step are
+# the same list and only the counter selects the schedule value f_i(s).
+
+def batched_registers(n, inst_bits, step_bits):
+    widths = [n, n, inst_bits, step_bits]
+    ids = {"BOT": 0, "TOP": 1, "INST": 2, "STEP": 3}
+    for name, w in (("C", 1), ("A2", 1), ("AH", 1), ("Q", ANGLE_BITS)):
+        ids[name] = len(widths)
+        widths.append(w)
+    return widths, ids
+
+
+def batched_tables(mats, n, inst_bits):
+    """Per-level U_L tables (address BOT, TOP, INST) and U_R tables (address
+    TOP, INST) for the instance matrices mats[i] (sizes 2^{n_i} <= 2^n)."""
+    N = 1 << n
+    n_inst = 1 << inst_bits
+    tl = [np.zeros(n_inst * N * N, np.uint32) for _ in range(n)]
+    tr = [np.zeros(n_inst * N, np.uint32) for _ in range(n)]
+    norms = np.zeros(n_inst)
+    m = np.arange(N, dtype=np.int64)
+    for i, A in enumerate(mats):
+        Ni = A.shape[0]
+        ni = int(round(math.log2(Ni)))
+        col = np.linalg.norm(A, axis=0)
+        norms[i] = float(np.linalg.norm(A))
+        for l in range(n):
+            b = n - 1 - l  # the rotated qubit of global level l
+            if b >= ni:
+                continue  # above the instance's size: identity
+            li = ni - 1 - b  # the instance's own level
+            for k in range(Ni):
+                if col[k] == 0.0:
+                    continue
+                ang = tree_angles(A[:, k] / col[k])
+                base = (i * N + k) * N
+                tl[l][base: base + N] = angle_code(ang[li])[(m >> (b + 1)) & ((1 << li) - 1)]
+            ang = tree_angles(col / norms[i])
+            tr[l][i * N: (i + 1) * N] = angle_code(ang[li])[(m >> (b + 1)) & ((1 << li) - 1)]
+    return tl, tr, norms
+
+
+def config5(seed=5, n_inst=256, n_min=3, n_max=7, kappa=(10.0, 50.0, 100.0), T=2000,
+            max_half_band=16):
+    """Batched linear-system walks: n_inst seeded SPD banded systems of sizes
+    2^{U[n_min, n_max]}, half-bandwidths U{1 .. min(16, N/4)} and condition
+    numbers drawn from `kappa`, all walked at once in one state."""
+    rng = np.random.default_rng(seed)
+    inst_bits = max(1, int(math.ceil(math.log2(n_inst))))
+    step_bits = max(1, int(math.ceil(math.log2(T + 1))))
+    n = n_max
+    widths, ids = batched_registers(n, inst_bits, step_bits)
+    mats, sizes, kap, hbs = [], [], [], []
+    for _ in range(n_inst):
+        ni = int(rng.integers(n_min, n_max + 1))
+        Ni = 1 << ni
+        hb = int(rng.integers(1, max(1, min(max_half_band, Ni // 4)) + 1))
+        k = float(kappa[int(rng.integers(0, len(kappa)))])
+        mats.append(spd_banded(Ni, hb, k, rng))
+        sizes.append(Ni), kap.append(k), hbs.append(hb)
+    tl, tr, norms = batched_tables(mats, n, inst_bits)
+    # LCU angle of A(f) per (step, instance): address (INST, STEP).
+    tf = np.zeros((1 << step_bits) << inst_bits, np.uint32)
+    for mstep in range(T):
+        s = mstep / T
+        th = [lcu_angle(schedule(s, kap[i]), norms[i]) for i in range(n_inst)]
+        tf[(mstep << inst_bits) + np.arange(n_inst)] = angle_code(th)
+    # U_b: RY(pi / 2) on the instance's own TOP qubits, identity above.
+    tb = [np.zeros(1 << inst_bits, np.uint32) for _ in range(n)]
+    for b in range(n):
+        tb[b][:n_inst] = angle_code([math.pi / 2 if b < int(math.log2(sizes[i])) else 0.0
+                                     for i in range(n_inst)])
+    tables = tl + tr + [tf] + tb
+    cfg = {"widths": widths, "ids": ids, "n": n, "inst_bits": inst_bits, "step_bits": step_bits,
+           "eps": 1e-14, "tables": tables, "t_l": list(range(n)),
+           "t_r": list(range(n, 2 * n)), "t_f": 2 * n, "t_b": list(range(2 * n + 1, 3 * n + 1)),
+           "mats": mats, "sizes": sizes, "kappa": kap, "half_band": hbs, "norms": norms,
+           "n_inst": n_inst, "T": T, "name": f"qlss-batch{n_inst}-T{T}"}
+    return cfg
+
+
+def _batched_ub(cfg, dagger, ctrls):
+    """U_b (or its inverse) with per-instance angles."""
+    ids, n = cfg["ids"], cfg["n"]
+    Qr, INST = ids["Q"], ids["INST"]
+    sc = -ANGLE_SCALE if dagger else ANGLE_SCALE
+    g = []
+    for b in range(n):
+        t = cfg["t_b"][b]
+        g += [("qload", INST, Qr, t), ("ry_reg", TOP, b, Qr, sc, 0.0, tuple(ctrls)),
+              ("qunload", INST, Qr, t)]
+    return g
+
+
+def batched_prep(cfg):
+    """Uniform superposition over the instances, then |b_i> on every instance."""
+    g = [("h", cfg["ids"]["INST"], b, ()) for b in range(cfg["inst_bits"])]
+    return g + _batched_ub(cfg, False, ())
+
+
+def _batched_uq(cfg, ctrls):
+    ids, n = cfg["ids"], cfg["n"]
+    A2 = ids["A2"]
+    pred = ((A2, 0, 1),) + tuple((TOP, b, 0) for b in range(n)) + tuple(ctrls)
+    return ([("h", A2, 0, ())] + _batched_ub(cfg, True, ()) + [("phase", pred, math.pi)]
+            + _batched_ub(cfg, False, ()) + [("h", A2, 0, ())])
+
+
+def batched_walk_step(cfg):
+    """One walk step for every instance; identical for every step (the STEP
+    register selects the schedule value and is incremented at the end)."""
+    ids, n = cfg["ids"], cfg["n"]
+    INST, STEP, C, Qr, AH = ids["INST"], ids["STEP"], ids["C"], ids["Q"], ids["AH"]
+    span_l, span_r = 3, 2  # (BOT, TOP, INST) and (TOP, INST)
+
+    def theta_gate(dagger, c):
+        sc = -ANGLE_SCALE if dagger else ANGLE_SCALE
+        return [("qload", (INST, 2), Qr, cfg["t_f"]), ("ry_reg", C, 0, Qr, sc, 0.0, c),
+                ("qunload", (INST, 2), Qr, cfg["t_f"])]
+
+    on, off = ((AH, 0, 1),), ((AH, 0, 0),)
+    kw = {"span_l": span_l, "span_r": span_r}
+    g = (_batched_uq(cfg, on)
+         + u_af(n, ids, cfg["t_l"], cfg["t_r"], None, off, dagger=True, theta_gate=theta_gate,
+                **kw)
+         + u_af(n, ids, cfg["t_l"], cfg["t_r"], None, on, dagger=False, theta_gate=theta_gate,
+                **kw)
+         + _batched_uq(cfg, off)
+         + [("x", AH, 0, ())])
+    return g + reflection(n, ids) + [("add", STEP, -1, 1, ())]
+
+
+def batched_circuit(cfg, n_steps):
+    step = batched_walk_step(cfg)
+    gates = batched_prep(cfg)
+    for _ in range(n_steps):
+        gates += step
+    return {"widths": cfg["widths"], "eps": cfg["eps"], "tables": cfg["tables"],
+            "gates": gates, "name": cfg["name"]}
+
+
+def instance_block(state, cfg, i):
+    """Flagged block of instance i: amplitudes of |0>_AH |j>_TOP |i>_INST with
+    every ancilla 0 (any step count), over j < N_i."""
+    ids = cfg["ids"]
+    off = np.cumsum([0] + cfg["widths"])
+    Ni = cfg["sizes"][i]
+    mask_keep = (((1 << cfg["n"]) - 1) << int(off[TOP])) | \
+        (((1 << cfg["inst_bits"]) - 1) << int(off[ids["INST"]])) | \
+        (((1 << cfg["step_bits"]) - 1) << int(off[ids["STEP"]]))
+    v = np.zeros(Ni, np.complex128)
+    for k, a in state.items():
+        if k & ~mask_keep:
+            continue
+        if (k >> int(off[ids["INST"]])) & ((1 << cfg["inst_bits"]) - 1) != i:
+            continue
+        j = (k >> int(off[TOP])) & ((1 << cfg["n"]) - 1)
+        if j < Ni:
+            v[j] = a
+    return v

@@ -95,3 +95,44 @@ def test_full_size_walk_steps_keep_norm_and_fp32_fidelity(sqs, full):
     ov = sum(np.conj(v) * d32.get(k, 0) for k, v in d64.items())
     n32 = sum(abs(v) ** 2 for v in d32.values())
     assert abs(ov) ** 2 / (n2 * n32) >= 1 - 1e-6
+
+
+@pytest.mark.parametrize("amp32", [False, True])
+def test_small_batch_matches_oracle(sqs, amp32):
+    cfg = Q.config5(seed=9, n_inst=8, n_min=2, n_max=3, T=10)
+    circ = Q.batched_circuit(cfg, 10)
+    o = oracle.run_circuit(circ)
+    g = sqs.run_circuit(circ, amp32=amp32)
+    got, ref = g.to_dict(), o.to_dict()
+    if amp32:
+        assert compare_states(got, ref, atol=1e-5, band=1e-5) >= 1 - 1e-6
+    else:
+        assert compare_states(got, ref, eps=1e-14, atol=1e-12) >= 1 - 1e-10
+        assert g.peak_nnz() == o.peak()
+
+
+def test_full_batch_instances(sqs):
+    """256 instances of sizes 8..128: every instance keeps its share of the
+    norm, and small instances equal their walk alone on the oracle."""
+    cfg = Q.config5()
+    steps = 2
+    g = sqs.run_circuit(Q.batched_circuit(cfg, steps))
+    lo, hi, amps = g.export()
+    off = np.cumsum([0] + cfg["widths"])
+    sh, m = int(off[cfg["ids"]["INST"]]), (1 << cfg["inst_bits"]) - 1
+    inst = (lo >> np.uint64(sh)) & np.uint64(m)
+    p = np.bincount(inst.astype(np.int64), weights=np.abs(amps) ** 2, minlength=cfg["n_inst"])
+    assert np.abs(p - 1.0 / cfg["n_inst"]).max() < 1e-10
+    small = [i for i in range(cfg["n_inst"]) if cfg["sizes"][i] <= 16][:3]
+    assert small
+    scale = 2.0 ** (-cfg["inst_bits"] / 2)
+    for i in small:
+        circ = Q.batched_circuit(cfg, steps)
+        ib = cfg["inst_bits"]
+        pre = [("x", cfg["ids"]["INST"], b, ()) for b in range(ib) if (i >> b) & 1]
+        alone = oracle.run_circuit(dict(circ, gates=pre + circ["gates"][ib:])).to_dict()
+        sel = inst == i
+        part = {(int(h) << 64) | int(l): complex(a)
+                for l, h, a in zip(lo[sel], hi[sel], amps[sel])}
+        assert set(part) == set(alone)
+        assert max(abs(part[k] - scale * alone[k]) for k in part) < 1e-12

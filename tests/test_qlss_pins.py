@@ -138,3 +138,62 @@ def test_walk_converges_to_the_solution():
         assert abs(o.norm2() - 1) < 1e-9
     assert errs[0] > errs[1] > errs[2]
     assert errs[1] < 5e-3
+
+
+def _single_instance_circuit(cfg, i, n_steps):
+    """Instance i alone: INST preset to i instead of the superposition."""
+    circ = Q.batched_circuit(cfg, n_steps)
+    ib = cfg["inst_bits"]
+    pre = [("x", cfg["ids"]["INST"], b, ()) for b in range(ib) if (i >> b) & 1]
+    gates = pre + [g for g in circ["gates"][ib:]]  # drop the H on INST
+    return dict(circ, gates=gates)
+
+
+def test_batched_instances_are_independent():
+    """The batched state restricted to instance i is 2^{-inst_bits/2} times
+    the state of instance i walked alone (nothing acts on INST)."""
+    cfg = Q.config5(seed=7, n_inst=4, n_min=2, n_max=3, T=6)
+    o = oracle.run_circuit(Q.batched_circuit(cfg, 6))
+    d = o.to_dict()
+    off = np.cumsum([0] + cfg["widths"])
+    sh, m = int(off[cfg["ids"]["INST"]]), (1 << cfg["inst_bits"]) - 1
+    scale = 2.0 ** (-cfg["inst_bits"] / 2)
+    for i in range(cfg["n_inst"]):
+        alone = oracle.run_circuit(_single_instance_circuit(cfg, i, 6)).to_dict()
+        part = {k: v for k, v in d.items() if (k >> sh) & m == i}
+        assert set(part) == set(alone)
+        assert max(abs(part[k] - scale * alone[k]) for k in part) < 1e-12
+
+
+def test_batched_block_encoding_per_instance():
+    """Each instance's block of the batched U_A is its own A_i / ||A_i||_F,
+    whatever its size below the register width."""
+    cfg = Q.config5(seed=8, n_inst=4, n_min=2, n_max=4, T=4)
+    n, ids = cfg["n"], cfg["ids"]
+    off = np.cumsum([0] + cfg["widths"])
+    fwd = Q.u_a(n, ids, cfg["t_l"], cfg["t_r"], (), span_l=3, span_r=2)
+    for i in range(cfg["n_inst"]):
+        A, nf = cfg["mats"][i], cfg["norms"][i]
+        N = A.shape[0]
+        for j in range(N):
+            o = _basis(cfg["widths"], [(ids["INST"], i), (Q.TOP, j)])
+            for g in fwd:
+                o.apply(g, cfg["tables"])
+            d = o.to_dict()
+            base = i << int(off[ids["INST"]])
+            col = np.array([d.get(base | (r << int(off[Q.TOP])), 0).real for r in range(N)])
+            assert np.abs(col - A[:, j] / nf).max() < 4 * n * Q.ANGLE_SCALE
+
+
+def test_batched_walk_converges_per_instance():
+    cfg = Q.config5(seed=5, n_inst=4, n_min=2, n_max=3, kappa=(5.0,), T=150)
+    o = oracle.run_circuit(Q.batched_circuit(cfg, 150))
+    d = o.to_dict()
+    assert abs(o.norm2() - 1) < 1e-9
+    for i in range(cfg["n_inst"]):
+        v = Q.instance_block(d, cfg, i)
+        A = cfg["mats"][i]
+        N = A.shape[0]
+        x = np.linalg.solve(A, np.full(N, N ** -0.5))
+        x /= np.linalg.norm(x)
+        assert abs(np.vdot(x, v)) ** 2 / np.vdot(v, v).real > 0.99
