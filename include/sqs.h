@@ -74,6 +74,12 @@ typedef enum {
                                      Both give bit-identical states.  A step
                                      whose target bit is known constant always
                                      takes the expansion path (no merge).     */
+#define SQS_MERGE_PLAIN 64u       /* disable the host-proven shortcuts: the
+                                     constant-bit expansion and the copy-pair
+                                     fold (a target whose every partner is
+                                     known to hold +-1 times the branch's
+                                     amplitude).  Results are bit-identical
+                                     either way; this flag exists to show it. */
 
 /*
  * One control (or predicate) qubit: bit `bit` of register `reg` must equal
@@ -274,6 +280,7 @@ uint64_t sqs_launch_count(const sqs_state* st);
 #define SQS_K_PAIR_CLUSTER 9u /* cluster merge: pairing in a thread-block cluster */
 #define SQS_K_SORT 10u      /* radix-sort merge: one LSD pass (histogram, scan, scatter) */
 #define SQS_K_SORT_MERGE 11u /* radix-sort merge: neighbours combined, 2x2, prune */
+#define SQS_K_FOLD 12u      /* copy-pair fold: both children from one member   */
 typedef struct {
   uint32_t kernel; /* SQS_K_*                          */
   uint32_t call;   /* API call index since enabling     */
@@ -348,6 +355,7 @@ typedef struct {
   uint64_t steps_hash;       /*   per-CTA bucket merge                         */
   uint64_t steps_sort;       /*   radix-sort merge                             */
   uint64_t steps_cluster;    /*   binned cluster merge                         */
+  uint64_t steps_fold;       /*   copy-pair fold                               */
 } sqs_stats;
 sqs_status sqs_state_stats(const sqs_state* st, sqs_stats* out);
 

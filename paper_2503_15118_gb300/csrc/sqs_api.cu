@@ -127,6 +127,10 @@ struct sqs_state {
   std::vector<uint32_t> writes_since, reads_since;  // operations since that step
   std::vector<uint8_t> arith_since;  // the bit's register was an arithmetic destination since
   std::vector<int8_t> const_val;     // value when the bit is known constant, else -1
+  // +1 / -1 when every branch's partner across the bit is known to exist with
+  // exactly +1 / -1 times its amplitude (set by an uncontrolled expansion with
+  // U[1][b] = +-U[0][b], kept while nothing reads or writes the bit), else 0.
+  std::vector<int8_t> pair_sign;
   int64_t n_branch = 0;
   int64_t last_target = -1;
 
@@ -330,6 +334,16 @@ sqs_status sync_ctl(sqs_state* st, bool report_only = false) {
   return SQS_OK;
 }
 
+// Replaces the count bound by the exact count, mid-step.  Inside a learned-
+// sizing flush a pending bucket overflow must reach the flush, which rolls
+// back and replays; anywhere else a device error is sticky.
+sqs_status sync_bound(sqs_state* st) {
+  sqs_status s = sync_ctl(st, true);
+  if (s == SQS_OK) return s;
+  if (st->defer_frees && (st->ctl_host->err & ~sqs::kErrBucket) == 0) return s;
+  return sync_ctl(st);
+}
+
 sqs_status check_usable(sqs_state* st) {
   if (!st) return SQS_ERR_ARG;
   return st->sticky;
@@ -475,27 +489,33 @@ sqs_status densify(sqs_state* st);
 // in one pass (the constant-bit path of the merge).
 sqs_status run_expand(sqs_state* st, const Gate1& g, int64_t rec_idx) {
   const OpList& L = st->ops_buf;
-  constexpr uint32_t kChunkLog2 = 12;  // chunk of input slots per output segment
-  // Expansion doubles the slots of the layout; a sparse segmented state is
-  // packed densely first so that slots track branches, not capacity.
-  if (st->cur.segmented && st->cur.slots(st->ub) > 4 * std::max<uint64_t>(st->ub, 4096)) {
-    sqs_status s = densify(st);
-    if (s != SQS_OK) return st->sticky = s;
+  constexpr uint32_t kChunkLog2 = 12;  // input slots per chunk of the kernel
+  // Output bound: an expansion at most doubles the branches, a fold keeps
+  // their number (each pair's two members become its two children).
+  auto out_bound = [&] {
+    return g.fold_sign ? st->ub : std::min(max_branches(st), 2 * st->ub);
+  };
+  uint64_t need = std::max<uint64_t>(out_bound(), 1);
+  if (need > st->alt.cap && st->ub > 1) {
+    sqs_status s = sync_bound(st);  // the bound outgrew the allocation: exact count
+    if (s != SQS_OK) return s;
+    need = std::max<uint64_t>(out_bound(), 1);
   }
   const uint64_t in_slots = st->cur.slots(st->ub);
-  const uint64_t nseg = std::max<uint64_t>(1, (in_slots + (1ull << kChunkLog2) - 1) >> kChunkLog2);
-  if (nseg > 0xffffffffull) return st->sticky = fail(st, SQS_ERR_CAPACITY, "state too large");
-  const uint64_t need = nseg << (kChunkLog2 + 1);
+  const uint64_t chunks =
+      st->cur.segmented
+          ? std::max<uint64_t>(1, (uint64_t)st->cur.n_seg << (st->cur.seg_log2 - kChunkLog2))
+          : std::max<uint64_t>(1, (st->ub + (1ull << kChunkLog2) - 1) >> kChunkLog2);
   if (st->alt.cap < need && !ensure_store(st, st->alt, need))
     return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate %llu branches",
                              (unsigned long long)need);
-  st->alt.set_segments(kChunkLog2 + 1, (uint32_t)nseg);
+  st->alt.set_dense();
   const int out_slot = (st->cur_slot + 1) & 3;
   cudaError_t e;
   {
-    Traced tr(st, SQS_K_EXPAND);
+    Traced tr(st, g.fold_sign ? SQS_K_FOLD : SQS_K_EXPAND);
     e = sqs::launch_expand(launch_of(st, in_slots), st->kw, st->amp32, st->ctl, st->cur.view(),
-                           st->cur_slot, L, g, st->alt.view(), out_slot);
+                           st->cur_slot, chunks, L, g, st->alt.view(), out_slot);
   }
   if (e != cudaSuccess) return cuda_fail(st, e, "expand launch");
   if (rec_idx >= 0) {
@@ -505,7 +525,7 @@ sqs_status run_expand(sqs_state* st, const Gate1& g, int64_t rec_idx) {
   }
   std::swap(st->cur, st->alt);
   st->cur_slot = out_slot;
-  st->ub = std::min(max_branches(st), 2 * st->ub);
+  st->ub = out_bound();
   return SQS_OK;
 }
 
@@ -661,7 +681,7 @@ sqs_status run_sorted(sqs_state* st, const Gate1& g, int64_t rec_idx) {
     const uint64_t c = 1ull << sqs::sort_merge_chunk_log2();
     const uint64_t out_need = std::max<uint64_t>(1, (st->ub + c - 1) / c) * 2 * c;
     if (st->ub > 1 && (st->bk.cap < st->ub || st->alt.cap < std::max(out_need, st->ub))) {
-      sqs_status s = sync_ctl(st);
+      sqs_status s = sync_bound(st);
       if (s != SQS_OK) return s;
     }
   }
@@ -776,8 +796,9 @@ sqs_status run_branching(sqs_state* st, const Gate1& g, double est_in = -1.0,
                          int64_t rec_idx = -1) {
   sqs_status s = run_pending(st, true);  // leaves the fused tail in ops_buf
   if (s != SQS_OK) return st->sticky = s;
-  if (g.no_partners) {
-    st->stats.steps_expand++;
+  if (g.no_partners || g.fold_sign) {
+    if (g.fold_sign) st->stats.steps_fold++;
+    else st->stats.steps_expand++;
     return run_expand(st, g, rec_idx);
   }
   const bool sort_ok = st->ub < (1ull << 31) && !(st->flags & SQS_MERGE_CLUSTER);
@@ -821,6 +842,7 @@ void history_reset(sqs_state* st, bool known_zero) {
   st->reads_since.assign(n, 0);
   st->arith_since.assign(n, 0);
   st->const_val.assign(n, known_zero ? 0 : -1);
+  st->pair_sign.assign(n, 0);
   st->n_branch = 0;
   st->last_target = -1;
 }
@@ -860,6 +882,37 @@ void note_field_read(sqs_state* st, uint32_t off, uint32_t w) {
 void note_op(sqs_state* st, const HostOp& h) {
   const DevOp& d = h.d;
   for_bits(d.pmask, st->total_bits, [&](uint32_t q) { st->reads_since[q]++; });
+  // Any bit the operation reads or writes loses its copy-pair property.
+  {
+    auto clear = [&](uint32_t q) {
+      if (q < st->total_bits) st->pair_sign[q] = 0;
+    };
+    for_bits(d.pmask, st->total_bits, clear);
+    switch (d.kind) {
+      case sqs::OP_XOR:
+        for_bits(d.xmask, st->total_bits, clear);
+        break;
+      case sqs::OP_MUL_XOR:
+        for_bits(d.xmask, st->total_bits, clear);
+        clear(d.sel_bit);
+        break;
+      case sqs::OP_MUL:
+        clear(d.sel_bit);
+        break;
+      case sqs::OP_ADD_CONST:
+        for (uint32_t b = 0; b < d.dst_w; ++b) clear(d.dst_off + b);
+        break;
+      case sqs::OP_ADD_REG:
+      case sqs::OP_SUB_REG:
+      case sqs::OP_SWAP:
+      case sqs::OP_QRAM:
+        for (uint32_t b = 0; b < d.dst_w; ++b) clear(d.dst_off + b);
+        for (uint32_t b = 0; b < d.src_w; ++b) clear(d.src_off + b);
+        break;
+      default:
+        break;
+    }
+  }
   switch (d.kind) {
     case sqs::OP_XOR:
     case sqs::OP_MUL_XOR: {
@@ -932,7 +985,13 @@ void features(const sqs_state* st, const Gate1& g, uint32_t n_ctrl, float* x) {
 }
 
 void note_branch(sqs_state* st, const Gate1& g) {
-  for_bits(g.cmask, st->total_bits, [&](uint32_t q) { st->reads_since[q]++; });
+  for_bits(g.cmask, st->total_bits, [&](uint32_t q) {
+    st->reads_since[q]++;
+    st->pair_sign[q] = 0;
+  });
+  if (g.mode == 1)
+    for (uint32_t b = 0; b < g.ang_w; ++b)
+      if (g.ang_off + b < st->total_bits) st->pair_sign[g.ang_off + b] = 0;
   const uint32_t t = g.t;
   st->last_branch[t] = st->n_branch++;
   st->writes_since[t] = st->reads_since[t] = 0;
@@ -946,12 +1005,50 @@ sqs_status issue_branching(sqs_state* st, const Gate1& g_in, uint32_t n_ctrl) {
   float x[SQS_PRED_FEATURES];
   Gate1 g = g_in;
   features(st, g, n_ctrl, x);
-  // A target bit known constant over the whole state has no partner anywhere.
-  g.no_partners = (st->const_val[g.t] >= 0) ? 1u : 0u;
+  // Host-proven shortcuts (off under SQS_MERGE_PLAIN): a target bit known
+  // constant over the whole state has no partner anywhere; a copy-paired bit
+  // has every partner, holding +-1 times the branch's own amplitude.
+  const bool plain = (st->flags & SQS_MERGE_PLAIN) != 0;
+  const int8_t b0 = st->const_val[g.t];
+  g.no_partners = (!plain && b0 >= 0) ? 1u : 0u;
+  g.fold_sign = plain ? 0 : st->pair_sign[g.t];
+  g.fold_kill = -1;
+  g.fold_tmax = 0;
+  if (g.fold_sign && g.mode == 2 && g.eps > 0.0) {
+    // Child r = (U[r][0] + s U[r][1]) a0 vanishes exactly when U[r][0] = -s U[r][1];
+    // evaluated as fma(U[r][0], a0, round(U[r][1] * s a0)) it is the rounding
+    // error of one product, at most 2^-53 |U[r][0] a0| per component, so it
+    // falls below eps / 2 (and is pruned) while |a0| < eps 2^52 / |U[r][0]|.
+    const double s = (double)g.fold_sign;
+    for (int r = 0; r < 2; ++r) {
+      const double ur0 = g.u[2 * (2 * r)], ur1 = g.u[2 * (2 * r + 1)];
+      // FP32 states flush that residue (below 2^-21 of the summed terms) when
+      // |U[r][0]| <= 1, which every unitary satisfies.
+      if (ur0 == -s * ur1 && ur0 != 0.0 && (!st->amp32 || std::fabs(ur0) <= 1.0)) {
+        const double t = std::ldexp(g.eps, 52) / std::fabs(ur0) * (1.0 - 1e-12);
+        std::memcpy(&g.fold_tmax, &t, 8);
+        g.fold_kill = r;
+        break;
+      }
+    }
+  }
+  // An expansion that always acts (no controls that can fail) with
+  // U[1][b0] = +-U[0][b0] leaves every branch paired with +-1 times itself.
+  int8_t new_sign = 0;
+  if (!plain && b0 >= 0 && g.mode != 1 && predicate_known(st, g.cmask, g.cval) == 1) {
+    // Compared as numbers (0.0 == -0.0): the children U[r][b0] * a then
+    // agree, or agree after a sign flip, in every nonzero component, and a
+    // signed zero sums like an unsigned one.
+    const double* r0 = &g.u[2 * (0 * 2 + b0)];  // U[0][b0] (re, im)
+    const double* r1 = &g.u[2 * (1 * 2 + b0)];  // U[1][b0]
+    if (r0[0] == r1[0] && r0[1] == r1[1]) new_sign = 1;
+    else if (r0[0] == -r1[0] && r0[1] == -r1[1]) new_sign = -1;
+  }
   g.vary[0] = g.vary[1] = 0ull;
   for (uint32_t q = 0; q < st->total_bits; ++q)
     if (st->const_val[q] < 0) g.vary[q >> 6] |= 1ull << (q & 63);
   note_branch(st, g);
+  st->pair_sign[g.t] = new_sign;
   if ((st->flags & SQS_SIZING_LEARNED) && st->predictor) {
     sqs_state::Lazy q;
     q.g = g;
@@ -1205,7 +1302,7 @@ sqs_status sqs_state_create(const uint32_t* reg_widths, uint32_t n_regs, uint32_
                             void* cuda_stream, sqs_state** out) {
   if (!out || !reg_widths || n_regs == 0 || n_regs > 128) return SQS_ERR_ARG;
   if (flags & ~(SQS_AMP_FP32 | SQS_SIZING_LEARNED | SQS_MERGE_HASH | SQS_MERGE_SORT |
-                SQS_MERGE_CLUSTER | SQS_MERGE_TUNED))
+                SQS_MERGE_CLUSTER | SQS_MERGE_TUNED | SQS_MERGE_PLAIN))
     return SQS_ERR_ARG;
   uint32_t total = 0;
   for (uint32_t j = 0; j < n_regs; ++j) {

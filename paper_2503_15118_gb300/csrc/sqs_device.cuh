@@ -71,12 +71,14 @@ __device__ __forceinline__ uint64_t khash(u128 k) {
 // value an FP64 accumulation rounded to the FP32 store would give.
 // Complex product with one product fused into the sum (two instructions per
 // component): one rounding fewer than the host's complex<double> product.
+// The sign sits on an input of the FMA (a negated multiplicand), never on a
+// product, so no separate negation is issued.
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(__fma_rn(a.x, b.x, -__dmul_rn(a.y, b.y)),
+  return make_double2(__fma_rn(-a.y, b.y, __dmul_rn(a.x, b.x)),
                       __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x)));
 }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)),
+  return make_float2(__fmaf_rn(-a.y, b.y, __fmul_rn(a.x, b.x)),
                      __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
 }
 // u * a + p (real u), fused per component.
@@ -85,6 +87,14 @@ __device__ __forceinline__ double2 rfma(double u, double2 a, double2 p) {
 }
 __device__ __forceinline__ float2 rfma(float u, float2 a, float2 p) {
   return make_float2(__fmaf_rn(u, a.x, p.x), __fmaf_rn(u, a.y, p.y));
+}
+// u * a - p (real u), fused per component: the same bits as u * a + (-p),
+// with the sign flip carried by the FMA's addend instead of an instruction.
+__device__ __forceinline__ double2 rfms(double u, double2 a, double2 p) {
+  return make_double2(__fma_rn(u, a.x, -p.x), __fma_rn(u, a.y, -p.y));
+}
+__device__ __forceinline__ float2 rfms(float u, float2 a, float2 p) {
+  return make_float2(__fmaf_rn(u, a.x, -p.x), __fmaf_rn(u, a.y, -p.y));
 }
 // c * a + p (complex c), fused.
 __device__ __forceinline__ double2 cfma(double2 c, double2 a, double2 p) {
@@ -109,10 +119,15 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
   return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
 }
-// Exact negation by the sign bits (no arithmetic instruction).
+// Exact negation by the sign bits, written as an integer XOR in PTX so that
+// it stays an integer instruction and never occupies the FP64 pipe.
+__device__ __forceinline__ double neg_bits(double x) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  asm("xor.b64 %0, %0, 0x8000000000000000;" : "+l"(u));
+  return __longlong_as_double((long long)u);
+}
 __device__ __forceinline__ double2 cneg(double2 a) {
-  return make_double2(__longlong_as_double(__double_as_longlong(a.x) ^ (long long)0x8000000000000000ull),
-                      __longlong_as_double(__double_as_longlong(a.y) ^ (long long)0x8000000000000000ull));
+  return make_double2(neg_bits(a.x), neg_bits(a.y));
 }
 __device__ __forceinline__ float2 cneg(float2 a) {
   return make_float2(__int_as_float(__float_as_int(a.x) ^ (int)0x80000000u),
@@ -136,6 +151,11 @@ __device__ __forceinline__ bool keep_amp(double2 a, double eps, float, double ep
       (unsigned long long)__double_as_longlong(a.y) & 0x7fffffffffffffffull;
   if (ax >= e || ay >= e) return true;
   if ((ax | ay) == 0ull) return e == 0ull;  // exact zero: kept only when eps = 0
+  // Both components below eps/2 (the exponent of a normal eps minus one):
+  // |a|^2 < eps^2 / 2, a removal the FP64 test below would decide the same
+  // way.  Cancellation residues take this exit without FP64 arithmetic.
+  const unsigned long long eh = e > (1ull << 52) ? e - (1ull << 52) : 0ull;
+  if (ax < eh && ay < eh) return false;
   return !(norm2(a) < eps2);
 }
 __device__ __forceinline__ bool keep_amp(float2 a, double, float epsf, double eps2) {
@@ -144,6 +164,8 @@ __device__ __forceinline__ bool keep_amp(float2 a, double, float epsf, double ep
   const unsigned int ay = (unsigned int)__float_as_int(a.y) & 0x7fffffffu;
   if (ax >= e || ay >= e) return true;
   if ((ax | ay) == 0u) return eps2 == 0.0;
+  const unsigned int eh = e > (1u << 23) ? e - (1u << 23) : 0u;  // epsf / 2, as above
+  if (ax < eh && ay < eh) return false;
   return !(norm2(a) < eps2);
 }
 __device__ __forceinline__ void to_amp(double2& out, double2 v) { out = v; }
@@ -256,6 +278,100 @@ __device__ __forceinline__ bool apply_ops(uint32_t n_ops, const DevOp* ops, cons
   return true;
 }
 
+// The same run applied to NI branches at once, operation-major: each
+// operation's descriptor is read from shared memory and dispatched once for
+// the NI branches a thread carries, instead of once per branch.  Per branch
+// the arithmetic and its order are those of apply_ops.  live[q] is cleared
+// for a branch the run prunes; branches already dead are left alone (their
+// QRAM reads are skipped).
+template <int KW, class AT, int NI>
+__device__ __forceinline__ void apply_ops_n(uint32_t n_ops, const DevOp* ops, const AT* tab,
+                                            typename KT<KW>::T (&k)[NI], AT (&a)[NI],
+                                            bool (&live)[NI]) {
+  typedef typename KT<KW>::T K;
+  uint32_t idx[NI];
+#pragma unroll
+  for (int q = 0; q < NI; ++q) idx[q] = 0;
+#pragma unroll 1
+  for (uint32_t o = 0; o < n_ops; ++o) {
+    const DevOp& op = ops[o];
+    const uint32_t kind = op.kind;
+    const K pm = mk<KW>(op.pmask[0], op.pmask[1]);
+    const K pv = mk<KW>(op.pval[0], op.pval[1]);
+    if (kind == OP_XOR) {
+      const K xm = mk<KW>(op.xmask[0], op.xmask[1]);
+#pragma unroll
+      for (int q = 0; q < NI; ++q)
+        if ((k[q] & pm) == pv) k[q] ^= xm;
+    } else if (kind == OP_MUL || kind == OP_MUL_XOR) {
+      const uint32_t sel = op.sel_bit, sh = op.shift;
+      const K xm = kind == OP_MUL_XOR ? mk<KW>(op.xmask[0], op.xmask[1]) : (K)0;
+#pragma unroll
+      for (int q = 0; q < NI; ++q) {
+        if ((k[q] & pm) == pv) {
+          const uint32_t one = sel < 128 ? (uint32_t)((k[q] >> sel) & (K)1) : 0u;
+          idx[q] |= (1u + one) << sh;
+          k[q] ^= xm;
+        }
+      }
+    } else if (kind == OP_ADD_REG || kind == OP_SUB_REG || kind == OP_ADD_CONST) {
+      const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
+      const uint64_t c = op.constant;
+#pragma unroll
+      for (int q = 0; q < NI; ++q) {
+        if ((k[q] & pm) == pv) {
+          const uint64_t d = get_field(k[q], doff, dw);
+          const uint64_t sv = kind == OP_ADD_CONST ? c : get_field(k[q], soff, sw);
+          k[q] = set_field<K>(k[q], doff, dw, kind == OP_SUB_REG ? d - sv : d + sv);
+        }
+      }
+    } else if (kind == OP_TABLE) {
+      const uint32_t base = op.tab_off;
+#pragma unroll
+      for (int q = 0; q < NI; ++q) {
+        if (idx[q]) a[q] = cmul(a[q], tab[base + idx[q]]);
+        idx[q] = 0;
+      }
+    } else if (kind == OP_QRAM) {
+      const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
+      const uint64_t n_ent = op.n_entries;
+      const uint32_t eb = (uint32_t)op.constant;
+      const void* tbl = op.table;
+#pragma unroll
+      for (int q = 0; q < NI; ++q) {
+        if (live[q] && (k[q] & pm) == pv) {
+          const uint64_t addr = get_field(k[q], soff, sw);
+          uint64_t d = 0;
+          if (addr < n_ent) {
+            switch (eb) {
+              case 1: d = __ldg((const uint8_t*)tbl + addr); break;
+              case 2: d = __ldg((const uint16_t*)tbl + addr); break;
+              case 4: d = __ldg((const uint32_t*)tbl + addr); break;
+              default: d = __ldg((const unsigned long long*)tbl + addr); break;
+            }
+          }
+          k[q] = set_field<K>(k[q], doff, dw, get_field(k[q], doff, dw) ^ d);
+        }
+      }
+    } else if (kind == OP_SWAP) {
+      const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
+#pragma unroll
+      for (int q = 0; q < NI; ++q) {
+        if ((k[q] & pm) == pv) {
+          const uint64_t v1 = get_field(k[q], doff, dw);
+          const uint64_t v2 = get_field(k[q], soff, sw);
+          k[q] = set_field<K>(set_field<K>(k[q], doff, dw, v2), soff, sw, v1);
+        }
+      }
+    } else if (kind == OP_PRUNE) {
+      const double eps = op.eps, eps2 = op.eps2;
+#pragma unroll
+      for (int q = 0; q < NI; ++q)
+        if (live[q] && !keep_amp(a[q], eps, (float)eps, eps2)) live[q] = false;
+    }
+  }
+}
+
 // Copies the launch's operations and factor table into shared memory: the
 // per-branch loop then reads them with broadcast shared loads instead of
 // indexed parameter-space loads.
@@ -322,9 +438,11 @@ __device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, b
     }
     if (has0 && has1) {
       const AT p01 = rmul(u01, a1);
-      const AT p11 = same1 ? (neg1 ? cneg(p01) : p01) : rmul(u11, a1);
       o0 = rfma(u00, a0, p01);
-      o1 = rfma(u10, a0, p11);
+      if (same1)
+        o1 = neg1 ? rfms(u10, a0, p01) : rfma(u10, a0, p01);
+      else
+        o1 = rfma(u10, a0, rmul(u11, a1));
       flush_residue(o0, a0, a1);
       flush_residue(o1, a0, a1);
     } else if (has0) {
@@ -353,5 +471,33 @@ __device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, b
     }
   }
 }
+
+// One child of a pair whose both members are present, real coefficients
+// (mode 2): the same expression children() evaluates for it.
+template <class AT>
+__device__ __forceinline__ AT child_real(const Gate1& g, int r, AT a0, AT a1) {
+  typedef typename Coef<AT>::S S;
+  const S u00 = Coef<AT>::r(g, 0), u01 = Coef<AT>::r(g, 1), u10 = Coef<AT>::r(g, 2),
+          u11 = Coef<AT>::r(g, 3);
+  const AT p01 = rmul(u01, a1);
+  AT o;
+  if (r == 0) {
+    o = rfma(u00, a0, p01);
+  } else {
+    const bool same1 = g.reuse & 2u, neg1 = g.reuse & 8u;
+    o = same1 ? (neg1 ? rfms(u10, a0, p01) : rfma(u10, a0, p01)) : rfma(u10, a0, rmul(u11, a1));
+  }
+  flush_residue(o, a0, a1);
+  return o;
+}
+
+// Both components' magnitudes below the bit pattern t (FP64 storage); an
+// FP32 residue is always flushed, so the test passes.
+__device__ __forceinline__ bool below_bits(double2 a, uint64_t t) {
+  return ((unsigned long long)__double_as_longlong(a.x) & 0x7fffffffffffffffull) < t &&
+         ((unsigned long long)__double_as_longlong(a.y) & 0x7fffffffffffffffull) < t;
+}
+__device__ __forceinline__ bool below_bits(float2, uint64_t) { return true; }
+
 
 }  // namespace sqs

@@ -110,6 +110,16 @@ struct Gate1 {            // the interference operation of one merge step
   float epsf;             // eps rounded to FP32
   uint32_t no_partners;   // the target bit is constant over the state: expand only
   uint64_t vary[2];       // key bits not known constant over the state (sort digits)
+  // Copy-pair fold: +1 / -1 when every branch's partner across the target bit
+  // is known to exist with amplitude exactly +1 / -1 times its own; 0 otherwise.
+  int32_t fold_sign;
+  // Fold with real U (mode 2) where child r's coefficient cancels exactly
+  // (U[r][0] = -fold_sign * U[r][1]): that child is the rounding residue of
+  // one product, below eps whenever both components of the branch's
+  // amplitude are below fold_tmax (bit pattern, FP64 states; FP32 states
+  // flush it always).  -1: no child cancels.
+  int32_t fold_kill;
+  uint64_t fold_tmax;
 };
 
 struct Launch {
@@ -159,10 +169,15 @@ cudaError_t launch_rsort_merge(const Launch& L, int kw, bool amp32, Ctl* ctl, Ar
 cudaError_t launch_pair(const Launch& L, int kw, bool amp32, Ctl* ctl, const Gate1& g, Arr bk,
                         Arr out, int out_slot);
 // Interference step whose target bit is constant over the state (no pair can
-// exist): the fused run, then both children of every controlled branch, into
-// output segment c for input chunk c (segments twice the chunk size).
+// exist): the fused run, then both children of every controlled branch,
+// appended to the dense array `out` (count in cnt[out_slot]; input chunks of
+// 2^12 slots, n_chunks of them).  With
+// g.fold_sign set (every pair present with a1 = fold_sign * a0) the bit-0
+// member of each controlled pair emits both children and the bit-1 member
+// nothing: the copy-pair fold, with no partition and no pairing.
 cudaError_t launch_expand(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
-                          const OpList& ops, const Gate1& g, Arr out, int out_slot);
+                          uint64_t n_chunks, const OpList& ops, const Gate1& g, Arr out,
+                          int out_slot);
 cudaError_t launch_probabilities(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr a, int slot,
                                  uint32_t off, uint32_t w, double* probs, double* norm2);
 // Copies a segmented array into a dense one given exclusive segment offsets.

@@ -174,16 +174,18 @@ __global__ void __launch_bounds__(kStreamThreads)
     for (int q = 0; q < kPartILP; ++q) {
       const uint32_t j = q * blockDim.x + threadIdx.x;
       live[q] = j < lim;
+      k[q] = 0;
+      v[q].x = v[q].y = 0;
       if (live[q]) {
         k[q] = ld_key<KW>(in, base + j);
         v[q] = ((const AT*)in.amp)[base + j];
       }
     }
+    apply_ops_n<KW, AT, kPartILP>(ops.n, sops, tab, k, v, live);
     unsigned int pos[kPartILP];
     uint32_t bkt[kPartILP];
 #pragma unroll
     for (int q = 0; q < kPartILP; ++q) {
-      if (live[q]) live[q] = apply_ops<KW, AT>(ops.n, sops, tab, k[q], v[q]);
       if (live[q]) {
         const uint64_t h = khash(k[q] & ~bmask);
         bkt[q] = (uint32_t)(((h >> 32) * (uint64_t)bk.n_seg) >> 32);
@@ -348,17 +350,24 @@ __global__ void __launch_bounds__(kPairThreads)
 // Constant target bit: no branch has a partner, so each controlled branch
 // expands into its two children directly (no partition, no pairing).  The
 // input is walked in chunks of kExpandChunk slots (a dense range, or a slice
-// of one segment); chunk c becomes output segment c, of twice the size.
+// of one segment).
+// Copy-pair fold (g.fold_sign != 0): every controlled branch has its partner,
+// holding fold_sign times its amplitude, so the bit-0 member alone emits the
+// pair's two children and the bit-1 member emits nothing.  The output is
+// dense: each block reserves every round's outputs with one atomic.
 constexpr uint32_t kExpandChunkLog2 = 12;
+
+constexpr int kExpandILP = 4;  // branches per thread per round
 
 template <int KW, class AT>
 __global__ void __launch_bounds__(kStreamThreads)
-    k_expand(Ctl* ctl, Arr in, int in_slot, Arr out, int out_slot,
+    k_expand(Ctl* ctl, Arr in, int in_slot, uint64_t n_chunks, Arr out, int out_slot,
              const __grid_constant__ OpList ops, Gate1 g, uint32_t seq) {
   typedef typename KT<KW>::T K;
   __shared__ AT tab[kTabEntries];
   __shared__ DevOp sops[kMaxOps];
-  __shared__ unsigned int seg_fill;
+  __shared__ unsigned int wtot[kStreamThreads / 32];
+  __shared__ unsigned long long round_base;
   if (ctl->err) return;
   load_ops(ops, sops, tab);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -372,11 +381,10 @@ __global__ void __launch_bounds__(kStreamThreads)
   const K bmask = ((K)1) << g.t;
   const K cmask = mk<KW>(g.cmask[0], g.cmask[1]);
   const K cval = mk<KW>(g.cval[0], g.cval[1]);
-  const unsigned int lane = threadIdx.x & 31u;
+  const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned int lt = (1u << lane) - 1u;
-  for (uint64_t c = blockIdx.x; c < out.n_seg; c += gridDim.x) {
-    if (threadIdx.x == 0) seg_fill = 0;
-    __syncthreads();
+  const uint32_t per_round = kExpandILP * blockDim.x;
+  for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
     uint64_t ibase, cnt;
     if (in.seg_cnt) {
       const uint64_t sg = c >> cps_log2;
@@ -388,54 +396,113 @@ __global__ void __launch_bounds__(kStreamThreads)
       ibase = c << kExpandChunkLog2;
       cnt = ibase >= n_dense ? 0 : (n_dense - ibase < chunk ? n_dense - ibase : chunk);
     }
-    const uint64_t obase = c << out.seg_log2;
-    for (uint64_t r = 0; r < cnt; r += blockDim.x) {
-      bool keep0 = false, keep1 = false;
-      K k0 = 0, k1 = 0;
-      AT o0, o1;
-      if (r + threadIdx.x < cnt) {
-        K k = ld_key<KW>(in, ibase + r + threadIdx.x);
-        AT v = ((const AT*)in.amp)[ibase + r + threadIdx.x];
-        if (apply_ops<KW, AT>(ops.n, sops, tab, k, v)) {
-          if ((k & cmask) != cval) {
-            keep0 = true;
-            k0 = k;
-            o0 = v;
-          } else {
-            const bool kt = (k & bmask) != (K)0;
-            k0 = k & ~bmask;
-            k1 = k | bmask;
-            const uint64_t av = g.mode == 1 ? get_field(k0, g.ang_off, g.ang_w) : 0ull;
-            if (!kt)
-              children<AT>(g, av, true, v, false, v, o0, o1);
-            else
-              children<AT>(g, av, false, v, true, v, o0, o1);
-            keep0 = keep_amp(o0, g.eps, g.epsf, g.eps2);
-            keep1 = keep_amp(o1, g.eps, g.epsf, g.eps2);
-          }
+    for (uint64_t r = 0; r < cnt; r += per_round) {
+      K k[kExpandILP];
+      AT v[kExpandILP];
+      bool live[kExpandILP];
+#pragma unroll
+      for (int q = 0; q < kExpandILP; ++q) {
+        const uint64_t j = r + (uint64_t)q * blockDim.x + threadIdx.x;
+        live[q] = j < cnt;
+        k[q] = 0;
+        v[q].x = v[q].y = 0;
+        if (live[q]) {
+          k[q] = ld_key<KW>(in, ibase + j);
+          v[q] = ((const AT*)in.amp)[ibase + j];
         }
       }
-      const unsigned int b0 = __ballot_sync(0xffffffffu, keep0);
-      const unsigned int b1 = __ballot_sync(0xffffffffu, keep1);
-      const unsigned int tot = __popc(b0) + __popc(b1);
-      unsigned int wbase = 0;
-      if (lane == 0 && tot) wbase = atomicAdd(&seg_fill, tot);
-      wbase = __shfl_sync(0xffffffffu, wbase, 0);
-      if (keep0) {
-        const uint64_t pos = obase + wbase + __popc(b0 & lt);
-        st_key<KW>(out, pos, k0);
-        ((AT*)out.amp)[pos] = o0;
+      apply_ops_n<KW, AT, kExpandILP>(ops.n, sops, tab, k, v, live);
+      K k0[kExpandILP], k1[kExpandILP];
+      AT o0[kExpandILP], o1[kExpandILP];
+      unsigned int b0[kExpandILP], b1[kExpandILP];
+      unsigned int wsum = 0;
+#pragma unroll
+      for (int q = 0; q < kExpandILP; ++q) {
+        bool keep0 = false, keep1 = false;
+        k0[q] = k1[q] = 0;
+        if (live[q]) {
+          if ((k[q] & cmask) != cval) {
+            keep0 = true;  // controls not met: the branch is unchanged
+            k0[q] = k[q];
+            o0[q] = v[q];
+          } else {
+            const bool kt = (k[q] & bmask) != (K)0;
+            k0[q] = k[q] & ~bmask;
+            k1[q] = k[q] | bmask;
+            const uint64_t av = g.mode == 1 ? get_field(k0[q], g.ang_off, g.ang_w) : 0ull;
+            if (g.fold_sign == 0) {
+              if (!kt)
+                children<AT>(g, av, true, v[q], false, v[q], o0[q], o1[q]);
+              else
+                children<AT>(g, av, false, v[q], true, v[q], o0[q], o1[q]);
+              keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
+              keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
+            } else if (!kt) {
+              // The partner holds exactly fold_sign * v: the pair's 2x2 as the
+              // merge evaluates it, without looking the partner up.
+              auto fold = [&](const AT& a1) {
+                if (g.fold_kill >= 0 && below_bits(v[q], g.fold_tmax)) {
+                  // The cancelling child is a residue the merge would prune.
+                  if (g.fold_kill == 1) {
+                    o0[q] = child_real<AT>(g, 0, v[q], a1);
+                    keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
+                  } else {
+                    o1[q] = child_real<AT>(g, 1, v[q], a1);
+                    keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
+                  }
+                } else {
+                  children<AT>(g, av, true, v[q], true, a1, o0[q], o1[q]);
+                  keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
+                  keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
+                }
+              };
+              if (g.fold_sign > 0)
+                fold(v[q]);
+              else
+                fold(cneg(v[q]));
+            }
+          }
+        }
+        b0[q] = __ballot_sync(0xffffffffu, keep0);
+        b1[q] = __ballot_sync(0xffffffffu, keep1);
+        wsum += __popc(b0[q]) + __popc(b1[q]);
       }
-      if (keep1) {
-        const uint64_t pos = obase + wbase + __popc(b0) + __popc(b1 & lt);
-        st_key<KW>(out, pos, k1);
-        ((AT*)out.amp)[pos] = o1;
+      // Dense output: the block reserves the round's outputs with one atomic
+      // on the output count; each warp writes its items in (item, lane) order.
+      if (lane == 0) wtot[warp] = wsum;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned int sum = 0;
+        for (unsigned int w = 0; w < blockDim.x / 32u; ++w) {
+          const unsigned int t = wtot[w];
+          wtot[w] = sum;
+          sum += t;
+        }
+        round_base = sum ? atomicAdd(&ctl->cnt[out_slot], (unsigned long long)sum) : 0ull;
+        if (sum && round_base + sum > out.cap)
+          raise_err(ctl, kErrCapacity, seq, round_base + sum);
       }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      out.seg_cnt[c] = seg_fill;
-      if (seg_fill) atomicAdd(&ctl->cnt[out_slot], (unsigned long long)seg_fill);
+      __syncthreads();
+      uint64_t wb = round_base + wtot[warp];
+#pragma unroll
+      for (int q = 0; q < kExpandILP; ++q) {
+        if ((b0[q] >> lane) & 1u) {
+          const uint64_t pos = wb + __popc(b0[q] & lt);
+          if (pos < out.cap) {
+            st_key<KW>(out, pos, k0[q]);
+            ((AT*)out.amp)[pos] = o0[q];
+          }
+        }
+        if ((b1[q] >> lane) & 1u) {
+          const uint64_t pos = wb + __popc(b0[q]) + __popc(b1[q] & lt);
+          if (pos < out.cap) {
+            st_key<KW>(out, pos, k1[q]);
+            ((AT*)out.amp)[pos] = o1[q];
+          }
+        }
+        wb += __popc(b0[q]) + __popc(b1[q]);
+      }
+      __syncthreads();  // wtot and round_base are reused by the next round
     }
   }
 }
@@ -991,12 +1058,13 @@ cudaError_t launch_apply_compact(const Launch& L, int kw, bool amp32, Ctl* ctl, 
 }
 
 cudaError_t launch_expand(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
-                          const OpList& ops, const Gate1& g, Arr out, int out_slot) {
-  uint64_t grid = out.n_seg < 1 ? 1 : out.n_seg;
+                          uint64_t n_chunks, const OpList& ops, const Gate1& g, Arr out,
+                          int out_slot) {
+  uint64_t grid = n_chunks < 1 ? 1 : n_chunks;
   if (grid > (uint64_t)L.sm_count * 8) grid = (uint64_t)L.sm_count * 8;
-#define SQS_EX(KW_, AT_)                                                                 \
-  k_expand<KW_, AT_><<<(int)grid, kStreamThreads, 0, L.stream>>>(ctl, in, in_slot, out, \
-                                                                 out_slot, ops, g, L.seq)
+#define SQS_EX(KW_, AT_)                                                                  \
+  k_expand<KW_, AT_><<<(int)grid, kStreamThreads, 0, L.stream>>>(ctl, in, in_slot, n_chunks, \
+                                                                 out, out_slot, ops, g, L.seq)
   SQS_DISPATCH(kw, amp32, SQS_EX);
 #undef SQS_EX
   return cudaGetLastError();

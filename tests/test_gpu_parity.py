@@ -385,3 +385,50 @@ def test_standalone_compaction_after_wide_segments(sqs, merge, last, then):
     got, ref = g.to_dict(), o.to_dict()
     assert set(got) == set(ref)
     assert compare_states(got, ref) > 1 - 1e-12
+
+
+def _plain_and_fast(sqs, circ, amp32=False):
+    fast = sqs.State(circ["widths"], amp32=amp32)
+    fast.trace_enable(1 << 14)
+    fast.run(circ)
+    plain = sqs.run_circuit(circ, amp32=amp32, merge=sqs.MERGE_PLAIN)
+    return fast, plain
+
+
+@pytest.mark.parametrize("amp32", [False, True])
+def test_copy_pair_fold(sqs, amp32):
+    """A qubit expanded by an uncontrolled H-like gate and left untouched has
+    every partner, with +-1 times the branch's amplitude: the next gate on it
+    folds without a merge, and the state equals the merged one bit for bit."""
+    widths = [8, 8, 8]
+    gates = [("h", 0, b, ()) for b in range(6)] + [("x", 1, 0, ()), ("h", 1, 0, ())]
+    gates += [("x", 2, 1, ((0, 2, 1),)), ("add", 2, -1, 5, ()), ("phase", ((0, 1, 1),), 0.7),
+              ("x", 2, 3, ((0, 0, 1),))]
+    gates += [("h", 0, 4, ()),                       # +1 pair: fold (the cancelling H)
+              ("ry", 1, 0, 0.9, ((0, 5, 1),)),       # -1 pair, controlled consumer: fold
+              ("h", 0, 1, ()),                       # read by the phase: merge
+              ("h", 0, 0, ())]                       # read as a control: merge
+    circ = {"widths": widths, "eps": 1e-14, "tables": [], "gates": gates}
+    fast, plain = _plain_and_fast(sqs, circ, amp32)
+    names = [r[0] for r in fast.trace_read()[0]]
+    assert names.count("k_fold") == 2
+    assert fast.stats()["steps_fold"] == 2 and plain.stats()["steps_fold"] == 0
+    df, dp = fast.to_dict(), plain.to_dict()
+    assert set(df) == set(dp) and all(df[k] == dp[k] for k in df)
+    o = oracle.run_circuit(circ)
+    if amp32:
+        assert compare_states(df, o.to_dict(), atol=ATOL32, band=ATOL32) >= 1 - 1e-6
+    else:
+        assert set(df) == set(o.to_dict())
+        assert compare_states(df, o.to_dict()) >= 1 - 1e-12
+
+
+def test_fold_takes_config2_cancellations(sqs):
+    circ = W.config2(seed=2, n_branch=16, n_perm=300, n_cancel=6)
+    fast, plain = _plain_and_fast(sqs, circ)
+    assert fast.stats()["steps_fold"] == 6
+    df, dp = fast.to_dict(), plain.to_dict()
+    assert set(df) == set(dp) and all(df[k] == dp[k] for k in df)
+    o = oracle.run_circuit(circ)
+    assert fast.nnz() == o.nnz() == 2 ** 10
+    assert compare_states(df, o.to_dict()) >= 1 - 1e-12

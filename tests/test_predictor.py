@@ -103,13 +103,15 @@ def test_learned_sizing_gains_over_exact_bound(S, trained):
     (bit for bit) with fewer host waits than exact sizing, which must read the
     count back whenever the doubling bound outgrows the buffers, and a small
     fraction of the memory that sizing from that bound alone, without any
-    count read-back, would reserve."""
+    count read-back, would reserve.  Both run without the host-proven
+    shortcuts (the copy-pair fold keeps the exact bound tight through the
+    cancelling gates, which would hide what sizing has to do)."""
     import torch
     p, _, _ = trained
     c = W.config2(seed=2, n_branch=20, n_perm=500, n_cancel=8)
     res = {}
     for mode in ("exact", "learned"):
-        g = S.State(c["widths"], learned=(mode == "learned"))
+        g = S.State(c["widths"], learned=(mode == "learned"), merge=S.MERGE_PLAIN)
         if mode == "learned":
             g.set_predictor(p)
         g.run(c)

@@ -125,8 +125,10 @@ def test_tuned_choice_measures_both_paths(sqs):
     class, then keeps one; whichever it keeps, the state is the bucket
     merge's, bit for bit."""
     circ = W.config2(seed=2, n_branch=14, n_perm=200, n_cancel=4)
-    t = sqs.run_circuit(circ, merge=TUNED)
-    b = sqs.run_circuit(circ, merge=BUCKET)
+    # Without the host-proven shortcuts every interference step merges, so
+    # size classes recur and both paths get timed.
+    t = sqs.run_circuit(circ, merge=TUNED | sqs.MERGE_PLAIN)
+    b = sqs.run_circuit(circ, merge=BUCKET | sqs.MERGE_PLAIN)
     st = t.stats()
     assert st["steps_sort"] >= 1 and st["steps_hash"] >= 1
     dt, db = t.to_dict(), b.to_dict()
