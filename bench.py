@@ -399,8 +399,8 @@ def main():
             return 0.0
         nin = n_in[gi]
         nout = n_in[gi + 1] if gi + 1 < len(gates) else n_final
-        if name == "k_pair":
-            return float(nin + nout) * rb
+        if name in ("k_pair", "k_fold", "k_expand", "k_rsort_merge", "k_pair_cluster"):
+            return float(nin + nout) * rb  # read every input, write every output
         return 2.0 * nin * rb  # partition / fused pass: read and write every branch
 
     launches_dom = [(alg_bytes(n, c), statistics.mean(v), c) for (n, c), v in by_call.items()
