@@ -222,6 +222,79 @@ def variants(circ, widths, stream, probs, norm, flush, args, st64):
 
 BENCH_UNITS = [0]
 
+# Per-gate microbenchmark: one gate on a seeded random state of N branches
+# (64-qubit keys, 4 x 16-bit registers), N on a log grid, with the fraction
+# of branches whose partner across the target bit is present set to 0, 0.5
+# or 1 for interference gates.  Bytes per unit as in the kernels' table:
+# a fused pass reads and writes every branch; an interference step reads
+# every input and writes every output.
+PER_GATE_SIZES = (1 << 10, 1 << 14, 1 << 18, 1 << 22, 1 << 24)
+PER_GATE_KINDS = (
+    ("h", ("h", 2, 5, ()), (0.0, 0.5, 1.0)),
+    ("ry", ("ry", 1, 9, 0.7, ()), (0.0, 1.0)),
+    ("u1q", ("u1q", 3, 3, "U", ()), (0.5,)),
+    ("x", ("x", 0, 7, ()), None),
+    ("cnot", ("x", 0, 7, ((1, 2, 1),)), None),
+    ("toffoli", ("x", 0, 7, ((1, 2, 1), (2, 3, 1))), None),
+    ("add", ("add", 1, 2, 0, ()), None),
+    ("swap", ("swap", 0, 3, ()), None),
+    ("phase", ("phase", ((1, 4, 1),), 0.77), None),
+    ("qram_load", ("qload", 0, 1, 0), None),
+)
+
+
+def per_gate(args):
+    import numpy as np
+    import torch
+
+    from paper_2503_15118_gb300 import sqs
+    widths = [16, 16, 16, 16]
+    rb = 24
+    U = np.array([[0.6, -0.8j], [0.8, 0.6j]])
+    table = np.random.default_rng(7).integers(0, 2 ** 16, size=2 ** 16).astype(np.uint16)
+    hbm, _ = peaks()
+    stream = torch.cuda.Stream()
+    st = sqs.State(widths, capacity_hint=1 << 25, stream=stream.cuda_stream, eps=1e-14)
+    rows = []
+    reps = max(3, min(args.steps, 7))
+    for n in PER_GATE_SIZES:
+        states = {}
+        for name, gate, fracs in PER_GATE_KINDS:
+            if gate[0] == "u1q":
+                gate = ("u1q", gate[1], gate[2], U, gate[4])
+            for pf in (fracs or (None,)):
+                key = (pf, gate[1:3] if fracs else None)
+                if key not in states:
+                    target = (gate[1], gate[2]) if fracs else None
+                    states[key] = W.random_state(widths, n, seed=n % 1000 + 17,
+                                                 pair_fraction=pf or 0.0, target=target)
+                lo, hi, amps = states[key]
+                times, n_out = [], 0
+                for rep in range(reps + 1):
+                    st.import_(lo, hi, amps)
+                    st.sync()
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    st.apply(gate, [table])
+                    st.flush()
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    if rep:
+                        times.append(a.elapsed_time(b))
+                    n_out = st.nnz()
+                ms = statistics.median(times)
+                byts = (n + n_out) * rb if fracs else 2 * n * rb
+                gbs = byts / (ms / 1e3) / 1e9
+                rows.append({"gate": name, "n": n, "pair_fraction": pf, "n_out": n_out, "ms": ms,
+                             "updates_per_s": n / (ms / 1e3), "gb_per_s": gbs,
+                             "frac_hbm": gbs / hbm})
+    st.close()
+    print(json.dumps({"per_gate": rows, "unit": UNIT, "hbm_gbs": hbm, "reps": reps,
+                      "timing": "CUDA events around one gate call and its flush, median"}),
+          flush=True)
+    return 0
+
 
 def qlss_workloads(stream, flush, args):
     """Updates/s of the linear-system walk (one system, N = 1024) and of the
@@ -294,6 +367,8 @@ def main():
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step and exit (the target of ncu captures)")
     ap.add_argument("--amp32", dest="amp32", action="store_true")
+    ap.add_argument("--per-gate", action="store_true",
+                    help="per-gate microbenchmark (updates/s and HBM fraction per gate kind and size)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -302,6 +377,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.per_gate:
+        import torch
+        torch.cuda.set_device(local)
+        return per_gate(args)
 
     import torch
     torch.cuda.set_device(local)
