@@ -165,6 +165,15 @@ struct sqs_state {
   };
   std::map<uint32_t, Tune> tune;
 
+  // Half-angle tables of register-valued rotations, per (scale, offset,
+  // digits); kept for the state's lifetime (queued steps may point to them).
+  struct AngTab {
+    double scale, offset;
+    uint32_t digits;
+    double2* dev;
+  };
+  std::vector<AngTab> ang_tabs;
+
   sqs_stats stats{};
   std::unordered_map<void*, size_t> sizes;
 };
@@ -1239,6 +1248,24 @@ sqs_status apply_1q(sqs_state* st, uint32_t reg, uint32_t bit, const double* m,
   g.ang_w = mode == 1 ? st->width[angle_reg] : 0;
   g.scale = scale;
   g.offset = offset;
+  g.ang_tab = nullptr;
+  g.ang_digits = 0;
+  if (mode == 1) {
+    const uint32_t digits = (g.ang_w + 15) / 16;
+    for (const auto& t : st->ang_tabs)
+      if (t.scale == scale && t.offset == offset && t.digits == digits) g.ang_tab = t.dev;
+    if (!g.ang_tab && st->ang_tabs.size() < 32) {
+      double2* dev = (double2*)dalloc(st, ((size_t)digits << 16) * sizeof(double2));
+      if (dev && sqs::launch_angle_table(st->stream, dev, digits, scale, offset) == cudaSuccess) {
+        st->ang_tabs.push_back(sqs_state::AngTab{scale, offset, digits, dev});
+        g.ang_tab = dev;
+      } else if (dev) {
+        dfree_now(st, dev);
+      }
+      cudaGetLastError();
+    }
+    g.ang_digits = g.ang_tab ? digits : 0;
+  }
   g.eps = st->eps;
   g.eps2 = st->eps * st->eps;
   g.epsf = (float)st->eps;
@@ -1366,6 +1393,7 @@ void sqs_state_destroy(sqs_state* st) {
   dfree(st, st->ctl);
   dfree(st, st->scratch);
   dfree(st, st->sort_buf);
+  for (auto& t : st->ang_tabs) dfree(st, t.dev);
   for (auto& kv : st->tune)
     for (cudaEvent_t e : kv.second.ev)
       if (e) cudaEventDestroy(e);

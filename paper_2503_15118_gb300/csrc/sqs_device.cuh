@@ -38,6 +38,22 @@ __device__ __forceinline__ uint64_t lo64(u128 k) { return (uint64_t)k; }
 __device__ __forceinline__ uint64_t hi64(uint64_t) { return 0; }
 __device__ __forceinline__ uint64_t hi64(u128 k) { return (uint64_t)(k >> 64); }
 
+// Key with only bit t set, built from its two 64-bit words (no variable
+// 128-bit shift, whose results for t >= 64 one compiled instantiation got
+// wrong), and the mask of bits below t likewise.
+template <int KW>
+__device__ __forceinline__ typename KT<KW>::T bit_mask(uint32_t t) {
+  const uint64_t lo = t < 64 ? (1ull << t) : 0ull;
+  const uint64_t hi = (t >= 64 && t < 128) ? (1ull << (t - 64)) : 0ull;
+  return mk<KW>(lo, hi);
+}
+template <int KW>
+__device__ __forceinline__ typename KT<KW>::T low_mask_bits(uint32_t t) {
+  const uint64_t lo = t >= 64 ? ~0ull : ((1ull << t) - 1ull);
+  const uint64_t hi = t <= 64 ? 0ull : (t >= 128 ? ~0ull : ((1ull << (t - 64)) - 1ull));
+  return mk<KW>(lo, hi);
+}
+
 __device__ __forceinline__ uint64_t wmask(uint32_t w) {
   return w >= 64 ? ~0ull : ((1ull << w) - 1ull);
 }
@@ -419,6 +435,29 @@ __device__ __forceinline__ void flush_residue(float2& o, float2 a0, float2 a1) {
   if (fabsf(o.x) + fabsf(o.y) <= size * 4.76837158e-7f) o = make_float2(0.f, 0.f);
 }
 
+// cos and sin of theta / 2 for theta = scale * v + offset (mode 1).  With a
+// digit table, the angle is the sum of one table angle per 16-bit digit of
+// v, combined by the angle-addition formulas (four FP64 operations per digit
+// after the first) instead of a full sincos per branch.
+__device__ __forceinline__ void half_angle_cs(const Gate1& g, uint64_t v, double& cs,
+                                              double& sn) {
+  if (g.ang_tab) {
+    const double2 t = __ldg(&g.ang_tab[v & 0xffffull]);
+    cs = t.x;
+    sn = t.y;
+    for (uint32_t j = 1; j < g.ang_digits; ++j) {
+      const double2 u = __ldg(&g.ang_tab[((uint64_t)j << 16) | ((v >> (16 * j)) & 0xffffull)]);
+      const double c2 = __fma_rn(-sn, u.y, __dmul_rn(cs, u.x));  // cos(a + b)
+      const double s2 = __fma_rn(sn, u.x, __dmul_rn(cs, u.y));   // sin(a + b)
+      cs = c2;
+      sn = s2;
+    }
+  } else {
+    const double theta = g.scale * (double)v + g.offset;
+    sincos(theta * 0.5, &sn, &cs);
+  }
+}
+
 template <class AT>
 __device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, bool has0, AT a0,
                                          bool has1, AT a1, AT& o0, AT& o1) {
@@ -428,9 +467,8 @@ __device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, b
   if (g.mode == 2 || g.mode == 1) {
     S u00, u01, u10, u11;
     if (g.mode == 1) {
-      const double theta = g.scale * (double)angle_value + g.offset;
       double sn, cs;
-      sincos(theta * 0.5, &sn, &cs);
+      half_angle_cs(g, angle_value, cs, sn);
       u00 = (S)cs, u01 = (S)-sn, u10 = (S)sn, u11 = (S)cs;
     } else {
       u00 = Coef<AT>::r(g, 0), u01 = Coef<AT>::r(g, 1), u10 = Coef<AT>::r(g, 2),

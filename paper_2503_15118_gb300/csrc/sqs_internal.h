@@ -120,6 +120,11 @@ struct Gate1 {            // the interference operation of one merge step
   // flush it always).  -1: no child cancels.
   int32_t fold_kill;
   uint64_t fold_tmax;
+  // Mode 1: (cos, sin) of the half angle per 16-bit digit of the angle
+  // register's value, digit j at [j << 16, (j + 1) << 16), the offset folded
+  // into digit 0 (device table owned by the state; null: direct sincos).
+  const double2* ang_tab;
+  uint32_t ang_digits;
 };
 
 struct Launch {
@@ -130,6 +135,9 @@ struct Launch {
 };
 
 // Launchers (sqs_kernels.cu).  Each returns cudaGetLastError() after enqueueing.
+// Fills tab[j << 16 | d] = (cos, sin)(scale / 2 * d * 2^(16 j) + (j == 0 ? offset / 2 : 0)).
+cudaError_t launch_angle_table(cudaStream_t s, double2* tab, uint32_t digits, double scale,
+                               double offset);
 cudaError_t launch_init(const Launch& L, Ctl* ctl, Arr a, int slot, bool amp32);
 cudaError_t launch_apply_inplace(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr a, int slot,
                                  const OpList& ops);

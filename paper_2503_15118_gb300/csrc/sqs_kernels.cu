@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kStreamThreads)
   load_ops(ops, sops, tab);
   const uint64_t n_dense = ctl->cnt[in_slot];
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, n_dense);
-  const K bmask = ((K)1) << g.t;
+  const K bmask = bit_mask<KW>(g.t);
   const uint32_t C = 1u << bk.seg_log2;
   // Units of kPartILP * blockDim slots: a slice of a segment, or of the dense
   // array.
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kPairThreads)
   __syncthreads();
   if (threadIdx.x == 0) bk.seg_cnt[b] = 0u;  // bucket is clean for the next use
 
-  const K bmask = ((K)1) << g.t;
+  const K bmask = bit_mask<KW>(g.t);
   const K cmask = mk<KW>(g.cmask[0], g.cmask[1]);
   const K cval = mk<KW>(g.cval[0], g.cval[1]);
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kStreamThreads)
   const uint64_t chunk = 1ull << kExpandChunkLog2;
   // Chunks per input segment (segments are at least one chunk long).
   const uint32_t cps_log2 = in.seg_cnt ? in.seg_log2 - kExpandChunkLog2 : 0u;
-  const K bmask = ((K)1) << g.t;
+  const K bmask = bit_mask<KW>(g.t);
   const K cmask = mk<KW>(g.cmask[0], g.cmask[1]);
   const K cval = mk<KW>(g.cval[0], g.cval[1]);
   const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(kBinThreads)
   load_ops(ops, sm.ops, sm.tab);
   const uint64_t n_dense = ctl->cnt[in_slot];
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, n_dense);
-  const K bmask = ((K)1) << g.t;
+  const K bmask = bit_mask<KW>(g.t);
   const uint32_t B = bins.n_seg;
   const uint32_t cap = 1u << bins.seg_log2;
   uint32_t per_seg = 1;
@@ -873,7 +873,7 @@ __global__ void __launch_bounds__(kPairCThreads)
   }
   cluster_sync_all();  // every slot array of the cluster is cleared and loaded
 
-  const K bmask = ((K)1) << g.t;
+  const K bmask = bit_mask<KW>(g.t);
   const K cmask = mk<KW>(g.cmask[0], g.cmask[1]);
   const K cval = mk<KW>(g.cval[0], g.cval[1]);
   constexpr uint32_t kSlotsAll = kSlotsPerCta * kClusterCtas;
@@ -1054,6 +1054,25 @@ cudaError_t launch_apply_compact(const Launch& L, int kw, bool amp32, Ctl* ctl, 
                                                 L.seq)
   SQS_DISPATCH(kw, amp32, SQS_AC);
 #undef SQS_AC
+  return cudaGetLastError();
+}
+
+__global__ void k_angle_table(double2* tab, uint32_t digits, double scale, double offset) {
+  const uint64_t n = (uint64_t)digits << 16;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = (uint32_t)(i >> 16);
+    const double d = (double)(i & 0xffffull) * ldexp(1.0, 16 * (int)j);
+    const double arg = 0.5 * scale * d + (j == 0 ? 0.5 * offset : 0.0);
+    double sn, cs;
+    sincos(arg, &sn, &cs);
+    tab[i] = make_double2(cs, sn);
+  }
+}
+
+cudaError_t launch_angle_table(cudaStream_t s, double2* tab, uint32_t digits, double scale,
+                               double offset) {
+  k_angle_table<<<256, 256, 0, s>>>(tab, digits, scale, offset);
   return cudaGetLastError();
 }
 

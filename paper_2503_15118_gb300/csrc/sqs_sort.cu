@@ -40,7 +40,7 @@ static_assert(kRadix == kSortThreads, "one digit per thread in the tile scan");
 // The pair-class key: bit t deleted, the bits above it shifted down by one.
 template <class K>
 __device__ __forceinline__ K drop_bit(K k, uint32_t t) {
-  const K low = (((K)1) << t) - (K)1;
+  const K low = low_mask_bits<sizeof(K) == 16 ? 2 : 1>(t);
   return (k & low) | ((k >> 1) & ~low);
 }
 
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kStreamThreads)
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[(out_slot + 1) & 3] = 0;
   const uint64_t n = *n_ptr;
   const uint64_t chunk = 1ull << kMergeChunkLog2;
-  const K bmask = ((K)1) << g.t;
+  const K bmask = bit_mask<KW>(g.t);
   const K cmask = mk<KW>(g.cmask[0], g.cmask[1]);
   const K cval = mk<KW>(g.cval[0], g.cval[1]);
   const unsigned int lane = threadIdx.x & 31u;
