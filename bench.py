@@ -296,36 +296,75 @@ def per_gate(args):
     return 0
 
 
-def qlss_workloads(stream, flush, args):
-    """Updates/s of the linear-system walk (one system, N = 1024) and of the
-    batched walk (256 systems of sizes 8..128), a few walk steps each."""
+MERGE_KERNELS = ("k_partition", "k_pair", "k_expand", "k_fold", "k_bin", "k_pair_cluster",
+                 "k_rsort_pass", "k_rsort_merge")
+
+
+def extra_workloads(stream, flush, args):
+    """Updates/s of the other workloads:
+    - config 1 batched: 2^16 instances of the 20-qubit circuit in one state,
+      each loading its own QRAM table, with the HBM-roofline fraction of its
+      interference steps (every expand / merge launch: inputs read plus
+      outputs written, over their event-timed duration);
+    - the linear-system walk (one system, N = 1024), 4 walk steps;
+    - the batched walk (256 systems of sizes 8..128), 2 walk steps;
+    each in FP64 and FP32 storage."""
     from paper_2503_15118_gb300 import qlss, sqs
     out = {}
+    with open(os.path.join(ROOT, "tests", "golden", "config1_seed1_gates.json")) as f:
+        stored = json.load(f)
     cfg4 = W.config4(seed=4)
     cfg5 = qlss.config5(seed=5)
-    for name, circ, hint in (
+    work = (("config1_batch65536", W.config1_batch(stored, inst_bits=16), 1 << 26),
             ("qlss_walk_N1024_4steps", qlss.walk_circuit(cfg4, n_steps=4), 1 << 23),
-            ("qlss_batch256_2steps", qlss.batched_circuit(cfg5, 2), 1 << 23)):
-        st = sqs.State(circ["widths"], capacity_hint=hint, stream=stream.cuda_stream,
-                       eps=circ["eps"])
+            ("qlss_batch256_2steps", qlss.batched_circuit(cfg5, 2), 1 << 23))
+    hbm, _ = peaks()
+    for name, circ, hint in work:
+        for amp32 in (False, True):
+            st = sqs.State(circ["widths"], capacity_hint=hint, stream=stream.cuda_stream,
+                           eps=circ["eps"], amp32=amp32)
 
-        def step():
+            def step():
+                st.reset()
+                st.run(circ)
+
+            for _ in range(args.warmup):
+                step()
+            st.sync()
             st.reset()
-            st.run(circ)
-
-        for _ in range(args.warmup):
-            step()
-        st.sync()
-        st.reset()
-        units = 0
-        for g in circ["gates"]:
-            units += st.nnz()
-            st.apply(g, circ["tables"])
-        ms = _timed_steps(st, step, flush, stream, max(3, args.steps // 2))
-        out[name] = {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            n_in = []
+            for g in circ["gates"]:
+                n_in.append(st.nnz())
+                st.apply(g, circ["tables"])
+            n_in.append(st.nnz())
+            units = sum(n_in[:-1])
+            ms = _timed_steps(st, step, flush, stream, max(3, args.steps // 2))
+            entry = {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                      "units_per_step": units, "gates": len(circ["gates"]),
                      "peak_nnz": st.peak_nnz(), "key_words": st.kw}
-        st.close()
+            # Interference-step roofline from one traced step.
+            st.trace_enable(1 << 16)
+            st.trace_read()
+            step()
+            st.sync()
+            recs, _ = st.trace_read(cap=1 << 16)
+            rb = 8 * st.kw + (8 if amp32 else 16)
+            byts, tms = 0.0, 0.0
+            for kname, call, kms in recs:
+                gi = call - 2
+                if kname in MERGE_KERNELS and 0 <= gi < len(circ["gates"]):
+                    if kname in ("k_partition", "k_bin", "k_rsort_pass"):
+                        byts += 2.0 * n_in[gi] * rb
+                    else:
+                        byts += float(n_in[gi] + n_in[gi + 1]) * rb
+                    tms += kms
+            if tms > 0:
+                gbs = byts / (tms / 1e3) / 1e9
+                entry["interference_roofline"] = {"achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                                  "frac": gbs / hbm,
+                                                  "kernel_ms_per_step": tms}
+            out[name + ("_f32" if amp32 else "_f64")] = entry
+            st.close()
     return out
 
 
@@ -529,7 +568,7 @@ def main():
     }
     if not args.no_variants:
         line["variants"] = variants(circ, widths, stream, probs, norm, flush, args, st)
-        line["variants"].update(qlss_workloads(stream, flush, args))
+        line["variants"].update(extra_workloads(stream, flush, args))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, _ = cpu_baseline(circ)
         line["cpu_baseline"] = cb

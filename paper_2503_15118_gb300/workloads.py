@@ -172,6 +172,54 @@ def config1(seed=1, n_gates=200, cap=4096, accept=None):
     return circ
 
 
+def _decode_gate(g, remap):
+    """A stored gate (JSON lists) as a gate tuple, registers renumbered."""
+    def ctrls(cs):
+        return tuple((remap[c[0]], c[1], c[2]) for c in cs)
+    op = g[0]
+    if op in ("h", "x"):
+        return (op, remap[g[1]], g[2], ctrls(g[3]))
+    if op == "ry":
+        return (op, remap[g[1]], g[2], float(g[3]), ctrls(g[4]))
+    if op == "phase":
+        return (op, ctrls(g[1]), float(g[2]))
+    raise ValueError(f"config 1 has no gate {op!r}")
+
+
+def config1_batch(stored, inst_bits=16, seed=1):
+    """2^inst_bits instances of config 1 in one state.
+
+    Every instance runs the same stored gate list (config 1, seed 1, its nnz
+    cap enforced on the oracle); instance i loads its own seeded 256-entry
+    uint8 table (instance 0: the seed-1 table), so the instances' states
+    differ.  Registers: addr 8, inst, data 8, anc 4 -- the instance register
+    sits next to addr so that the QRAM address (addr, inst) spans consecutive
+    registers; the instances start in uniform superposition (H on every
+    instance qubit).  `stored` is the dict of tests/golden/config1_seed1_gates.json.
+    """
+    remap = {0: 0, 1: 2, 2: 3}
+    widths = [8, inst_bits, 8, 4]
+    n_inst = 1 << inst_bits
+    base = config1_prefix(seed)[0]["tables"][0]
+    rng = np.random.default_rng(seed + 1000)
+    table = rng.integers(0, 256, size=n_inst * 256, dtype=np.uint64).astype(np.uint8)
+    table[:256] = base
+    gates = [("h", 1, b, ()) for b in range(inst_bits)]
+    for g in stored["gates"]:
+        if g[0] == "qload":
+            gates.append(("qload", (0, 2), remap[g[2]], 0))
+        else:
+            gates.append(_decode_gate(g, remap))
+    return {"widths": widths, "eps": stored["eps"], "tables": [table], "gates": gates,
+            "n_inst": n_inst, "inst_bits": inst_bits,
+            "name": f"config1-batch{n_inst}-seed{seed}"}
+
+
+def config1_instance_table(batch, i):
+    """The 256-entry table instance i of a config-1 batch loads."""
+    return batch["tables"][0][i * 256:(i + 1) * 256]
+
+
 # ---------------------------------------------------------------------------
 # Config 2: 64 qubits = four 16-bit registers in one uint64 key, FP64.
 # 24 branching gates (16 H of which 8 on reserved cancel qubits, 8 RY) interleaved

@@ -432,3 +432,27 @@ def test_fold_takes_config2_cancellations(sqs):
     o = oracle.run_circuit(circ)
     assert fast.nnz() == o.nnz() == 2 ** 10
     assert compare_states(df, o.to_dict()) >= 1 - 1e-12
+
+
+def test_config1_batch_sampled_instances(sqs):
+    """256 instances of config 1 in one state (own QRAM table each): sampled
+    instances equal config 1 run alone on the oracle, scaled by 1/16."""
+    import json
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "golden", "config1_seed1_gates.json")) as f:
+        stored = json.load(f)
+    batch = W.config1_batch(stored, inst_bits=8)
+    g = sqs.run_circuit(batch)
+    lo, hi, amps = g.export()
+    inst = (lo >> np.uint64(8)) & np.uint64(255)
+    fresh = build_config1(seed=1)
+    for i in (0, 77, 255):
+        ref = oracle.run_circuit(dict(fresh, tables=[W.config1_instance_table(batch, i)])).to_dict()
+        sel = inst == i
+        part = {}
+        for l, a in zip(lo[sel], amps[sel]):
+            k = int(l)
+            part[(k & 0xff) | ((k >> 16) << 8)] = complex(a)
+        assert set(part) == set(ref)
+        assert max(abs(part[k] - ref[k] / 16.0) for k in part) < 1e-12

@@ -197,3 +197,38 @@ def test_batched_walk_converges_per_instance():
         x = np.linalg.solve(A, np.full(N, N ** -0.5))
         x /= np.linalg.norm(x)
         assert abs(np.vdot(x, v)) ** 2 / np.vdot(v, v).real > 0.99
+
+
+def test_config1_batch_instances_are_config1():
+    """The stored config-1 gate list is what the oracle-driven rejection
+    sampling produces, and instance i of the batched form equals config 1
+    run alone with instance i's table, scaled by 2^{-inst_bits/2}."""
+    import json
+    import os
+
+    from paper_2503_15118_gb300 import workloads as W
+    from tests.helpers import build_config1
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "golden", "config1_seed1_gates.json")) as f:
+        stored = json.load(f)
+    fresh = build_config1(seed=1)
+    assert len(stored["gates"]) == len(fresh["gates"])
+    for s_g, f_g in zip(stored["gates"], fresh["gates"]):
+        assert s_g[0] == f_g[0]
+    batch = W.config1_batch(stored, inst_bits=2)
+    o = oracle.run_circuit(batch)
+    d = o.to_dict()
+    off_inst = 8
+    for i in range(4):
+        alone = dict(fresh, tables=[W.config1_instance_table(batch, i)])
+        ref = oracle.run_circuit(alone).to_dict()
+        # fresh uses registers (addr, data, anc); the batch (addr, inst, data, anc)
+        part = {}
+        for k, a in d.items():
+            if (k >> off_inst) & 3 != i:
+                continue
+            addr = k & 0xff
+            rest = k >> (off_inst + 2)
+            part[addr | (rest << 8)] = a
+        assert set(part) == set(ref)
+        assert max(abs(part[k] - 0.5 * ref[k]) for k in part) < 1e-12
