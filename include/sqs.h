@@ -345,6 +345,38 @@ sqs_status sqs_state_record(sqs_state* st, uint32_t enable);
  * floats), writes the number available to *n and clears the records. */
 sqs_status sqs_state_read_records(sqs_state* st, float* X, float* y, uint32_t cap, uint32_t* n);
 
+/* ---- CUDA-graph capture -------------------------------------------------
+ * Small states are bound by launch latency (tens of microseconds per gate);
+ * a circuit that runs many times from |0...0> can be captured once and
+ * replayed as one CUDA graph.
+ *
+ * sqs_capture_begin resets the state to |0...0> (now, and as the graph's
+ * first node), sizes its buffers for static_bound branches and starts
+ * capturing the state's stream (thread-local capture mode).  Until
+ * sqs_capture_end, every call is recorded instead of run; the branch-count
+ * bound is held at static_bound (an operation whose result would exceed it is
+ * detected on the device and reported, sticky, at the next wait); calls that
+ * wait for the device, copy to or from host memory or allocate return
+ * SQS_ERR_STATE and make the capture fail (readouts, sqs_table_create,
+ * sqs_import, sqs_sync; run the circuit once without capture first so that
+ * QRAM tables and rotation tables exist).  Learned sizing and the sort,
+ * cluster and measured merges cannot be captured, nor can a state created on
+ * the legacy default stream (SQS_ERR_ARG).
+ * sqs_capture_end closes the capture, instantiates the graph into *out and
+ * leaves the state at |0...0> (nothing was run).  On failure nothing is
+ * returned and the state is usable.
+ * sqs_graph_launch replays the graph on the state's stream: the state becomes
+ * what the captured calls make of |0...0>, asynchronously, exactly as if they
+ * were issued again (pending operations are discarded as by a reset).  It
+ * fails with SQS_ERR_STATE when the state's buffers were reallocated since
+ * the capture (a larger state grew them): capture again.  Destroy graphs
+ * before their state. */
+typedef struct sqs_graph sqs_graph;
+sqs_status sqs_capture_begin(sqs_state* st, uint64_t static_bound);
+sqs_status sqs_capture_end(sqs_state* st, sqs_graph** out);
+sqs_status sqs_graph_launch(sqs_state* st, sqs_graph* g);
+void sqs_graph_destroy(sqs_graph* g);
+
 typedef struct {
   uint64_t host_waits;       /* times the host read the device counts         */
   uint64_t overflow_reruns;  /* learned-mode steps re-run at the exact size    */

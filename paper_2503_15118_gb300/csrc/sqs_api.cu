@@ -77,6 +77,20 @@ struct Store {
   }
 };
 
+// The host-side bookkeeping that describes the device state: buffer roles,
+// the count slot and bound, and the per-qubit history.
+struct HostSnap {
+  Store cur, alt, bk;
+  int cur_slot = 0;
+  uint64_t ub = 1;
+  uint32_t call = 0;
+  std::vector<int64_t> last_branch;
+  std::vector<uint32_t> writes_since, reads_since;
+  std::vector<uint8_t> arith_since;
+  std::vector<int8_t> const_val, pair_sign;
+  int64_t n_branch = 0, last_target = -1;
+};
+
 // A queued non-interference operation; factors c0/c1 of amplitude operations
 // stay on the host and are folded into the launch's factor table.
 struct HostOp {
@@ -174,6 +188,15 @@ struct sqs_state {
   };
   std::vector<AngTab> ang_tabs;
 
+  // CUDA-graph capture (sqs_capture_begin / _end): while capturing, nothing
+  // may wait for the device or allocate, and the branch-count bound is held
+  // at static_ub (buffers are sized for it when the capture begins).
+  bool capturing = false;
+  uint64_t static_ub = 0;
+  sqs_status capture_err = SQS_OK;
+  HostSnap entry_snap;
+  uint64_t launches_at_capture = 0;
+
   sqs_stats stats{};
   std::unordered_map<void*, size_t> sizes;
 };
@@ -200,6 +223,10 @@ sqs_status cuda_fail(sqs_state* st, cudaError_t e, const char* what) {
 void* dalloc(sqs_state* st, size_t bytes) {
   if (bytes == 0) bytes = 256;
   void* p = nullptr;
+  if (st->capturing) {
+    st->capture_err = SQS_ERR_STATE;  // buffers are sized when the capture begins
+    return nullptr;
+  }
   if (st->has_alloc) {
     p = st->alloc.alloc(st->alloc.ctx, bytes, (void*)st->stream);
   } else if (cudaMallocAsync(&p, bytes, st->stream) != cudaSuccess) {
@@ -256,6 +283,10 @@ uint64_t round_cap(uint64_t need) {
 // Makes s hold at least `need` branches (contents are not kept).
 bool ensure_store(sqs_state* st, Store& s, uint64_t need) {
   if (s.k0 && s.cap >= need) return true;
+  if (st->capturing) {  // buffers are sized when a capture begins
+    st->capture_err = SQS_ERR_STATE;
+    return false;
+  }
   free_store(st, s);
   const uint64_t cap = round_cap(need);
   const uint64_t nseg = (cap >> kBucketLog2) + 1;
@@ -276,12 +307,18 @@ uint64_t max_branches(const sqs_state* st) {
   return st->total_bits >= 62 ? (1ull << 62) : (1ull << st->total_bits);
 }
 
+// The count bound after an operation: v, held at the static bound while a
+// graph is captured (the device checks every write against the buffers).
+uint64_t bound_after(const sqs_state* st, uint64_t v) {
+  return st->static_ub ? std::min(v, st->static_ub) : v;
+}
+
 // Brackets one launch with trace events when tracing is on.
 struct Traced {
   sqs_state* st;
   int idx = -1;
   Traced(sqs_state* s, uint32_t kernel) : st(s) {
-    if (st->ev.empty()) return;
+    if (st->ev.empty() || st->capturing) return;
     const size_t used = st->trace.size();
     if (2 * (used + 1) > st->ev.size()) {
       st->trace_dropped++;
@@ -326,6 +363,10 @@ bool ctrl_touches(const uint64_t mask[2], uint32_t q) { return (mask[q >> 6] >> 
 // Reads the control block (waits for the stream) and converts device errors.
 // With report_only, a device error is returned without becoming sticky.
 sqs_status sync_ctl(sqs_state* st, bool report_only = false) {
+  if (st->capturing) {
+    st->capture_err = SQS_ERR_STATE;
+    return fail(st, SQS_ERR_STATE, "a host wait inside a graph capture (raise the static bound)");
+  }
   cudaError_t e = cudaMemcpyAsync(st->ctl_host, st->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
                                   st->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
@@ -356,6 +397,15 @@ sqs_status sync_bound(sqs_state* st) {
 sqs_status check_usable(sqs_state* st) {
   if (!st) return SQS_ERR_ARG;
   return st->sticky;
+}
+
+// Calls that wait for the device or copy to or from host memory cannot be
+// part of a graph capture.
+sqs_status no_capture(sqs_state* st, const char* what) {
+  if (!st) return SQS_ERR_ARG;
+  if (!st->capturing) return SQS_OK;
+  st->capture_err = SQS_ERR_STATE;
+  return fail(st, SQS_ERR_STATE, "%s inside a graph capture", what);
 }
 
 // Folds the amplitude factors of one group of MUL ops into entries
@@ -504,11 +554,11 @@ sqs_status run_expand(sqs_state* st, const Gate1& g, int64_t rec_idx) {
   auto out_bound = [&] {
     return g.fold_sign ? st->ub : std::min(max_branches(st), 2 * st->ub);
   };
-  uint64_t need = std::max<uint64_t>(out_bound(), 1);
+  uint64_t need = std::max<uint64_t>(bound_after(st, out_bound()), 1);
   if (need > st->alt.cap && st->ub > 1) {
     sqs_status s = sync_bound(st);  // the bound outgrew the allocation: exact count
     if (s != SQS_OK) return s;
-    need = std::max<uint64_t>(out_bound(), 1);
+    need = std::max<uint64_t>(bound_after(st, out_bound()), 1);
   }
   const uint64_t in_slots = st->cur.slots(st->ub);
   const uint64_t chunks =
@@ -534,7 +584,7 @@ sqs_status run_expand(sqs_state* st, const Gate1& g, int64_t rec_idx) {
   }
   std::swap(st->cur, st->alt);
   st->cur_slot = out_slot;
-  st->ub = out_bound();
+  st->ub = bound_after(st, out_bound());
   return SQS_OK;
 }
 
@@ -577,7 +627,7 @@ sqs_status run_binned(sqs_state* st, const Gate1& g, uint64_t B1, int64_t rec_id
   }
   std::swap(st->cur, st->alt);
   st->cur_slot = out_slot;
-  st->ub = std::min(max_branches(st), 2 * st->ub);
+  st->ub = bound_after(st, std::min(max_branches(st), 2 * st->ub));
   return SQS_OK;
 }
 
@@ -651,7 +701,7 @@ sqs_status run_hashed(sqs_state* st, const Gate1& g, double est_in, int64_t rec_
   }
   std::swap(st->cur, st->alt);
   st->cur_slot = out_slot;
-  st->ub = std::min(max_branches(st), 2 * st->ub);
+  st->ub = bound_after(st, std::min(max_branches(st), 2 * st->ub));
   return SQS_OK;
 }
 
@@ -765,7 +815,7 @@ sqs_status run_sorted(sqs_state* st, const Gate1& g, int64_t rec_idx) {
   }
   std::swap(st->cur, st->alt);
   st->cur_slot = out_slot;
-  st->ub = std::min(max_branches(st), 2 * st->ub);
+  st->ub = bound_after(st, std::min(max_branches(st), 2 * st->ub));
   return SQS_OK;
 }
 
@@ -1282,6 +1332,10 @@ sqs_status flush_all(sqs_state* st) {
 
 sqs_status ensure_scratch(sqs_state* st, size_t bytes) {
   if (st->scratch_bytes >= bytes && st->scratch) return SQS_OK;
+  if (st->capturing) {
+    st->capture_err = SQS_ERR_STATE;
+    return fail(st, SQS_ERR_STATE, "scratch allocation inside a graph capture");
+  }
   dfree(st, st->scratch);
   st->scratch = (double*)dalloc(st, bytes);
   st->scratch_bytes = st->scratch ? bytes : 0;
@@ -1318,7 +1372,53 @@ sqs_status densify(sqs_state* st) {
   return SQS_OK;
 }
 
+HostSnap take_snap(const sqs_state* st) {
+  HostSnap h;
+  h.cur = st->cur;
+  h.alt = st->alt;
+  h.bk = st->bk;
+  h.cur_slot = st->cur_slot;
+  h.ub = st->ub;
+  h.call = st->call;
+  h.last_branch = st->last_branch;
+  h.writes_since = st->writes_since;
+  h.reads_since = st->reads_since;
+  h.arith_since = st->arith_since;
+  h.const_val = st->const_val;
+  h.pair_sign = st->pair_sign;
+  h.n_branch = st->n_branch;
+  h.last_target = st->last_target;
+  return h;
+}
+
+void put_snap(sqs_state* st, const HostSnap& h) {
+  st->cur = h.cur;
+  st->alt = h.alt;
+  st->bk = h.bk;
+  st->cur_slot = h.cur_slot;
+  st->ub = h.ub;
+  st->call = h.call;
+  st->last_branch = h.last_branch;
+  st->writes_since = h.writes_since;
+  st->reads_since = h.reads_since;
+  st->arith_since = h.arith_since;
+  st->const_val = h.const_val;
+  st->pair_sign = h.pair_sign;
+  st->n_branch = h.n_branch;
+  st->last_target = h.last_target;
+}
+
 }  // namespace
+
+// A captured sequence of calls: the CUDA graph, and the host bookkeeping
+// (buffer roles, count slot and bound, per-qubit history) before and after.
+struct sqs_graph {
+  sqs_state* st = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  HostSnap entry, exit;
+  uint64_t launches = 0;
+};
 
 extern "C" {
 
@@ -1550,6 +1650,10 @@ sqs_status sqs_apply_phase(sqs_state* st, const sqs_ctrl* pred, uint32_t n_pred,
 
 sqs_status sqs_table_create(sqs_state* st, const void* host_entries, uint64_t n_entries,
                             uint32_t entry_bytes, sqs_table** out) {
+  {
+    sqs_status g = no_capture(st, "sqs_table_create");
+    if (g != SQS_OK) return g;
+  }
   sqs_status s = check_usable(st);
   if (s != SQS_OK) return s;
   if (!out || (n_entries && !host_entries) ||
@@ -1666,6 +1770,10 @@ sqs_status sqs_probabilities_device(sqs_state* st, uint32_t reg, double* probs_d
 }
 
 sqs_status sqs_probabilities(sqs_state* st, uint32_t reg, double* probs, double* norm2) {
+  {
+    sqs_status g = no_capture(st, "sqs_probabilities");
+    if (g != SQS_OK) return g;
+  }
   sqs_status s = flush_all(st);
   if (s != SQS_OK) return s;
   if (reg >= st->width.size() || (probs && st->width[reg] > 26))
@@ -1690,6 +1798,10 @@ sqs_status sqs_probabilities(sqs_state* st, uint32_t reg, double* probs, double*
 }
 
 sqs_status sqs_nnz(sqs_state* st, uint64_t* out) {
+  {
+    sqs_status g = no_capture(st, "sqs_nnz");
+    if (g != SQS_OK) return g;
+  }
   sqs_status s = flush_all(st);
   if (s != SQS_OK) return s;
   if (!out) return fail(st, SQS_ERR_ARG, "null output");
@@ -1700,6 +1812,10 @@ sqs_status sqs_nnz(sqs_state* st, uint64_t* out) {
 }
 
 sqs_status sqs_peak_nnz(sqs_state* st, uint64_t* out) {
+  {
+    sqs_status g = no_capture(st, "sqs_peak_nnz");
+    if (g != SQS_OK) return g;
+  }
   sqs_status s = flush_all(st);
   if (s != SQS_OK) return s;
   if (!out) return fail(st, SQS_ERR_ARG, "null output");
@@ -1710,6 +1826,10 @@ sqs_status sqs_peak_nnz(sqs_state* st, uint64_t* out) {
 }
 
 sqs_status sqs_export(sqs_state* st, uint64_t* keys, double* amps, uint64_t cap, uint64_t* n) {
+  {
+    sqs_status g = no_capture(st, "sqs_export");
+    if (g != SQS_OK) return g;
+  }
   sqs_status s = flush_all(st);
   if (s != SQS_OK) return s;
   if (!n) return fail(st, SQS_ERR_ARG, "null count");
@@ -1749,6 +1869,10 @@ sqs_status sqs_export(sqs_state* st, uint64_t* keys, double* amps, uint64_t cap,
 }
 
 sqs_status sqs_import(sqs_state* st, const uint64_t* keys, const double* amps, uint64_t n) {
+  {
+    sqs_status g = no_capture(st, "sqs_import");
+    if (g != SQS_OK) return g;
+  }
   sqs_status s = check_usable(st);
   if (s != SQS_OK) return s;
   if (n && (!keys || !amps)) return fail(st, SQS_ERR_ARG, "null buffers");
@@ -1807,6 +1931,10 @@ sqs_status sqs_import(sqs_state* st, const uint64_t* keys, const double* amps, u
 }
 
 sqs_status sqs_sync(sqs_state* st) {
+  {
+    sqs_status g = no_capture(st, "sqs_sync");
+    if (g != SQS_OK) return g;
+  }
   sqs_status s = flush_all(st);
   if (s != SQS_OK) return s;
   return sync_ctl(st);
@@ -1872,6 +2000,10 @@ sqs_status sqs_state_record(sqs_state* st, uint32_t enable) {
 }
 
 sqs_status sqs_state_read_records(sqs_state* st, float* X, float* y, uint32_t cap, uint32_t* n) {
+  {
+    sqs_status g = no_capture(st, "sqs_state_read_records");
+    if (g != SQS_OK) return g;
+  }
   if (!st || !n || (cap && (!X || !y))) return SQS_ERR_ARG;
   sqs_status s = flush_all(st);
   if (s != SQS_OK) return s;
@@ -1898,6 +2030,96 @@ sqs_status sqs_state_read_records(sqs_state* st, float* X, float* y, uint32_t ca
   *n = w;
   st->rec_x.clear();
   return SQS_OK;
+}
+
+sqs_status sqs_capture_begin(sqs_state* st, uint64_t static_bound) {
+  sqs_status s = check_usable(st);
+  if (s != SQS_OK) return s;
+  if (st->capturing) return fail(st, SQS_ERR_ARG, "a capture is already open");
+  if (st->flags & (SQS_SIZING_LEARNED | SQS_MERGE_SORT | SQS_MERGE_CLUSTER | SQS_MERGE_TUNED))
+    return fail(st, SQS_ERR_ARG, "graph capture runs the bucket merge with exact sizing");
+  if (static_bound == 0 || static_bound > max_branches(st))
+    return fail(st, SQS_ERR_ARG, "static bound out of range");
+  if (st->stream == nullptr)
+    return fail(st, SQS_ERR_ARG, "graph capture needs a stream other than the legacy default");
+  // Buffers for every operation on up to static_bound branches.
+  const uint64_t B = std::max<uint64_t>(1, (static_bound + 1535) / 1536);
+  const uint64_t cap = std::max<uint64_t>(B << kSegLog2, 2 * static_bound + 8192);
+  if (!ensure_store(st, st->cur, cap) || !ensure_store(st, st->alt, cap) ||
+      !ensure_store(st, st->bk, B << kBucketLog2))
+    return st->sticky = fail(st, SQS_ERR_OOM, "cannot size buffers for the capture");
+  s = sqs_state_reset(st);  // the state the graph starts from, now
+  if (s != SQS_OK) return s;
+  st->entry_snap = take_snap(st);
+  st->launches_at_capture = st->launches;
+  cudaError_t e = cudaStreamBeginCapture(st->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(st, e, "begin capture");
+  st->capturing = true;
+  st->static_ub = static_bound;
+  st->capture_err = SQS_OK;
+  return sqs_state_reset(st);  // ... and the graph's first node
+}
+
+sqs_status sqs_capture_end(sqs_state* st, sqs_graph** out) {
+  if (!st || !out) return SQS_ERR_ARG;
+  if (!st->capturing) return fail(st, SQS_ERR_ARG, "no capture is open");
+  sqs_status s = st->sticky == SQS_OK ? run_pending(st, false) : st->sticky;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st->stream, &graph);
+  const uint64_t launches = st->launches - st->launches_at_capture;
+  HostSnap exit_snap = take_snap(st);
+  st->capturing = false;
+  st->static_ub = 0;
+  put_snap(st, st->entry_snap);  // nothing ran: the device holds the entry state
+  st->launches = st->launches_at_capture;
+  st->pending.clear();
+  if (s == SQS_OK && st->capture_err != SQS_OK) s = st->capture_err;
+  if (s == SQS_OK && (e != cudaSuccess || !graph)) s = SQS_ERR_CUDA;
+  cudaGraphExec_t exec = nullptr;
+  if (s == SQS_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) s = SQS_ERR_CUDA;
+  if (s != SQS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    st->sticky = SQS_OK;
+    return fail(st, s, "capture failed (%s)", st->err.c_str());
+  }
+  sqs_graph* g = new sqs_graph();
+  g->st = st;
+  g->graph = graph;
+  g->exec = exec;
+  g->entry = st->entry_snap;
+  g->exit = std::move(exit_snap);
+  g->launches = launches;
+  *out = g;
+  return SQS_OK;
+}
+
+sqs_status sqs_graph_launch(sqs_state* st, sqs_graph* g) {
+  sqs_status s = check_usable(st);
+  if (s != SQS_OK) return s;
+  if (!g || g->st != st) return fail(st, SQS_ERR_ARG, "graph of another state");
+  if (st->capturing) return fail(st, SQS_ERR_STATE, "graph launch inside a capture");
+  // The graph writes the buffers it was captured with, in their roles then.
+  const void* now[3] = {st->cur.k0, st->alt.k0, st->bk.k0};
+  const void* then[3] = {g->entry.cur.k0, g->entry.alt.k0, g->entry.bk.k0};
+  for (const void* p : then)
+    if (std::find(std::begin(now), std::end(now), p) == std::end(now))
+      return fail(st, SQS_ERR_STATE, "the state's buffers changed since the capture");
+  st->pending.clear();
+  st->lazy.clear();
+  put_snap(st, g->entry);
+  cudaError_t e = cudaGraphLaunch(g->exec, st->stream);
+  if (e != cudaSuccess) return cuda_fail(st, e, "graph launch");
+  put_snap(st, g->exit);
+  st->launches += g->launches;
+  return SQS_OK;
+}
+
+void sqs_graph_destroy(sqs_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
 }
 
 sqs_status sqs_state_stats(const sqs_state* st, sqs_stats* out) {

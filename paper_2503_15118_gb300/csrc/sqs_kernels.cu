@@ -83,6 +83,10 @@ __global__ void __launch_bounds__(kStreamThreads)
   const uint64_t n_dense = ctl->cnt[in_slot];
   const uint64_t chunk = 1ull << out.seg_log2;
   const unsigned int lane = threadIdx.x & 31u;
+  if (!in.seg_cnt && n_dense > ((uint64_t)out.n_seg << out.seg_log2)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) raise_err(ctl, kErrCapacity, seq, n_dense);
+    return;
+  }
   // Every output segment gets its count written, including those past the
   // device-side count (the host sized them from an upper bound).
   for (uint64_t c = blockIdx.x; c < out.n_seg; c += gridDim.x) {
@@ -376,6 +380,12 @@ __global__ void __launch_bounds__(kStreamThreads)
   }
   const uint64_t n_dense = ctl->cnt[in_slot];
   const uint64_t chunk = 1ull << kExpandChunkLog2;
+  // A dense input longer than the chunks the host sized from its bound (a
+  // static bound the state outgrew) is an error, never a partial pass.
+  if (!in.seg_cnt && n_dense > (n_chunks << kExpandChunkLog2)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) raise_err(ctl, kErrCapacity, seq, n_dense);
+    return;
+  }
   // Chunks per input segment (segments are at least one chunk long).
   const uint32_t cps_log2 = in.seg_cnt ? in.seg_log2 - kExpandChunkLog2 : 0u;
   const K bmask = bit_mask<KW>(g.t);

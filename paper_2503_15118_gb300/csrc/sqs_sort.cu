@@ -83,6 +83,10 @@ __global__ void __launch_bounds__(kSortThreads)
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, *n_ptr);
   }
   const uint64_t n_dense = in.seg_cnt ? 0ull : *n_ptr;
+  if (n_dense > n_tiles * (uint64_t)kSortTile) {  // tiles sized from a bound the state outgrew
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, kErrCapacity);
+    return;
+  }
   for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     h[threadIdx.x] = 0u;
     uint64_t base;

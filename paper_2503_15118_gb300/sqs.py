@@ -92,6 +92,10 @@ SIGNATURES = {
     "sqs_qram_load": (_S, [_P, _u32, _u32, _P]),
     "sqs_qram_unload": (_S, [_P, _u32, _u32, _P]),
     "sqs_qram_load_span": (_S, [_P, _u32, _u32, _u32, _P]),
+    "sqs_capture_begin": (_S, [_P, _u64]),
+    "sqs_capture_end": (_S, [_P, ctypes.POINTER(ctypes.c_void_p)]),
+    "sqs_graph_launch": (_S, [_P, _P]),
+    "sqs_graph_destroy": (None, [_P]),
     "sqs_qram_unload_span": (_S, [_P, _u32, _u32, _u32, _P]),
     "sqs_prune": (_S, [_P, _dbl, _UP]),
     "sqs_probabilities": (_S, [_P, _u32, _DP, _DP]),
@@ -439,11 +443,54 @@ class State:
         else:
             raise ValueError(f"unknown gate {op!r}")
 
+    # --- CUDA-graph capture (include/sqs.h) -----------------------------------
+    def capture_begin(self, static_bound):
+        self._chk(self.lib.sqs_capture_begin(self.h, int(static_bound)))
+
+    def capture_end(self):
+        g = ctypes.c_void_p()
+        self._chk(self.lib.sqs_capture_end(self.h, ctypes.byref(g)))
+        return Graph(self, g)
+
+    def capture(self, circ, static_bound):
+        """Captures |0...0> followed by the circuit's gates as one graph."""
+        self.capture_begin(static_bound)
+        try:
+            self.run(circ)
+        except SqsError:
+            try:
+                self.capture_end()
+            except SqsError:
+                pass
+            raise
+        return self.capture_end()
+
     def run(self, circ, upto=None):
         tables = circ.get("tables", ())
         for g in circ["gates"] if upto is None else circ["gates"][:upto]:
             self.apply(g, tables)
         return self
+
+
+class Graph:
+    """A captured circuit (sqs_capture_begin / _end); launch() replays it."""
+
+    def __init__(self, state, handle):
+        self.state, self.h = state, handle
+
+    def launch(self):
+        self.state._chk(self.state.lib.sqs_graph_launch(self.state.h, self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.state.lib.sqs_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Predictor:
