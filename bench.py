@@ -365,6 +365,57 @@ def extra_workloads(stream, flush, args):
                                                   "kernel_ms_per_step": tms}
             out[name + ("_f32" if amp32 else "_f64")] = entry
             st.close()
+    out.update(graph_workloads(stream, stored, cfg5, args))
+    return out
+
+
+def graph_workloads(stream, stored, cfg5, args):
+    """The same circuit issued call by call against replayed as one captured
+    CUDA graph: config 1 (one instance, launch-bound) and the 256-system
+    batched walk (2 steps)."""
+    import torch
+
+    from paper_2503_15118_gb300 import qlss, sqs
+    out = {}
+    c1 = W.config1_from_stored(stored)
+    for name, circ in (("config1_single", c1), ("qlss_batch256_2steps", qlss.batched_circuit(cfg5, 2))):
+        st = sqs.State(circ["widths"], stream=stream.cuda_stream, eps=circ["eps"])
+        st.run(circ)  # tables exist before the capture
+        st.sync()
+        st.reset()
+        units = 0
+        for g in circ["gates"]:
+            units += st.nnz()
+            st.apply(g, circ["tables"])
+        peak = st.peak_nnz()
+        graph = st.capture(circ, static_bound=2 * peak)
+        reps = max(5, args.steps)
+        res = {}
+        for mode in ("eager", "graph"):
+            for _ in range(3):
+                if mode == "graph":
+                    graph.launch()
+                else:
+                    st.reset()
+                    st.run(circ)
+            st.sync()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                if mode == "graph":
+                    graph.launch()
+                else:
+                    st.reset()
+                    st.run(circ)
+            b.record(stream)
+            torch.cuda.synchronize()
+            res[mode] = a.elapsed_time(b) / reps
+        out[name + "_graph"] = {"value": units / (res["graph"] / 1e3), "unit": UNIT,
+                                "ms_per_step": res["graph"], "eager_ms_per_step": res["eager"],
+                                "eager_value": units / (res["eager"] / 1e3),
+                                "units_per_step": units, "static_bound": 2 * peak}
+        graph.close()
+        st.close()
     return out
 
 

@@ -215,6 +215,16 @@ def config1_batch(stored, inst_bits=16, seed=1):
             "name": f"config1-batch{n_inst}-seed{seed}"}
 
 
+def config1_from_stored(stored, seed=1):
+    """Config 1 itself from the stored gate list (registers addr, data, anc)."""
+    ident = {0: 0, 1: 1, 2: 2}
+    gates = [("qload", 0, 1, 0) if g[0] == "qload" else _decode_gate(g, ident)
+             for g in stored["gates"]]
+    table = config1_prefix(seed)[0]["tables"][0]
+    return {"widths": list(stored["widths"]), "eps": stored["eps"], "tables": [table],
+            "gates": gates, "name": f"config1-seed{seed}"}
+
+
 def config1_instance_table(batch, i):
     """The 256-entry table instance i of a config-1 batch loads."""
     return batch["tables"][0][i * 256:(i + 1) * 256]
