@@ -117,14 +117,22 @@ typedef struct {
  *   SQS_PERM_SUB_CONST  reg := (reg - constant) mod 2^{w_reg}
  *   SQS_PERM_SWAP       exchange reg and src_reg (equal widths)
  * Quantum arithmetic as oracles is stated in Sec. II.D.1 ("addition,
- * multiplication, and division ... implemented by the same method"). */
+ * multiplication, and division ... implemented by the same method"): the
+ * multiply-add, multiply-by-odd-constant and divide-XOR kinds are those oracles
+ * in their reversible forms (the sources, and the destination's previous value,
+ * determine the result, so each map is a bijection on keys).  Sources must be
+ * registers other than the destination; controls may not sit inside it. */
 typedef enum {
   SQS_PERM_X = 0,
   SQS_PERM_ADD_REG = 1,
   SQS_PERM_SUB_REG = 2,
   SQS_PERM_ADD_CONST = 3,
   SQS_PERM_SUB_CONST = 4,
-  SQS_PERM_SWAP = 5
+  SQS_PERM_SWAP = 5,
+  SQS_PERM_MUL_ADD = 6,   /* reg := (reg + src_reg * src2_reg) mod 2^{w_reg}        */
+  SQS_PERM_MUL_CONST = 7, /* reg := (reg * constant) mod 2^{w_reg}, constant odd      */
+  SQS_PERM_DIV_XOR = 8    /* reg := reg XOR (src_reg / src2_reg) (integer quotient,
+                             0 when src2_reg holds 0), truncated to w_reg          */
 } sqs_perm_kind;
 
 typedef struct {
@@ -135,6 +143,7 @@ typedef struct {
   uint64_t constant; /* *_CONST: added / subtracted value                 */
   uint32_t n_ctrl;   /* number of valid entries of ctrl (<= SQS_MAX_CTRL) */
   sqs_ctrl ctrl[SQS_MAX_CTRL];
+  uint32_t src2_reg; /* MUL_ADD, DIV_XOR: second source register           */
 } sqs_perm_op;
 
 /* ---- state lifetime --------------------------------------------------- */

@@ -62,6 +62,9 @@ def _bind(lib):
         "or_apply_x": (None, [P, u32, u32, CP, u32]),
         "or_apply_add": (None, [P, u32, i32, u64, i32, CP, u32]),
         "or_apply_swap": (None, [P, u32, u32, CP, u32]),
+        "or_apply_mul_add": (None, [P, u32, u32, u32, CP, u32]),
+        "or_apply_mul_const": (None, [P, u32, u64, CP, u32]),
+        "or_apply_div_xor": (None, [P, u32, u32, u32, CP, u32]),
         "or_apply_phase": (None, [P, CP, u32, dbl]),
         "or_qram": (None, [P, u32, u32, P, u64, u32]),
         "or_qram_span": (None, [P, u32, u32, u32, P, u64, u32]),
@@ -168,6 +171,18 @@ class OracleState:
         c, n = _ctrls(preds)
         self.lib.or_apply_phase(self.h, c, n, float(phi))
 
+    def mul_add(self, dst, src1, src2, ctrls=()):
+        c, n = _ctrls(ctrls)
+        self.lib.or_apply_mul_add(self.h, dst, src1, src2, c, n)
+
+    def mul_const(self, dst, const, ctrls=()):
+        c, n = _ctrls(ctrls)
+        self.lib.or_apply_mul_const(self.h, dst, int(const) & (2 ** 64 - 1), c, n)
+
+    def div_xor(self, dst, src1, src2, ctrls=()):
+        c, n = _ctrls(ctrls)
+        self.lib.or_apply_div_xor(self.h, dst, src1, src2, c, n)
+
     def qram(self, addr_reg, data_reg, table):
         """addr_reg: a register, or (first, count): the address is then the
         concatenation of consecutive registers, the first one lowest."""
@@ -249,6 +264,12 @@ class OracleState:
             self.swap(g[1], g[2], g[3])
         elif op == "phase":
             self.phase(g[1], g[2])
+        elif op == "muladd":
+            self.mul_add(g[1], g[2], g[3], g[4])
+        elif op == "mulc":
+            self.mul_const(g[1], g[2], g[3])
+        elif op == "divxor":
+            self.div_xor(g[1], g[2], g[3], g[4])
         elif op in ("qload", "qunload"):
             self.qram(g[1], g[2], tables[g[3]])
         elif op == "prune":

@@ -120,6 +120,25 @@ class DenseState:
                       | (((1 << self.widths[r2]) - 1) << self.off[r2]))
             new = (self.idx & clear) | (v2 << self.off[r1]) | (v1 << self.off[r2])
             self.permute(np.where(self._ctrl_mask(ctrls), new, self.idx))
+        elif op in ("muladd", "mulc", "divxor"):
+            # Arithmetic oracles (Sec. II.D.1), in Python integers per basis state.
+            dst = g[1]
+            w = self.widths[dst]
+            d = self._field(dst)
+            if op == "mulc":
+                r = np.array([(int(x) * int(g[2])) % (1 << w) for x in d], np.int64)
+                ctrls = g[3]
+            else:
+                a, bb = self._field(g[2]), self._field(g[3])
+                if op == "muladd":
+                    r = np.array([(int(x) + int(y) * int(z)) % (1 << w)
+                                  for x, y, z in zip(d, a, bb)], np.int64)
+                else:
+                    r = np.array([(int(x) ^ (int(y) // int(z) if z else 0)) % (1 << w)
+                                  for x, y, z in zip(d, a, bb)], np.int64)
+                ctrls = g[4]
+            new = (self.idx & ~(((1 << w) - 1) << self.off[dst])) | (r << self.off[dst])
+            self.permute(np.where(self._ctrl_mask(ctrls), new, self.idx))
         elif op == "phase":
             _, preds, phi = g
             self.psi[self._ctrl_mask(preds)] *= np.exp(1j * phi)
@@ -222,6 +241,18 @@ def _perm_image(widths, off, g, x, tables):
         if not ctrl_ok(ctrls):
             return x
         return with_field(with_field(x, r1, field(r2)), r2, field(r1))
+    if op == "muladd":
+        _, dst, a, b, ctrls = g
+        return with_field(x, dst, field(dst) + field(a) * field(b)) if ctrl_ok(ctrls) else x
+    if op == "mulc":
+        _, dst, c, ctrls = g
+        return with_field(x, dst, field(dst) * c) if ctrl_ok(ctrls) else x
+    if op == "divxor":
+        _, dst, a, b, ctrls = g
+        if not ctrl_ok(ctrls):
+            return x
+        q = field(a) // field(b) if field(b) else 0
+        return with_field(x, dst, field(dst) ^ q)
     if op in ("qload", "qunload"):
         _, areg, dreg, ti = g
         t = tables[ti]

@@ -218,6 +218,40 @@ void or_apply_add(OState* s, uint32_t dst, int32_t src_reg, uint64_t constant, i
   });
 }
 
+// The arithmetic oracles of Sec. II.D.1 in reversible form: multiply-add
+// dst := (dst + a b) mod 2^w, multiply by an odd constant dst := (dst c) mod
+// 2^w, and divide-XOR dst := dst XOR floor(a / b) (0 when b = 0).
+void or_apply_mul_add(OState* s, uint32_t dst, uint32_t src1, uint32_t src2, const OCtrl* ctrl,
+                      uint32_t n_ctrl) {
+  const u128 m = low_mask(s->width[dst]);
+  permute(s, [&](u128 k) {
+    if (!controls_hold(s, k, ctrl, n_ctrl)) return k;
+    const u128 d = get_reg(s, k, dst);
+    const u128 a = get_reg(s, k, src1), b = get_reg(s, k, src2);
+    return set_reg(s, k, dst, (uint64_t)((d + a * b) & m));
+  });
+}
+
+void or_apply_mul_const(OState* s, uint32_t dst, uint64_t c, const OCtrl* ctrl, uint32_t n_ctrl) {
+  const u128 m = low_mask(s->width[dst]);
+  permute(s, [&](u128 k) {
+    if (!controls_hold(s, k, ctrl, n_ctrl)) return k;
+    const u128 d = get_reg(s, k, dst);
+    return set_reg(s, k, dst, (uint64_t)((d * (u128)c) & m));
+  });
+}
+
+void or_apply_div_xor(OState* s, uint32_t dst, uint32_t src1, uint32_t src2, const OCtrl* ctrl,
+                      uint32_t n_ctrl) {
+  const u128 m = low_mask(s->width[dst]);
+  permute(s, [&](u128 k) {
+    if (!controls_hold(s, k, ctrl, n_ctrl)) return k;
+    const uint64_t a = get_reg(s, k, src1), b = get_reg(s, k, src2);
+    const uint64_t q = b ? a / b : 0;
+    return set_reg(s, k, dst, (uint64_t)(((u128)get_reg(s, k, dst) ^ (u128)q) & m));
+  });
+}
+
 // Exchange of two registers of equal width.
 void or_apply_swap(OState* s, uint32_t r1, uint32_t r2, const OCtrl* ctrl, uint32_t n_ctrl) {
   permute(s, [&](u128 k) {

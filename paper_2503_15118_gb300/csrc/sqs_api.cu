@@ -959,7 +959,14 @@ void note_op(sqs_state* st, const HostOp& h) {
         clear(d.sel_bit);
         break;
       case sqs::OP_ADD_CONST:
+      case sqs::OP_MUL_CONST:
         for (uint32_t b = 0; b < d.dst_w; ++b) clear(d.dst_off + b);
+        break;
+      case sqs::OP_MUL_ADD:
+      case sqs::OP_DIV_XOR:
+        for (uint32_t b = 0; b < d.dst_w; ++b) clear(d.dst_off + b);
+        for (uint32_t b = 0; b < d.src_w; ++b) clear(d.src_off + b);
+        for (uint32_t b = 0; b < d.src2_w; ++b) clear(d.src2_off + b);
         break;
       case sqs::OP_ADD_REG:
       case sqs::OP_SUB_REG:
@@ -992,6 +999,13 @@ void note_op(sqs_state* st, const HostOp& h) {
       note_field_write(st, d.dst_off, d.dst_w, true);
       break;
     case sqs::OP_ADD_CONST:
+    case sqs::OP_MUL_CONST:
+      note_field_write(st, d.dst_off, d.dst_w, true);
+      break;
+    case sqs::OP_MUL_ADD:
+    case sqs::OP_DIV_XOR:
+      note_field_read(st, d.src_off, d.src_w);
+      note_field_read(st, d.src2_off, d.src2_w);
       note_field_write(st, d.dst_off, d.dst_w, true);
       break;
     case sqs::OP_SWAP:
@@ -1613,6 +1627,30 @@ sqs_status sqs_apply_perm(sqs_state* st, const sqs_perm_op* ops, uint32_t n_ops)
                                               : sqs::OP_SWAP;
         o.src_off = st->offset[p.src_reg];
         o.src_w = st->width[p.src_reg];
+        break;
+      }
+      case SQS_PERM_MUL_ADD:
+      case SQS_PERM_DIV_XOR: {
+        if (p.src_reg >= nr || p.src_reg == p.reg || p.src2_reg >= nr || p.src2_reg == p.reg)
+          return fail(st, SQS_ERR_ARG, "op %u: bad source registers", i);
+        for (uint32_t b = 0; b < st->width[p.reg]; ++b)
+          if (ctrl_touches(cm, o.dst_off + b))
+            return fail(st, SQS_ERR_ARG, "op %u: control inside the target register", i);
+        o.kind = p.kind == SQS_PERM_MUL_ADD ? sqs::OP_MUL_ADD : sqs::OP_DIV_XOR;
+        o.src_off = st->offset[p.src_reg];
+        o.src_w = st->width[p.src_reg];
+        o.src2_off = st->offset[p.src2_reg];
+        o.src2_w = st->width[p.src2_reg];
+        break;
+      }
+      case SQS_PERM_MUL_CONST: {
+        if (!(p.constant & 1ull))
+          return fail(st, SQS_ERR_ARG, "op %u: the multiplier must be odd (a bijection)", i);
+        for (uint32_t b = 0; b < st->width[p.reg]; ++b)
+          if (ctrl_touches(cm, o.dst_off + b))
+            return fail(st, SQS_ERR_ARG, "op %u: control inside the target register", i);
+        o.kind = sqs::OP_MUL_CONST;
+        o.constant = p.constant & wm;
         break;
       }
       case SQS_PERM_ADD_CONST:

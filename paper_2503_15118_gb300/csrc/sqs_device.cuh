@@ -239,6 +239,22 @@ __device__ __forceinline__ void raise_err(Ctl* ctl, unsigned int bit, uint32_t s
 }
 
 // ---- fused operation run ---------------------------------------------------------
+// Multiply-add, multiply by a constant, divide-XOR on key fields (mod 2^w by
+// set_field's truncation).
+template <class K>
+__device__ __forceinline__ K arith_op(const DevOp& op, K k) {
+  const uint64_t d = get_field(k, op.dst_off, op.dst_w);
+  uint64_t r;
+  if (op.kind == OP_MUL_CONST) {
+    r = d * op.constant;
+  } else {
+    const uint64_t a = get_field(k, op.src_off, op.src_w);
+    const uint64_t b = get_field(k, op.src2_off, op.src2_w);
+    r = op.kind == OP_MUL_ADD ? d + a * b : d ^ (b ? a / b : 0ull);
+  }
+  return set_field<K>(k, op.dst_off, op.dst_w, r);
+}
+
 // tab: the folded factors in the storage type (shared-memory copy).
 template <int KW, class AT>
 __device__ __forceinline__ bool apply_ops(uint32_t n_ops, const DevOp* ops, const AT* tab,
@@ -289,6 +305,8 @@ __device__ __forceinline__ bool apply_ops(uint32_t n_ops, const DevOp* ops, cons
       }
     } else if (kind == OP_PRUNE) {
       if (!keep_amp(a, op.eps, (float)op.eps, op.eps2)) return false;
+    } else if (kind == OP_MUL_ADD || kind == OP_MUL_CONST || kind == OP_DIV_XOR) {
+      if (on) k = arith_op(op, k);
     }
   }
   return true;
@@ -384,6 +402,10 @@ __device__ __forceinline__ void apply_ops_n(uint32_t n_ops, const DevOp* ops, co
 #pragma unroll
       for (int q = 0; q < NI; ++q)
         if (live[q] && !keep_amp(a[q], eps, (float)eps, eps2)) live[q] = false;
+    } else if (kind == OP_MUL_ADD || kind == OP_MUL_CONST || kind == OP_DIV_XOR) {
+#pragma unroll
+      for (int q = 0; q < NI; ++q)
+        if ((k[q] & pm) == pv) k[q] = arith_op(op, k[q]);
     }
   }
 }

@@ -29,7 +29,10 @@ enum OpKind : uint32_t {
   OP_MUL = 6,        // record factor choice (bit sel of key: c1, else c0) (phases, diag U)
   OP_MUL_XOR = 7,    // the same, then key ^= xmask                     (anti-diagonal U)
   OP_TABLE = 8,      // amp *= tab[tab_off + idx] unless idx == 0; idx := 0
-  OP_PRUNE = 9       // drop the branch when |amp| < eps
+  OP_PRUNE = 9,      // drop the branch when |amp| < eps
+  OP_MUL_ADD = 10,   // dst := dst + src * src2  (mod 2^w)
+  OP_MUL_CONST = 11, // dst := dst * constant    (mod 2^w, constant odd)
+  OP_DIV_XOR = 12    // dst := dst XOR (src / src2), 0 when src2 = 0
 };
 
 struct DevOp {
@@ -39,6 +42,7 @@ struct DevOp {
   uint32_t sel_bit;         // OP_MUL*: key bit choosing c0 / c1 (128 = no choice)
   uint32_t shift;           // OP_MUL*: position of this op's outcome in the index
   uint32_t tab_off;         // OP_TABLE: first entry of this group's table
+  uint32_t src2_off, src2_w;   // OP_MUL_ADD / OP_DIV_XOR: second source field
   uint64_t pmask[2], pval[2];  // predicate: (key & pmask) == pval
   uint64_t xmask[2];           // OP_XOR / OP_MUL_XOR
   uint64_t constant;           // OP_ADD_CONST (already reduced mod 2^w); QRAM: entry bytes

@@ -19,7 +19,8 @@ OK, ERR_ARG, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = 0, -1, -2
 AMP_FP64, AMP_FP32 = 0, 1
 SIZING_EXACT, SIZING_LEARNED = 0, 2
 MERGE_AUTO, MERGE_HASH, MERGE_SORT, MERGE_CLUSTER, MERGE_TUNED, MERGE_PLAIN = 0, 4, 8, 16, 32, 64
-PERM_X, PERM_ADD_REG, PERM_SUB_REG, PERM_ADD_CONST, PERM_SUB_CONST, PERM_SWAP = range(6)
+(PERM_X, PERM_ADD_REG, PERM_SUB_REG, PERM_ADD_CONST, PERM_SUB_CONST, PERM_SWAP, PERM_MUL_ADD,
+ PERM_MUL_CONST, PERM_DIV_XOR) = range(9)
 MAX_CTRL = 8     # controls inline in one permutation operation
 MAX_PRED = 128   # controls / predicates passed as an array
 
@@ -37,7 +38,8 @@ class Ctrl(ctypes.Structure):
 class PermOp(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("reg", ctypes.c_uint32), ("bit", ctypes.c_uint32),
                 ("src_reg", ctypes.c_uint32), ("constant", ctypes.c_uint64),
-                ("n_ctrl", ctypes.c_uint32), ("ctrl", Ctrl * MAX_CTRL)]
+                ("n_ctrl", ctypes.c_uint32), ("ctrl", Ctrl * MAX_CTRL),
+                ("src2_reg", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -261,10 +263,13 @@ class State:
                                          flat.ctypes.data_as(_DP), c, n))
 
     def perm(self, ops):
+        """ops: (kind, reg, bit, src_reg, constant, ctrls[, src2_reg]) tuples."""
         arr = (PermOp * max(1, len(ops)))()
-        for i, (kind, reg, bit, src, const, ctrls) in enumerate(ops):
+        for i, op in enumerate(ops):
+            kind, reg, bit, src, const, ctrls = op[:6]
             arr[i].kind, arr[i].reg, arr[i].bit = kind, reg, bit
             arr[i].src_reg, arr[i].constant = src, int(const) & (2 ** 64 - 1)
+            arr[i].src2_reg = op[6] if len(op) > 6 else 0
             arr[i].n_ctrl = len(ctrls)
             for j, c in enumerate(ctrls):
                 arr[i].ctrl[j] = Ctrl(int(c[0]), int(c[1]), int(c[2]) if len(c) > 2 else 1)
@@ -434,6 +439,12 @@ class State:
             self.perm([(PERM_SWAP, g[1], 0, g[2], 0, tuple(g[3]))])
         elif op == "phase":
             self.phase(g[1], g[2])
+        elif op == "muladd":
+            self.perm([(PERM_MUL_ADD, g[1], 0, g[2], 0, tuple(g[4]), g[3])])
+        elif op == "mulc":
+            self.perm([(PERM_MUL_CONST, g[1], 0, 0, g[2], tuple(g[3]))])
+        elif op == "divxor":
+            self.perm([(PERM_DIV_XOR, g[1], 0, g[2], 0, tuple(g[4]), g[3])])
         elif op == "qload":
             self.qram_load(g[1], g[2], tables[g[3]])
         elif op == "qunload":

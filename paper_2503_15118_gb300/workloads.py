@@ -16,6 +16,9 @@ and each gate is a tuple:
     ("x", reg, bit, ctrls)                      X / CNOT / Toffoli (FlipBool)
     ("add"|"sub", dst, src_reg, const, ctrls)   dst +-= src (src_reg<0: const)
     ("swap", r1, r2, ctrls)                     register exchange
+    ("muladd", dst, a, b, ctrls)                dst += a * b (mod 2^w)
+    ("mulc", dst, c, ctrls)                     dst *= c (mod 2^w), c odd
+    ("divxor", dst, a, b, ctrls)                dst ^= a // b (0 when b = 0)
     ("phase", preds, phi)                       a *= e^{i phi} where preds hold
     ("qload"|"qunload", addr_reg, data_reg, t)  data ^= tables[t][addr]; addr_reg
                                                 may be (first, count): the address
@@ -96,6 +99,14 @@ def _draw_gate(rng, kinds, qs, widths, n_tables, max_ctrl=2):
         return ("swap", a, b, ())
     if k == "qram":
         return ("qload", 0, 1, int(rng.integers(n_tables)))
+    if k in ("muladd", "divxor"):
+        if len(widths) < 3:
+            return ("x", t[0], t[1], ())
+        dst, a, b = (int(r) for r in rng.choice(len(widths), size=3, replace=False))
+        return (k, dst, a, b, ())
+    if k == "mulc":
+        dst = int(rng.integers(len(widths)))
+        return ("mulc", dst, int(rng.integers(0, 2 ** min(widths[dst], 62))) | 1, ())
     raise ValueError(k)
 
 
@@ -124,6 +135,11 @@ def inverse_gate(g):
         return ("add",) + tuple(g[1:])
     if op == "phase":
         return ("phase", g[1], -g[2])
+    if op == "divxor":
+        return g
+    if op == "mulc":
+        # the inverse of an odd c modulo 2^64 is its inverse modulo 2^w too
+        return ("mulc", g[1], pow(int(g[2]), -1, 2 ** 64), g[3])
     raise ValueError(op)
 
 

@@ -67,6 +67,9 @@ GATES_64 = [
     ("sub", 0, -1, 12345, ((3, 0, 1),)),
     ("swap", 0, 3, ()),
     ("phase", ((1, 4, 1), (2, 8, 0)), 0.77),
+    ("muladd", 0, 1, 2, ()),
+    ("mulc", 3, 12345, ((0, 2, 1),)),
+    ("divxor", 1, 2, 3, ((0, 5, 0),)),
 ]
 
 
@@ -109,6 +112,9 @@ GATES_128 = [
     ("x", 2, 31, ((1, 0, 1),)),
     ("swap", 1, 2, ()),
     ("phase", ((2, 30, 1),), -1.3),
+    ("muladd", 2, 0, 1, ()),
+    ("divxor", 1, 2, 0, ()),
+    ("mulc", 2, 0xDEADBEEF, ()),
 ]
 
 
@@ -148,11 +154,12 @@ def test_qram_load_unload(sqs):
 
 def _kinds_all():
     return ("x", "cx", "ccx", "ry", "cry", "phase", "cphase", "h", "ch", "u1q", "cu1q", "diag",
-            "adiag", "add", "sub", "swap", "qram")
+            "adiag", "add", "sub", "swap", "qram", "muladd", "mulc", "divxor")
 
 
 # Wide registers use a mix where branching gates are rare, so the state stays small.
-SPARSE_KINDS = ("x", "cx", "ccx", "add", "sub", "swap", "phase", "cphase", "qram") * 3 + (
+SPARSE_KINDS = ("x", "cx", "ccx", "add", "sub", "swap", "phase", "cphase", "qram", "muladd", "mulc",
+                "divxor") * 3 + (
     "h", "ry", "cu1q")
 
 

@@ -336,3 +336,47 @@ def test_mlp_oracle_forward_closed_form():
     p[-1] = 0.37
     y, _, _ = mlp.forward(p, np.ones((3, mlp.F)))
     assert np.allclose(y, 0.37)
+
+
+ARITH_KINDS = ("x", "cx", "h", "ry", "muladd", "mulc", "divxor", "add")
+
+
+@pytest.mark.parametrize("seed", [31, 32, 33])
+def test_arithmetic_oracles_match_dense(seed):
+    """Multiply-add, multiply by an odd constant and divide-XOR (the arithmetic
+    oracles of Sec. II.D.1) on the std::map oracle agree with the independent
+    dense statevector."""
+    widths = [3, 3, 3, 3]
+    circ = W.random_circuit(widths, 60, seed, kinds=ARITH_KINDS)
+    assert any(g[0] in ("muladd", "mulc", "divxor") for g in circ["gates"])
+    o = oracle.run_circuit(circ)
+    d = dense.run_dense(circ)
+    got = o.to_dict()
+    for k in range(1 << sum(widths)):
+        assert abs(got.get(k, 0) - d.psi[k]) < 1e-12
+
+
+def test_arithmetic_oracles_are_bijections_and_invert():
+    widths = [4, 4, 4]
+    rng = np.random.default_rng(4)
+    keys = np.arange(1 << 12, dtype=np.uint64)
+    amps = rng.standard_normal(1 << 12) + 1j * rng.standard_normal(1 << 12)
+    for gate in [("muladd", 0, 1, 2, ()), ("mulc", 1, 11, ((0, 0, 1),)), ("divxor", 2, 0, 1, ())]:
+        o = oracle.OracleState(widths)
+        o.import_(keys, np.zeros_like(keys), amps)
+        o.apply(gate)
+        d = o.to_dict()
+        assert len(d) == 1 << 12   # a bijection on the full space
+        assert sorted(abs(v) for v in d.values()) == sorted(abs(a) for a in amps)
+        if gate[0] != "muladd":
+            o.apply(W.inverse_gate(gate))
+            back = o.to_dict()
+            assert all(back[int(k)] == a for k, a in zip(keys, amps))
+    # multiply-add on a basis state: 5 + 3 * 7 = 26 = 10 (mod 16)
+    o = oracle.OracleState(widths)
+    o.import_(np.array([5 | (3 << 4) | (7 << 8)], np.uint64), np.zeros(1, np.uint64), np.ones(1))
+    o.apply(("muladd", 0, 1, 2, ()))
+    assert set(o.to_dict()) == {10 | (3 << 4) | (7 << 8)}
+    o.apply(("divxor", 1, 2, 0, ()))           # 3 ^ (7 // 10) = 3
+    o.apply(("divxor", 2, 0, 1, ()))           # 7 ^ (10 // 3) = 7 ^ 3 = 4
+    assert set(o.to_dict()) == {10 | (3 << 4) | (4 << 8)}
