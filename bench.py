@@ -298,6 +298,19 @@ def per_gate(args):
 
 MERGE_KERNELS = ("k_partition", "k_pair", "k_expand", "k_fold", "k_bin", "k_pair_cluster",
                  "k_rsort_pass", "k_rsort_merge")
+INTERFERENCE_KERNELS = MERGE_KERNELS + ("k_group_count", "k_group")
+
+
+def _interference(g):
+    """Whether a gate tuple is an interference step (a merge): H, RY, a
+    register-valued RY, or a u1q that is neither diagonal nor anti-diagonal."""
+    if g[0] in ("h", "ry", "ry_reg"):
+        return True
+    if g[0] == "u1q":
+        import numpy as np
+        m = np.asarray(g[3]).reshape(2, 2)
+        return not ((m[0, 1] == 0 and m[1, 0] == 0) or (m[0, 0] == 0 and m[1, 1] == 0))
+    return False
 
 
 def extra_workloads(stream, flush, args):
@@ -306,7 +319,8 @@ def extra_workloads(stream, flush, args):
       each loading its own QRAM table, with the HBM-roofline fraction of its
       interference steps (every expand / merge launch: inputs read plus
       outputs written, over their event-timed duration);
-    - the linear-system walk (one system, N = 1024), 4 walk steps;
+    - the linear-system walk (one system, N = 1024), 4 walk steps, for a
+      positive-definite and for a non-Hermitian A;
     - the batched walk (256 systems of sizes 8..128), 2 walk steps;
     each in FP64 and FP32 storage."""
     from paper_2503_15118_gb300 import qlss, sqs
@@ -317,12 +331,17 @@ def extra_workloads(stream, flush, args):
     cfg5 = qlss.config5(seed=5)
     work = (("config1_batch65536", W.config1_batch(stored, inst_bits=16), 1 << 26),
             ("qlss_walk_N1024_4steps", qlss.walk_circuit(cfg4, n_steps=4), 1 << 23),
+            ("qlss_walk_nonherm_N1024_4steps",
+             qlss.walk_circuit_nh(qlss.config4_nonherm(seed=4), n_steps=4), 1 << 24),
             ("qlss_batch256_2steps", qlss.batched_circuit(cfg5, 2), 1 << 23))
     hbm, _ = peaks()
     for name, circ, hint in work:
-        for amp32 in (False, True):
+        # The walks also run with every interference step alone, against
+        # their fused runs (the reflections about |b>).
+        forms = [(False, 0), (True, 0)] + ([(False, sqs.FUSE_OFF)] if name.startswith("qlss") else [])
+        for amp32, fuse_off in forms:
             st = sqs.State(circ["widths"], capacity_hint=hint, stream=stream.cuda_stream,
-                           eps=circ["eps"], amp32=amp32)
+                           eps=circ["eps"], amp32=amp32, merge=fuse_off)
 
             def step():
                 st.reset()
@@ -347,25 +366,77 @@ def extra_workloads(stream, flush, args):
             st.trace_read()
             step()
             st.sync()
+            r0 = st.stats()["runs_fused"]
             recs, _ = st.trace_read(cap=1 << 16)
+            entry["fused_runs_per_step"] = st.stats()["runs_fused"] - r0
+            # Algorithmic bytes: every interference gate reads its input and
+            # writes its output once, (N + M) * Rb, whichever kernels (and
+            # however many passes, or one fused run for several gates)
+            # execute it; time: every launch of those kernels.
             rb = 8 * st.kw + (8 if amp32 else 16)
-            byts, tms = 0.0, 0.0
-            for kname, call, kms in recs:
-                gi = call - 2
-                if kname in MERGE_KERNELS and 0 <= gi < len(circ["gates"]):
-                    if kname in ("k_partition", "k_bin", "k_rsort_pass"):
-                        byts += 2.0 * n_in[gi] * rb
-                    else:
-                        byts += float(n_in[gi] + n_in[gi + 1]) * rb
-                    tms += kms
+            byts = sum(float(n_in[i] + n_in[i + 1]) * rb
+                       for i, g in enumerate(circ["gates"]) if _interference(g))
+            tms = sum(kms for kname, _, kms in recs if kname in INTERFERENCE_KERNELS)
             if tms > 0:
                 gbs = byts / (tms / 1e3) / 1e9
                 entry["interference_roofline"] = {"achieved": gbs, "peak": hbm, "unit": "GB/s",
                                                   "frac": gbs / hbm,
                                                   "kernel_ms_per_step": tms}
-            out[name + ("_f32" if amp32 else "_f64")] = entry
+            out[name + ("_f32" if amp32 else "_f64") + ("_steps_alone" if fuse_off else "")] = entry
             st.close()
+    out["qlss_walk_N1024_4steps_learned"] = learned_walk(stream, flush, args, cfg4)
     out.update(graph_workloads(stream, stored, cfg5, args))
+    return out
+
+
+def learned_walk(stream, flush, args, cfg4):
+    """Learned against exact sizing on the N = 1024 walk (4 steps, FP64): the
+    predictor is trained on the walk traces of seeds 100..131 (N = 256, 2
+    steps) and run on seed 4.  Reports updates/s, host waits per step,
+    overflow re-runs, and whether the two results agree bit for bit."""
+    import numpy as np
+
+    from paper_2503_15118_gb300 import predictor, qlss, sqs
+    pred, loss, (X, _) = predictor.trained_on_walks()
+    circ = qlss.walk_circuit(cfg4, n_steps=4)
+    out = {"predictor": {"train_records": int(X.shape[0]), "train_mse": loss,
+                         "train_seeds": "100..131", "train_N": 256}}
+    states = {}
+    for mode in ("exact", "learned"):
+        st = sqs.State(circ["widths"], capacity_hint=1 << 23, stream=stream.cuda_stream,
+                       eps=circ["eps"], learned=(mode == "learned"))
+        if mode == "learned":
+            st.set_predictor(pred)
+
+        def step():
+            st.reset()
+            st.run(circ)
+
+        for _ in range(args.warmup):
+            step()
+        st.sync()
+        units = 0
+        st.reset()
+        if mode == "exact":
+            for g in circ["gates"]:
+                units += st.nnz()
+                st.apply(g, circ["tables"])
+            out["units_per_step"] = units
+        s0 = st.stats()
+        ms = _timed_steps(st, step, flush, stream, max(3, args.steps // 2))
+        s1 = st.stats()
+        out[mode] = {"value": out["units_per_step"] / (ms / 1e3), "unit": UNIT,
+                     "ms_per_step": ms,
+                     "host_waits_per_step": (s1["host_waits"] - s0["host_waits"]) / max(3, args.steps // 2),
+                     "overflow_reruns": s1["overflow_reruns"], "bytes_peak": s1["bytes_peak"]}
+        lo, hi, a = st.export()
+        o = np.lexsort((lo, hi))  # storage order depends on the bucket sizes
+        states[mode] = (lo[o], hi[o], a[o])
+        st.close()
+    pred.close()
+    (le, he, ae), (ll, hl, al) = states["exact"], states["learned"]
+    out["bit_identical"] = bool(le.shape == ll.shape and (le == ll).all() and (he == hl).all()
+                                and (ae == al).all())
     return out
 
 

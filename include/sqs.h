@@ -79,7 +79,26 @@ typedef enum {
                                      fold (a target whose every partner is
                                      known to hold +-1 times the branch's
                                      amplitude).  Results are bit-identical
-                                     either way; this flag exists to show it. */
+                                     either way; this flag exists to show it.
+                                     Also runs every interference step alone
+                                     (as SQS_FUSE_OFF).                       */
+#define SQS_FUSE_OFF 128u         /* run every interference step alone.  By
+                                     default (exact sizing, SQS_MERGE_AUTO or
+                                     SQS_MERGE_TUNED) interference steps issued
+                                     back to back on distinct target qubits,
+                                     with no other operation queued between
+                                     them and no step's controls or angle
+                                     register on another step's target, are
+                                     held and executed together when the run
+                                     ends (Sec. II.D.2: each coherent group --
+                                     the branches equal on every other qubit --
+                                     is transformed as one vector of up to
+                                     2^k entries, k <= 12).  The result is
+                                     bit-identical to the steps run one by
+                                     one, peak count included.  Runs end at
+                                     the next operation of another kind that
+                                     must execute, any read, sqs_flush, or
+                                     when they reach 12 steps.               */
 
 /*
  * One control (or predicate) qubit: bit `bit` of register `reg` must equal
@@ -290,6 +309,8 @@ uint64_t sqs_launch_count(const sqs_state* st);
 #define SQS_K_SORT 10u      /* radix-sort merge: one LSD pass (histogram, scan, scatter) */
 #define SQS_K_SORT_MERGE 11u /* radix-sort merge: neighbours combined, 2x2, prune */
 #define SQS_K_FOLD 12u      /* copy-pair fold: both children from one member   */
+#define SQS_K_GROUP_COUNT 13u /* fused run: coherent groups per bucket          */
+#define SQS_K_GROUP 14u     /* fused run: every group transformed in shared memory */
 typedef struct {
   uint32_t kernel; /* SQS_K_*                          */
   uint32_t call;   /* API call index since enabling     */
@@ -397,6 +418,8 @@ typedef struct {
   uint64_t steps_sort;       /*   radix-sort merge                             */
   uint64_t steps_cluster;    /*   binned cluster merge                         */
   uint64_t steps_fold;       /*   copy-pair fold                               */
+  uint64_t runs_fused;       /* fused runs executed (SQS_FUSE_OFF unset)      */
+  uint64_t steps_fused;      /*   interference steps inside them              */
 } sqs_stats;
 sqs_status sqs_state_stats(const sqs_state* st, sqs_stats* out);
 

@@ -26,6 +26,7 @@ using sqs::Arr;
 using sqs::Ctl;
 using sqs::DevOp;
 using sqs::Gate1;
+using sqs::GroupRun;
 using sqs::OpList;
 
 struct sqs_table {
@@ -187,6 +188,13 @@ struct sqs_state {
     double2* dev;
   };
   std::vector<AngTab> ang_tabs;
+
+  // Fused run (exact sizing): interference steps on distinct targets issued
+  // back to back with nothing queued between them, held until the run ends.
+  std::vector<Gate1> run_gates;
+  std::vector<HostOp> run_pre;       // operations queued before the run's first step
+  uint64_t run_tmask[2] = {0, 0};    // the run's target bits
+  uint64_t run_reads[2] = {0, 0};    // control and angle bits its steps read
 
   // CUDA-graph capture (sqs_capture_begin / _end): while capturing, nothing
   // may wait for the device or allocate, and the branch-count bound is held
@@ -520,7 +528,13 @@ sqs_status run_list(sqs_state* st, const OpList& L) {
 // Runs queued operations as standalone passes.  With keep_tail, the last
 // launch-sized group is left packed in st->ops_buf for the kernel that
 // follows to fuse; otherwise everything runs.
+sqs_status flush_run(sqs_state* st);
+
 sqs_status run_pending(sqs_state* st, bool keep_tail) {
+  if (!st->run_gates.empty()) {
+    sqs_status s = flush_run(st);  // the held run precedes everything queued
+    if (s != SQS_OK) return s;
+  }
   OpList& L = st->ops_buf;
   size_t from = 0;
   for (;;) {
@@ -891,6 +905,198 @@ sqs_status run_branching(sqs_state* st, const Gate1& g, double est_in = -1.0,
   return s;
 }
 
+// Digit windows of a fused run's sort: 8-bit windows over the key bits that
+// are neither targets of the run nor known constant (the sort key is the key
+// with the targets cleared; constant bits order nothing).
+std::vector<uint32_t> group_shifts(const sqs_state* st, const GroupRun& run) {
+  const uint32_t D = (uint32_t)sqs::sort_radix_bits();
+  std::vector<uint32_t> shifts;
+  for (uint32_t q = 0; q < st->total_bits;) {
+    const bool target = (run.tmask[q >> 6] >> (q & 63)) & 1ull;
+    const bool varying = (run.g[0].vary[q >> 6] >> (q & 63)) & 1ull;
+    if (target || !varying) {
+      ++q;
+      continue;
+    }
+    shifts.push_back(q);
+    q += D;
+  }
+  if (shifts.empty()) shifts.push_back(0);  // one pass still applies the queued run
+  return shifts;
+}
+
+// A fused run of k >= 2 interference steps (Sec. II.D.2): the queued
+// operations and a radix sort on the key with every target cleared (each
+// coherent group becomes contiguous), the group count (the output holds at
+// most 2^k branches per group), then every group transformed at once.
+// Bit-identical to the k steps one by one.
+sqs_status run_group(sqs_state* st, const std::vector<Gate1>& gates) {
+  sqs_status s = run_pending(st, true);  // leaves the fused operations in ops_buf
+  if (s != SQS_OK) return st->sticky = s;
+  const OpList& L = st->ops_buf;
+  GroupRun run;
+  std::memset(&run, 0, sizeof(run));
+  run.k = (uint32_t)gates.size();
+  for (uint32_t j = 0; j < run.k; ++j) {
+    run.g[j] = gates[j];
+    run.tmask[gates[j].t >> 6] |= 1ull << (gates[j].t & 63);
+  }
+  if (st->ub > 1 && (st->bk.cap < st->ub || st->alt.cap < st->ub)) {
+    s = sync_bound(st);  // tiles and buffers follow the bound: exact count first
+    if (s != SQS_OK) return s;
+  }
+  const std::vector<uint32_t> shifts = group_shifts(st, run);
+  const uint32_t npass = (uint32_t)shifts.size();
+  const uint64_t tile = (uint64_t)sqs::sort_tile();
+  const uint64_t in_slots = st->cur.slots(st->ub);
+  uint32_t per_seg = 1;
+  uint64_t tiles0;
+  if (st->cur.segmented) {
+    per_seg = (uint32_t)std::max<uint64_t>(1, ((1ull << st->cur.seg_log2) + tile - 1) / tile);
+    tiles0 = std::max<uint64_t>(1, (uint64_t)st->cur.n_seg * per_seg);
+  } else {
+    tiles0 = std::max<uint64_t>(1, (st->ub + tile - 1) / tile);
+  }
+  const uint64_t tilesN = std::max<uint64_t>(1, (st->ub + tile - 1) / tile);
+  const uint64_t radix = 1ull << sqs::sort_radix_bits();
+  const size_t hist_bytes = (size_t)(radix * std::max(tiles0, tilesN) * 4 + 255) & ~(size_t)255;
+  const size_t part_bytes = (sqs::sort_part_entries() * 4 + 255) & ~(size_t)255;
+  const size_t bytes = hist_bytes + part_bytes + 256;
+  if (st->sort_bytes < bytes) {
+    dfree(st, st->sort_buf);
+    st->sort_buf = (unsigned char*)dalloc(st, bytes);
+    st->sort_bytes = st->sort_buf ? bytes : 0;
+    if (!st->sort_buf) return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate sort scratch");
+  }
+  unsigned int* hist = (unsigned int*)st->sort_buf;
+  unsigned int* part = (unsigned int*)(st->sort_buf + hist_bytes);
+  unsigned long long* n_dev = (unsigned long long*)(st->sort_buf + hist_bytes + part_bytes);
+  const uint64_t need_in = std::max<uint64_t>(st->ub, 1);
+  if ((st->bk.cap < need_in && !ensure_store(st, st->bk, need_in)) ||
+      (st->alt.cap < need_in && !ensure_store(st, st->alt, need_in)))
+    return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate %llu branches",
+                             (unsigned long long)need_in);
+  // Pass p writes buf[p & 1]; the last pass lands in bk.
+  Store* buf[2];
+  buf[0] = (npass & 1) ? &st->bk : &st->alt;
+  buf[1] = (npass & 1) ? &st->alt : &st->bk;
+  const unsigned long long* n_ptr = &st->ctl->cnt[st->cur_slot];
+  Arr src = st->cur.view();
+  cudaError_t e = cudaSuccess;
+  for (uint32_t p = 0; p < npass && e == cudaSuccess; ++p) {
+    Store& dst = *buf[p & 1];
+    dst.set_dense();
+    Traced tr(st, SQS_K_SORT);
+    e = sqs::launch_rsort_pass(launch_of(st, in_slots), st->kw, st->amp32, st->ctl, src, n_ptr,
+                               p == 0 ? per_seg : 1u, p == 0 ? tiles0 : tilesN,
+                               p == 0 ? &L : nullptr, gates[0].t, shifts[p], hist, part, n_dev,
+                               dst.view(), run.tmask);
+    st->launches += 3;  // a pass is four kernels: histogram, two scan steps, scatter
+    src = dst.view();
+    n_ptr = n_dev;
+  }
+  if (e != cudaSuccess) return cuda_fail(st, e, "sort pass launch");
+  e = cudaMemsetAsync(&st->ctl->groups, 0,
+                      sizeof(st->ctl->groups) + sizeof(st->ctl->items) + sizeof(st->ctl->stage),
+                      st->stream);
+  if (e != cudaSuccess) return cuda_fail(st, e, "group counters");
+  {
+    Traced tr(st, SQS_K_GROUP_COUNT);
+    e = sqs::launch_group_count(launch_of(st, st->ub), st->kw, st->ctl, st->bk.view(), n_dev,
+                                run.tmask);
+  }
+  if (e != cudaSuccess) return cuda_fail(st, e, "group count launch");
+  s = sync_ctl(st);  // the output holds at most 2^k branches per group
+  if (s != SQS_OK) return s;
+  const uint64_t G = st->ctl_host->groups, n = st->ctl_host->items;
+  const uint64_t cap_all = max_branches(st);
+  const uint64_t out_need = std::max<uint64_t>(1, G >= (cap_all >> run.k) ? cap_all : G << run.k);
+  // Tiles short enough that groups which grow (up to 2^k branches each from
+  // few) spread over many CTAs: about 2^15 output slots per tile.
+  uint32_t tile_len = sqs::kGroupTile;
+  while (tile_len > 32 && (double)tile_len * (double)out_need > 32768.0 * (double)std::max<uint64_t>(n, 1))
+    tile_len >>= 1;
+  const uint64_t n_tiles = std::max<uint64_t>(1, (n + tile_len - 1) / tile_len);
+  if (st->alt.cap < out_need && !ensure_store(st, st->alt, out_need))
+    return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate %llu branches",
+                             (unsigned long long)out_need);
+  st->alt.set_dense();
+  const int out_slot = (st->cur_slot + 1) & 3;
+  {
+    Traced tr(st, SQS_K_GROUP);
+    e = sqs::launch_group(launch_of(st, n), st->kw, st->amp32, st->ctl, st->bk.view(), n_dev,
+                          tile_len, n_tiles, st->alt.view(), out_slot, run);
+    st->launches++;  // the peak update after the run
+  }
+  if (e != cudaSuccess) return cuda_fail(st, e, "group launch");
+  st->bk.set_dense();
+  std::swap(st->cur, st->alt);
+  st->cur_slot = out_slot;
+  st->ub = out_need;
+  st->stats.runs_fused++;
+  st->stats.steps_fused += run.k;
+  return SQS_OK;
+}
+
+// Executes the held run: alone (the per-step dispatch with its shortcuts) or
+// fused.  Operations queued after the run stay queued after it.
+sqs_status flush_run(sqs_state* st) {
+  if (st->run_gates.empty()) return SQS_OK;
+  std::vector<Gate1> gates;
+  gates.swap(st->run_gates);
+  std::vector<HostOp> after;
+  after.swap(st->pending);
+  st->pending.swap(st->run_pre);
+  st->run_tmask[0] = st->run_tmask[1] = st->run_reads[0] = st->run_reads[1] = 0;
+  sqs_status s = gates.size() == 1 ? run_branching(st, gates[0]) : run_group(st, gates);
+  if (st->pending.empty()) st->pending.swap(after);
+  else st->pending.insert(st->pending.end(), after.begin(), after.end());
+  return s;
+}
+
+// Fused runs wait for the device (the group count sizes the output), so a
+// graph capture runs every step alone.
+bool fusing(const sqs_state* st) {
+  return !(st->flags & (SQS_FUSE_OFF | SQS_MERGE_PLAIN | SQS_MERGE_HASH | SQS_MERGE_SORT |
+                        SQS_MERGE_CLUSTER)) &&
+         !st->recording && !st->capturing;
+}
+
+// Holds an interference step in the open run, or closes the run and opens a
+// new one with it.  A step joins when nothing was queued since the run's
+// last step, its target is new to the run and read by no step of it, and it
+// reads (controls, angle register) none of the run's targets nor its own.
+// A copy-pair fold always runs alone: one pass with no partition is cheaper
+// than its share of a fused run.
+sqs_status hold_step(sqs_state* st, const Gate1& g) {
+  uint64_t reads[2] = {g.cmask[0], g.cmask[1]};
+  if (g.mode == 1)
+    for (uint32_t b = 0; b < g.ang_w; ++b) {
+      const uint32_t q = g.ang_off + b;
+      if (q < 128) reads[q >> 6] |= 1ull << (q & 63);
+    }
+  uint64_t tbit[2] = {0, 0};
+  tbit[g.t >> 6] = 1ull << (g.t & 63);
+  const bool alone = (reads[0] & tbit[0]) || (reads[1] & tbit[1]) || g.fold_sign != 0;
+  const bool join = !st->run_gates.empty() && st->pending.empty() && !alone &&
+                    st->run_gates.size() < (size_t)sqs::kMaxRun &&
+                    !((st->run_tmask[0] | st->run_reads[0]) & tbit[0]) &&
+                    !((st->run_tmask[1] | st->run_reads[1]) & tbit[1]) &&
+                    !(reads[0] & st->run_tmask[0]) && !(reads[1] & st->run_tmask[1]);
+  if (!join) {
+    sqs_status s = flush_run(st);
+    if (s != SQS_OK) return s;
+    if (alone) return run_branching(st, g);
+    st->run_pre.swap(st->pending);
+  }
+  st->run_gates.push_back(g);
+  for (int w = 0; w < 2; ++w) {
+    st->run_tmask[w] |= tbit[w];
+    st->run_reads[w] |= reads[w];
+  }
+  return SQS_OK;
+}
+
 bool is_zero(double re, double im) { return re == 0.0 && im == 0.0; }
 
 // ---- structural history (features of the learned predictor) ---------------
@@ -1130,6 +1336,9 @@ sqs_status issue_branching(sqs_state* st, const Gate1& g_in, uint32_t n_ctrl) {
     st->lazy.push_back(std::move(q));
     return SQS_OK;
   }
+  if (fusing(st)) return hold_step(st, g);
+  sqs_status s = flush_run(st);
+  if (s != SQS_OK) return s;
   int64_t rec = -1;
   if (st->recording && st->rec_x.size() / SQS_PRED_FEATURES < st->rec_cap) {
     rec = (int64_t)(st->rec_x.size() / SQS_PRED_FEATURES);
@@ -1170,24 +1379,34 @@ sqs_status run_lazy(sqs_state* st) {
   };
   std::vector<Snap> snaps(n);
   st->defer_frees = true;
-  double est = (double)st->ub;
+  // Estimated count entering each step.  Chained step by step with the
+  // quarter-bit margin of grow_factor, and capped one bit plus a margin that
+  // widens with the square root of the steps chained (the errors of
+  // independent predictions add like a random walk) above the plain chained
+  // prediction: over long flushes (hundreds of steps of a linear-system
+  // walk) the per-step margins would otherwise compound into sizes far above
+  // any real count.
+  std::vector<double> est(n);
   {
-    // Buffers that must grow during the flush grow once, to the predicted
-    // peak, so that few of them wait in the graveyard.
-    double e = est, peak = est;
+    const double lmax = (double)std::min<uint32_t>(st->total_bits, 62);
+    double e = (double)st->ub, chain = std::log2(std::max(1.0, (double)st->ub));
     for (size_t i = 0; i < n; ++i) {
+      const double cap = std::exp2(std::min(lmax, chain + 1.0 + 0.25 * std::sqrt((double)i)));
+      e = std::max(1.0, std::min(e, cap));
+      est[i] = e;
       const double r = grow_factor(Y[i]);
       e = std::min(2.0 * e, std::max(1.0, e * r));
-      peak = std::max(peak, e);
+      chain += std::min(1.0, std::max(-8.0, (double)Y[i]));
     }
+    // Buffers that must grow during the flush grow once, to the predicted
+    // peak, so that few of them wait in the graveyard.
+    const double peak = *std::max_element(est.begin(), est.end());
     st->grow_hint_b = (uint64_t)(peak * 1.2 / 1536.0) + 1;
   }
   for (size_t i = 0; i < n && s == SQS_OK; ++i) {
     snaps[i] = Snap{st->cur, st->alt, st->bk, st->cur_slot, st->seq};
     st->pending = st->lazy[i].ops;
-    s = run_branching(st, st->lazy[i].g, est);
-    const double r = grow_factor(Y[i]);
-    est = std::min(2.0 * est, std::max(1.0, est * r));
+    s = run_branching(st, st->lazy[i].g, est[i]);
   }
   st->stats.learned_steps += n;
   if (s == SQS_OK) s = sync_ctl(st, true);
@@ -1443,7 +1662,7 @@ sqs_status sqs_state_create(const uint32_t* reg_widths, uint32_t n_regs, uint32_
                             void* cuda_stream, sqs_state** out) {
   if (!out || !reg_widths || n_regs == 0 || n_regs > 128) return SQS_ERR_ARG;
   if (flags & ~(SQS_AMP_FP32 | SQS_SIZING_LEARNED | SQS_MERGE_HASH | SQS_MERGE_SORT |
-                SQS_MERGE_CLUSTER | SQS_MERGE_TUNED | SQS_MERGE_PLAIN))
+                SQS_MERGE_CLUSTER | SQS_MERGE_TUNED | SQS_MERGE_PLAIN | SQS_FUSE_OFF))
     return SQS_ERR_ARG;
   uint32_t total = 0;
   for (uint32_t j = 0; j < n_regs; ++j) {
@@ -1526,6 +1745,9 @@ sqs_status sqs_state_reset(sqs_state* st) {
   if (!st) return SQS_ERR_ARG;
   st->pending.clear();
   st->lazy.clear();
+  st->run_gates.clear();
+  st->run_pre.clear();
+  st->run_tmask[0] = st->run_tmask[1] = st->run_reads[0] = st->run_reads[1] = 0;
   st->sticky = SQS_OK;
   st->err.clear();
   st->cur_slot = 0;

@@ -92,7 +92,9 @@ struct Ctl {
   unsigned int err;            // sticky error bits (kErr*)
   unsigned int err_where;      // launch sequence number of the first error
   double norm2;
-  unsigned long long pad[2];
+  unsigned long long groups;     // fused run: coherent groups of its input
+  unsigned long long items;      // fused run: branches of its input (after the queued run)
+  unsigned long long stage[16];  // fused run: branches after each of its operations
 };
 
 constexpr unsigned int kErrCapacity = 1u;  // output array too small
@@ -131,6 +133,20 @@ struct Gate1 {            // the interference operation of one merge step
   uint32_t ang_digits;
 };
 
+// A fused run of interference operations on distinct target bits (Sec.
+// II.D.2: the branches agreeing on every idle bit form a coherent group, and
+// the operation acts on each group).  Operation j acts on key bit g[j].t,
+// which is bit j of a branch's index inside its group; no operation's
+// controls or angle register touch any target of the run, so each group
+// either satisfies them as a whole or not at all.
+constexpr int kMaxRun = 12;
+struct GroupRun {
+  uint32_t k;            // operations in the run (2 <= k <= kMaxRun)
+  uint32_t pad;
+  uint64_t tmask[2];     // union of the target bits
+  Gate1 g[kMaxRun];
+};
+
 struct Launch {
   cudaStream_t stream;
   int sm_count;
@@ -164,11 +180,15 @@ int sort_tile();
 int sort_radix_bits();
 uint32_t sort_merge_chunk_log2();
 size_t sort_part_entries();
+// With clear_mask (two words, non-zero) the sort key is the key with those
+// bits cleared instead: a fused run's targets, so that every coherent group
+// ends contiguous.
 cudaError_t launch_rsort_pass(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in,
                               const unsigned long long* n_ptr, uint32_t per_seg,
                               uint64_t n_tiles, const OpList* first_ops, uint32_t t,
                               uint32_t shift, unsigned int* hist, unsigned int* part,
-                              unsigned long long* n_dev, Arr out);
+                              unsigned long long* n_dev, Arr out,
+                              const uint64_t* clear_mask = nullptr);
 // Combines neighbours of the sorted array `in` (*n_ptr branches): chunk c of
 // 2^sort_merge_chunk_log2() branches becomes segment c of `out` (twice the
 // size).  Adds the count into cnt[out_slot], clears cnt[(out_slot + 1) & 3].
@@ -213,6 +233,22 @@ cudaError_t launch_bin(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, in
 cudaError_t launch_pair_cluster(const Launch& L, int kw, bool amp32, Ctl* ctl, const Gate1& g,
                                 Arr bins, Arr out, int out_slot);
 
+// Fused run (sqs_group.cu), over `in`: the dense array (count *n_ptr)
+// sorted on the key with the run's targets cleared, so that each coherent
+// group is contiguous.  launch_group_count adds the number of groups to
+// ctl->groups and stores the count in ctl->items.  launch_group gives each
+// CTA the groups that start in its tile of tile_len (<= 2048) branches and
+// applies the run to them (in shared memory, each group a dense vector of
+// 2^k amplitudes with presence flags, one operation after another with the
+// pruning of each), appends the survivors to the dense `out` (count in
+// cnt[out_slot]), adds the branch count after each operation into
+// ctl->stage[j] and raises the peak to the largest of them.
+constexpr uint32_t kGroupTile = 2048;
+cudaError_t launch_group_count(const Launch& L, int kw, Ctl* ctl, Arr in,
+                               const unsigned long long* n_ptr, const uint64_t tmask[2]);
+cudaError_t launch_group(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in,
+                         const unsigned long long* n_ptr, uint32_t tile_len, uint64_t n_tiles,
+                         Arr out, int out_slot, const GroupRun& run);
 int pair_log2_capacity(int kw, bool amp32);  // log2 branches per bucket
 size_t pair_smem_bytes(int kw, bool amp32);  // dynamic shared memory of one bucket CTA
 

@@ -47,9 +47,13 @@ __device__ __forceinline__ K drop_bit(K k, uint32_t t) {
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 __device__ __forceinline__ uint32_t umin32(uint32_t a, uint32_t b) { return a < b ? a : b; }
 
+// The digit of the sort key: the pair-class key, or (a fused run: cm set)
+// the key with the run's targets cleared, whose groups the sort makes
+// contiguous.
 template <class K>
-__device__ __forceinline__ uint32_t digit_of(K k, uint32_t t, uint32_t shift) {
-  return (uint32_t)(drop_bit(k, t) >> shift) & (uint32_t)(kRadix - 1);
+__device__ __forceinline__ uint32_t digit_of(K k, uint32_t t, uint32_t shift, K cm) {
+  const K c = cm != (K)0 ? (k & ~cm) : drop_bit(k, t);
+  return (uint32_t)(c >> shift) & (uint32_t)(kRadix - 1);
 }
 
 // Tile `tile` of the input: a slice of one segment, or of the dense array.
@@ -72,8 +76,9 @@ template <int KW, class AT, bool FIRST>
 __global__ void __launch_bounds__(kSortThreads)
     k_rsort_hist(Ctl* ctl, Arr in, const unsigned long long* n_ptr, uint32_t per_seg,
                  const __grid_constant__ OpList ops, uint32_t t, uint32_t shift,
-                 uint64_t n_tiles, unsigned int* hist) {
+                 uint64_t n_tiles, unsigned int* hist, uint64_t cm0, uint64_t cm1) {
   typedef typename KT<KW>::T K;
+  const K cm = mk<KW>(cm0, cm1);
   __shared__ AT tab[FIRST ? kTabEntries : 1];
   __shared__ DevOp sops[FIRST ? kMaxOps : 1];
   __shared__ unsigned int h[kRadix];
@@ -104,7 +109,7 @@ __global__ void __launch_bounds__(kSortThreads)
           a.x = a.y = 0;  // only pruning reads the amplitude
         live = apply_ops<KW, AT>(ops.n, sops, tab, k, a);
       }
-      if (live) atomicAdd(&h[digit_of(k, t, shift)], 1u);
+      if (live) atomicAdd(&h[digit_of(k, t, shift, cm)], 1u);
     }
     __syncthreads();
     hist[(uint64_t)threadIdx.x * n_tiles + tile] = h[threadIdx.x];
@@ -187,8 +192,10 @@ template <int KW, class AT, bool FIRST>
 __global__ void __launch_bounds__(kSortThreads)
     k_rsort_scatter(Ctl* ctl, Arr in, const unsigned long long* n_ptr, uint32_t per_seg,
                     const __grid_constant__ OpList ops, uint32_t t, uint32_t shift,
-                    uint64_t n_tiles, const unsigned int* offs, Arr out) {
+                    uint64_t n_tiles, const unsigned int* offs, Arr out, uint64_t cm0,
+                    uint64_t cm1) {
   typedef typename KT<KW>::T K;
+  const K cm = mk<KW>(cm0, cm1);
   extern __shared__ __align__(16) unsigned char smem[];
   K* skey = (K*)smem;
   AT* samp = (AT*)(smem + (size_t)kSortTile * sizeof(K));
@@ -224,7 +231,7 @@ __global__ void __launch_bounds__(kSortThreads)
         if (FIRST) live = apply_ops<KW, AT>(ops.n, sops, tab, k[r], a[r]);
       }
       // Dead lanes get a value no live lane has, so they match only themselves.
-      d[r] = live ? digit_of(k[r], t, shift) : (uint32_t)kRadix + lane;
+      d[r] = live ? digit_of(k[r], t, shift, cm) : (uint32_t)kRadix + lane;
       const unsigned int peers = __match_any_sync(0xffffffffu, d[r]);
       unsigned int before = 0u;
       if (live) before = whist[warp][d[r]];
@@ -375,10 +382,11 @@ template <int KW, class AT, bool FIRST>
 cudaError_t pass_t(const Launch& L, Ctl* ctl, Arr in, const unsigned long long* n_ptr,
                    uint32_t per_seg, uint64_t n_tiles, const OpList& ops, uint32_t t,
                    uint32_t shift, unsigned int* hist, unsigned int* part,
-                   unsigned long long* n_dev, Arr out) {
+                   unsigned long long* n_dev, Arr out, const uint64_t* cm) {
+  const uint64_t cm0 = cm ? cm[0] : 0ull, cm1 = cm ? cm[1] : 0ull;
   const int grid = (int)std::min<uint64_t>(n_tiles, (uint64_t)L.sm_count * 8);
-  k_rsort_hist<KW, AT, FIRST><<<grid, kSortThreads, 0, L.stream>>>(ctl, in, n_ptr, per_seg, ops,
-                                                                   t, shift, n_tiles, hist);
+  k_rsort_hist<KW, AT, FIRST><<<grid, kSortThreads, 0, L.stream>>>(
+      ctl, in, n_ptr, per_seg, ops, t, shift, n_tiles, hist, cm0, cm1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const uint64_t m = n_tiles * (uint64_t)kRadix;
@@ -400,7 +408,7 @@ cudaError_t pass_t(const Launch& L, Ctl* ctl, Arr in, const unsigned long long* 
   }
   const int sgrid = (int)std::min<uint64_t>(n_tiles, (uint64_t)L.sm_count * 4);
   k_rsort_scatter<KW, AT, FIRST><<<sgrid, kSortThreads, smem, L.stream>>>(
-      ctl, in, n_ptr, per_seg, ops, t, shift, n_tiles, hist, out);
+      ctl, in, n_ptr, per_seg, ops, t, shift, n_tiles, hist, out, cm0, cm1);
   return cudaGetLastError();
 }
 
@@ -418,11 +426,11 @@ cudaError_t launch_rsort_pass(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr
                               const unsigned long long* n_ptr, uint32_t per_seg,
                               uint64_t n_tiles, const OpList* first_ops, uint32_t t,
                               uint32_t shift, unsigned int* hist, unsigned int* part,
-                              unsigned long long* n_dev, Arr out) {
+                              unsigned long long* n_dev, Arr out, const uint64_t* clear_mask) {
   if (n_tiles == 0) return cudaSuccess;
   if (first_ops) {
 #define SQS_P1(KW_, AT_) \
-  pass_t<KW_, AT_, true>(L, ctl, in, n_ptr, per_seg, n_tiles, *first_ops, t, shift, hist, part, n_dev, out)
+  pass_t<KW_, AT_, true>(L, ctl, in, n_ptr, per_seg, n_tiles, *first_ops, t, shift, hist, part, n_dev, out, clear_mask)
     return SQS_SORT_DISPATCH(kw, amp32, SQS_P1);
 #undef SQS_P1
   }
@@ -432,7 +440,7 @@ cudaError_t launch_rsort_pass(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr
     return o;
   }();
 #define SQS_P2(KW_, AT_) \
-  pass_t<KW_, AT_, false>(L, ctl, in, n_ptr, per_seg, n_tiles, kNone, t, shift, hist, part, n_dev, out)
+  pass_t<KW_, AT_, false>(L, ctl, in, n_ptr, per_seg, n_tiles, kNone, t, shift, hist, part, n_dev, out, clear_mask)
   return SQS_SORT_DISPATCH(kw, amp32, SQS_P2);
 #undef SQS_P2
 }

@@ -51,3 +51,21 @@ def trained_predictor(seed=0):
     X, y = collect(training_circuits())
     p, loss = train(X, y, seed=seed)
     return p, loss, (X, y)
+
+
+def walk_circuits(seeds=range(100, 132), N=256, steps=2, kappa=10.0):
+    """Linear-system walk circuits (config 4's construction) on other seeds:
+    the traces the predictor learns config 4 from."""
+    from . import qlss
+    out = []
+    for s in seeds:
+        cfg = qlss.config4(seed=s, N=N, half_band=min(8, N // 4), kappa=kappa, T=2000)
+        out.append(qlss.walk_circuit(cfg, n_steps=steps))
+    return out
+
+
+def trained_on_walks(seeds=range(100, 132), N=256, steps=2, seed=0):
+    """A predictor trained on walk traces (seeds 100..131 by default)."""
+    X, y = collect(walk_circuits(seeds, N, steps))
+    p, loss = train(X, y, seed=seed)
+    return p, loss, (X, y)

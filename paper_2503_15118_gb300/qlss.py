@@ -51,14 +51,16 @@ ANGLE_SCALE = 4.0 * math.pi / float(1 << ANGLE_BITS)  # RY has period 4 pi
 BOT, TOP = 0, 1
 
 
-def registers(n, inst_bits=0):
-    """Widths and register ids for system size 2^n (and an instance register)."""
+def registers(n, inst_bits=0, nonherm=False):
+    """Widths and register ids for system size 2^n (and an instance register;
+    nonherm adds the block qubit a_1 of the non-Hermitian embedding)."""
     widths = [n, n]
     ids = {"BOT": 0, "TOP": 1}
     if inst_bits:
         ids["INST"] = len(widths)
         widths.append(inst_bits)
-    for name, w in (("C", 1), ("A2", 1), ("AH", 1), ("Q", ANGLE_BITS)):
+    extra = (("A1", 1),) if nonherm else ()
+    for name, w in (("C", 1), ("A2", 1), ("AH", 1)) + extra + (("Q", ANGLE_BITS),):
         ids[name] = len(widths)
         widths.append(w)
     return widths, ids
@@ -438,4 +440,123 @@ def instance_block(state, cfg, i):
         j = (k >> int(off[TOP])) & ((1 << cfg["n"]) - 1)
         if j < Ni:
             v[j] = a
+    return v
+
+
+# ---- the non-Hermitian variant (Supp. D, second column of the table) --------
+#
+# A general (non-symmetric) A enters through the Hermitian embedding
+#     bA = [[0, A], [A^T, 0]]   on (a_1, TOP),  |b_bold> = |0>_{a_1} |b>,
+# with A(f) = (1 - f) (sigma_z (x) I) + f bA, so that A(0) gives H_0 and A(1)
+# gives H_1, and the final flagged state |0>_AH |1>_{a_1} |A^-1 b> / norm
+# (bA^-1 maps |0>|b> to |1>|A^-1 b>).
+#   * U_bA = X_{a_1} (|0><0|_{a_1} (x) U_{A^T} + |1><1|_{a_1} (x) U_A): its
+#     block is |1><0| (x) A^T / a + |0><1| (x) A / a = bA / a, a = ||A||_F
+#     (A and A^T share the Frobenius norm).  U_{A^T} is U_A built from the
+#     angle trees of A^T.
+#   * U_{A(f)}: the LCU on C selects sigma_z on a_1 (a phase pi on a_1 = 1)
+#     when C = 0 and U_bA when C = 1; lambda = (1 - f) + f ||A||_F as before.
+#   * U_Q reflects about |0>_{a_1} U_b|0>: the phase predicate adds a_1 = 0.
+# The ancillas of R are unchanged (C, A2, BOT, Q); a_1 belongs to the system.
+
+def nonherm_banded(N, half_band, kappa, rng):
+    """Banded, non-symmetric, indefinite A = D S with condition number kappa:
+    S the symmetric positive-definite banded matrix of spd_banded and D a
+    seeded diagonal of +-1 (orthogonal, so A has the singular values of S)."""
+    S = spd_banded(N, half_band, kappa, rng)
+    d = rng.choice(np.array([-1.0, 1.0]), size=N)
+    if N > 1 and np.all(d == d[0]):
+        d[-1] = -d[0]
+    return d[:, None] * S
+
+
+def u_bold_a(n, ids, tabs, ctrls, dagger=False):
+    """U_bA = X_{a_1} (|0><0| (x) U_{A^T} + |1><1| (x) U_A), all under ctrls.
+    tabs = (t_l(A), t_r(A), t_l(A^T), t_r(A^T)) as table-index lists."""
+    A1 = ids["A1"]
+    c = tuple(ctrls)
+    t_l, t_r, t_l2, t_r2 = tabs
+    sel = (u_a(n, ids, t_l2, t_r2, c + ((A1, 0, 0),), dagger)
+           + u_a(n, ids, t_l, t_r, c + ((A1, 0, 1),), dagger))
+    flip = [("x", A1, 0, c)]
+    return sel + flip if not dagger else flip + sel
+
+
+def u_af_nh(n, ids, tabs, theta, ctrls, dagger=False):
+    """Block-encoding of A(f) = (1 - f) (sigma_z (x) I) + f bA (LCU on C)."""
+    C, A1 = ids["C"], ids["A1"]
+    c = tuple(ctrls)
+    z = [("phase", c + ((C, 0, 0), (A1, 0, 1)), math.pi)]
+    return ([("ry", C, 0, theta, c)] + z + u_bold_a(n, ids, tabs, c + ((C, 0, 1),), dagger)
+            + [("ry", C, 0, -theta, c)])
+
+
+def u_q_nh(n, ids, ctrls):
+    """Block-encoding of Q_b_bold = I - |0><0|_{a_1} (x) |b><b|."""
+    A2, A1 = ids["A2"], ids["A1"]
+    g = [("h", A2, 0, ())] + [("h", TOP, b, ()) for b in range(n)]
+    pred = ((A2, 0, 1), (A1, 0, 0)) + tuple((TOP, b, 0) for b in range(n)) + tuple(ctrls)
+    g += [("phase", pred, math.pi)]
+    g += [("h", TOP, b, ()) for b in range(n)] + [("h", A2, 0, ())]
+    return g
+
+
+def u_h_nh(n, ids, tabs, theta):
+    """U_H = X_AH (|0><0| (x) U_M^dag + |1><1| (x) U_M), U_M = U_{A(f)} U_Q."""
+    AH = ids["AH"]
+    on, off = ((AH, 0, 1),), ((AH, 0, 0),)
+    return (u_q_nh(n, ids, on)
+            + u_af_nh(n, ids, tabs, theta, off, dagger=True)
+            + u_af_nh(n, ids, tabs, theta, on, dagger=False)
+            + u_q_nh(n, ids, off)
+            + [("x", AH, 0, ())])
+
+
+def config4_nonherm(seed=4, N=1024, half_band=8, kappa=10.0, T=2000, n_points=10):
+    """The linear-system walk on one seeded non-Hermitian banded system (the
+    pieces of config4, with A = D S and the tables of A and A^T)."""
+    rng = np.random.default_rng(seed)
+    n = int(round(math.log2(N)))
+    if 1 << n != N:
+        raise ValueError("N must be a power of two")
+    A = nonherm_banded(N, half_band, kappa, rng)
+    widths, ids = registers(n, nonherm=True)
+    t_l, t_r, nf = tables_for(A)
+    t_l2, t_r2, nf2 = tables_for(A.T)
+    tables = t_l + t_r + t_l2 + t_r2
+    tabs = tuple(list(range(i * n, (i + 1) * n)) for i in range(4))
+    steps = [schedule(m / T, kappa) for m in range(T)]
+    points = [int(round((i + 1) * T / n_points)) for i in range(n_points)]
+    return {"widths": widths, "ids": ids, "n": n, "eps": 1e-14, "tables": tables,
+            "tabs": tabs, "norm_f": nf, "A": A, "b": np.full(N, N ** -0.5),
+            "kappa": kappa, "T": T, "steps": steps, "points": points,
+            "prep": prepare_b(n), "nonherm": True,
+            "name": f"qlss-nonherm-N{N}-k{kappa:g}-T{T}"}
+
+
+def walk_step_nh(cfg, f):
+    n, ids = cfg["n"], cfg["ids"]
+    theta = lcu_angle(f, cfg["norm_f"])
+    return u_h_nh(n, ids, cfg["tabs"], theta) + reflection(n, ids)
+
+
+def walk_circuit_nh(cfg, n_steps=None):
+    steps = cfg["steps"] if n_steps is None else cfg["steps"][:n_steps]
+    gates = list(cfg["prep"])
+    for f in steps:
+        gates += walk_step_nh(cfg, f)
+    return {"widths": cfg["widths"], "eps": cfg["eps"], "tables": cfg["tables"],
+            "gates": gates, "name": cfg["name"]}
+
+
+def solution_block_nh(state, cfg):
+    """Amplitudes of |0>_AH |1>_{a_1} |j>_TOP with every ancilla 0, over j."""
+    n = cfg["n"]
+    off = np.cumsum([0] + cfg["widths"])
+    top_off, a1 = int(off[TOP]), 1 << int(off[cfg["ids"]["A1"]])
+    keep_mask = ((1 << n) - 1) << top_off
+    v = np.zeros(1 << n, np.complex128)
+    for k, a in state.items():
+        if k & a1 and not (k & ~keep_mask & ~a1):
+            v[(k >> top_off) & ((1 << n) - 1)] = a
     return v

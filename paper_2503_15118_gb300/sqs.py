@@ -19,6 +19,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = 0, -1, -2
 AMP_FP64, AMP_FP32 = 0, 1
 SIZING_EXACT, SIZING_LEARNED = 0, 2
 MERGE_AUTO, MERGE_HASH, MERGE_SORT, MERGE_CLUSTER, MERGE_TUNED, MERGE_PLAIN = 0, 4, 8, 16, 32, 64
+FUSE_OFF = 128
 (PERM_X, PERM_ADD_REG, PERM_SUB_REG, PERM_ADD_CONST, PERM_SUB_CONST, PERM_SWAP, PERM_MUL_ADD,
  PERM_MUL_CONST, PERM_DIV_XOR) = range(9)
 MAX_CTRL = 8     # controls inline in one permutation operation
@@ -47,7 +48,8 @@ class Stats(ctypes.Structure):
                 ("learned_steps", ctypes.c_uint64), ("bytes_live", ctypes.c_uint64),
                 ("bytes_peak", ctypes.c_uint64), ("steps_expand", ctypes.c_uint64),
                 ("steps_hash", ctypes.c_uint64), ("steps_sort", ctypes.c_uint64),
-                ("steps_cluster", ctypes.c_uint64), ("steps_fold", ctypes.c_uint64)]
+                ("steps_cluster", ctypes.c_uint64), ("steps_fold", ctypes.c_uint64),
+                ("runs_fused", ctypes.c_uint64), ("steps_fused", ctypes.c_uint64)]
 
 
 PRED_FEATURES, PRED_HIDDEN, PRED_PARAMS = 16, 32, 1633
@@ -60,7 +62,8 @@ class TraceRecord(ctypes.Structure):
 
 KERNEL_NAMES = {0: "k_init", 1: "k_apply_inplace", 2: "k_apply_compact", 3: "k_partition",
                 4: "k_pair", 5: "k_probabilities", 6: "k_convert", 7: "k_expand", 8: "k_bin",
-                9: "k_pair_cluster", 10: "k_rsort_pass", 11: "k_rsort_merge", 12: "k_fold"}
+                9: "k_pair_cluster", 10: "k_rsort_pass", 11: "k_rsort_merge", 12: "k_fold",
+                13: "k_group_count", 14: "k_group"}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)

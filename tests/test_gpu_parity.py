@@ -357,7 +357,7 @@ def test_constant_target_expand_path(sqs, merge):
     ]
     circ = {"widths": widths, "eps": 1e-14, "tables": [], "gates": gates}
     o = oracle.run_circuit(circ)
-    g = sqs.State(widths, merge=MERGES[merge])
+    g = sqs.State(widths, merge=MERGES[merge] | sqs.FUSE_OFF)  # every step alone
     g.trace_enable(4096)
     g.run(circ)
     recs, _ = g.trace_read()

@@ -143,3 +143,25 @@ def test_learned_sizing_gains_over_exact_bound(S, trained):
     print(f"\nexact: {te:.2f} ms, {we} host waits, peak {se['bytes_peak'] / 2**20:.1f} MiB; "
           f"learned: {tl:.2f} ms, {wl} host waits, peak {sl['bytes_peak'] / 2**20:.1f} MiB; "
           f"bound-only sizing would reserve {bound_bytes / 2**30:.3g} GiB")
+
+
+def test_learned_sizing_on_walks(S):
+    """Trained on walk traces of other seeds, learned sizing runs a walk of a
+    new seed to the exact-sizing state, bit for bit, with no more host waits."""
+    from paper_2503_15118_gb300 import predictor, qlss
+    p, loss, (X, _) = predictor.trained_on_walks(seeds=range(100, 106), N=32, steps=2)
+    assert X.shape[0] > 100 and loss < 1.0
+    cfg = qlss.config4(seed=4, N=32, half_band=4, kappa=10.0, T=2000)
+    circ = qlss.walk_circuit(cfg, n_steps=3)
+    res = {}
+    for mode in ("exact", "learned"):
+        g = S.State(circ["widths"], learned=(mode == "learned"))
+        if mode == "learned":
+            g.set_predictor(p)
+        g.run(circ)
+        d = g.to_dict()
+        res[mode] = (d, g.stats())
+    (de, se), (dl, sl) = res["exact"], res["learned"]
+    assert set(de) == set(dl) and all(de[k] == dl[k] for k in de)
+    assert sl["learned_steps"] > 0
+    assert sl["host_waits"] <= se["host_waits"]

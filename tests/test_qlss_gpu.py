@@ -44,9 +44,16 @@ def test_small_walk_matches_oracle(sqs, merge, amp32):
         assert g.peak_nnz() == o.peak()
 
 
+def _mid_step(cfg, step_fn):
+    """|b> prepared, then one walk step at the middle of the schedule (the
+    first step has f = 0, where U_A is never selected)."""
+    return {"widths": cfg["widths"], "eps": cfg["eps"], "tables": cfg["tables"],
+            "gates": cfg["prep"] + step_fn(cfg, cfg["steps"][cfg["T"] // 2])}
+
+
 def test_one_step_n256_matches_oracle(sqs):
     cfg = Q.config4(seed=4, N=256, half_band=8, kappa=10.0, T=2000)
-    circ = Q.walk_circuit(cfg, n_steps=1)
+    circ = _mid_step(cfg, Q.walk_step)
     o = oracle.run_circuit(circ)
     g = sqs.run_circuit(circ)
     assert g.nnz() == o.nnz()
@@ -136,3 +143,43 @@ def test_full_batch_instances(sqs):
                 for l, h, a in zip(lo[sel], hi[sel], amps[sel])}
         assert set(part) == set(alone)
         assert max(abs(part[k] - scale * alone[k]) for k in part) < 1e-12
+
+
+@pytest.mark.parametrize("merge", [0, 8])
+@pytest.mark.parametrize("amp32", [False, True])
+def test_small_nonherm_walk_matches_oracle(sqs, merge, amp32):
+    """The non-Hermitian variant (extra block qubit a_1, tables of A and A^T)."""
+    cfg = Q.config4_nonherm(seed=6, N=8, half_band=2, kappa=5.0, T=20)
+    circ = Q.walk_circuit_nh(cfg)
+    o = oracle.run_circuit(circ)
+    g = sqs.run_circuit(circ, amp32=amp32, merge=merge)
+    got, ref = g.to_dict(), o.to_dict()
+    if amp32:
+        assert compare_states(got, ref, atol=1e-5, band=1e-5) >= 1 - 1e-6
+    else:
+        assert compare_states(got, ref, eps=1e-14, atol=1e-12) >= 1 - 1e-10
+        assert g.peak_nnz() == o.peak()
+
+
+def test_nonherm_one_step_n256_matches_oracle(sqs):
+    cfg = Q.config4_nonherm(seed=4, N=256, half_band=8, kappa=10.0, T=2000)
+    circ = _mid_step(cfg, Q.walk_step_nh)
+    o = oracle.run_circuit(circ)
+    g = sqs.run_circuit(circ)
+    assert g.nnz() == o.nnz()
+    assert compare_states(g.to_dict(), o.to_dict(), eps=1e-14, atol=1e-12) >= 1 - 1e-10
+
+
+def test_nonherm_full_size_steps_keep_norm(sqs):
+    """N = 1024: two walk steps keep the norm, and the FP32-storage state
+    stays close to the FP64 one."""
+    cfg = Q.config4_nonherm(seed=4, N=1024, half_band=8, kappa=10.0, T=2000)
+    circ = Q.walk_circuit_nh(cfg, n_steps=2)
+    g64 = sqs.run_circuit(circ)
+    g32 = sqs.run_circuit(circ, amp32=True)
+    d64, d32 = g64.to_dict(), g32.to_dict()
+    n2 = sum(abs(v) ** 2 for v in d64.values())
+    assert abs(n2 - 1) < 1e-10
+    ov = sum(np.conj(v) * d32.get(k, 0) for k, v in d64.items())
+    n32 = sum(abs(v) ** 2 for v in d32.values())
+    assert abs(ov) ** 2 / (n2 * n32) >= 1 - 1e-6

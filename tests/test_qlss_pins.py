@@ -233,3 +233,92 @@ def test_config1_batch_instances_are_config1():
             part[addr | (rest << 8)] = a
         assert set(part) == set(ref)
         assert max(abs(part[k] - 0.5 * ref[k]) for k in part) < 1e-12
+
+
+# ---- non-Hermitian variant --------------------------------------------------
+
+def test_nonherm_matrix_shape_and_condition():
+    A = Q.nonherm_banded(16, 3, 7.0, np.random.default_rng(1))
+    i = np.arange(16)
+    assert np.all(A[np.abs(i[:, None] - i[None, :]) > 3] == 0)
+    assert np.abs(A - A.T).max() > 1e-3  # not symmetric
+    sv = np.linalg.svd(A, compute_uv=False)
+    assert abs(sv[0] / sv[-1] - 7.0) < 1e-9
+    ev = np.linalg.eigvals(A)
+    assert ev.real.min() < 0 < ev.real.max()  # indefinite
+
+
+@pytest.mark.parametrize("N", [4, 8])
+def test_nonherm_block_encoding_identity(N):
+    """<0|_anc U_bA |0>_anc = bA / ||A||_F with bA = [[0, A], [A^T, 0]] on
+    (a_1, TOP), every column."""
+    cfg = Q.config4_nonherm(seed=N, N=N, half_band=2, kappa=5.0, T=10)
+    n, ids, widths, A = cfg["n"], cfg["ids"], cfg["widths"], cfg["A"]
+    gates = Q.u_bold_a(n, ids, cfg["tabs"], ())
+    off = np.cumsum([0] + widths)
+    a1 = int(off[ids["A1"]])
+    bold = np.block([[np.zeros((N, N)), A], [A.T, np.zeros((N, N))]])
+    got = np.zeros((2 * N, 2 * N))
+    for c in range(2):
+        for j in range(N):
+            o = _basis(widths, [(ids["A1"], c), (Q.TOP, j)])
+            for g in gates:
+                o.apply(g, cfg["tables"])
+            d = o.to_dict()
+            for r in range(2):
+                for i in range(N):
+                    got[r * N + i, c * N + j] = d.get((r << a1) | (i << int(off[Q.TOP])), 0).real
+    assert np.abs(got - bold / cfg["norm_f"]).max() < 4 * n * Q.ANGLE_SCALE
+
+
+@pytest.mark.parametrize("f", [0.0, 0.37, 1.0])
+def test_nonherm_walk_block_encodes_h_of_s(f):
+    """<0|_anc U_H(s) |0>_anc = H(s) / lambda with A(f) = (1 - f) sigma_z (x) I
+    + f bA and Q = I - |0><0|_{a_1} (x) |b><b|, on (AH, a_1, TOP)."""
+    N = 4
+    cfg = Q.config4_nonherm(seed=3, N=N, half_band=1, kappa=4.0, T=10)
+    n, ids, widths, A, nf = cfg["n"], cfg["ids"], cfg["widths"], cfg["A"], cfg["norm_f"]
+    gates = Q.u_h_nh(n, ids, cfg["tabs"], Q.lcu_angle(f, nf))
+    off = np.cumsum([0] + widths)
+
+    def key(ah, c, top):
+        return (ah << int(off[ids["AH"]])) | (c << int(off[ids["A1"]])) | (top << int(off[Q.TOP]))
+
+    M = 2 * N
+    got = np.zeros((2 * M, 2 * M), np.complex128)
+    for ah in range(2):
+        for c in range(2):
+            for j in range(N):
+                o = _basis(widths, [(ids["AH"], ah), (ids["A1"], c), (Q.TOP, j)])
+                for g in gates:
+                    o.apply(g, cfg["tables"])
+                d = o.to_dict()
+                for ah2 in range(2):
+                    for c2 in range(2):
+                        for i in range(N):
+                            got[ah2 * M + c2 * N + i, ah * M + c * N + j] = d.get(key(ah2, c2, i), 0)
+    b = np.zeros(M)
+    b[:N] = N ** -0.5
+    Qb = np.eye(M) - np.outer(b, b)
+    bold = np.block([[np.zeros((N, N)), A], [A.T, np.zeros((N, N))]])
+    Af = (1 - f) * np.kron(np.diag([1.0, -1.0]), np.eye(N)) + f * bold
+    H = np.block([[np.zeros((M, M)), Af @ Qb], [Qb @ Af, np.zeros((M, M))]])
+    lam = (1 - f) + f * nf
+    assert np.abs(got - H / lam).max() < 4 * n * Q.ANGLE_SCALE + 1e-12
+
+
+def test_nonherm_walk_converges_to_the_solution():
+    """The flagged block |0>_AH |1>_{a_1} approaches A^-1 b / ||A^-1 b||, with
+    an error that falls as the walk lengthens."""
+    errs = []
+    for T in (50, 200, 800):
+        cfg = Q.config4_nonherm(seed=5, N=4, half_band=2, kappa=5.0, T=T)
+        o = oracle.run_circuit(Q.walk_circuit_nh(cfg))
+        v = Q.solution_block_nh(o.to_dict(), cfg)
+        x = np.linalg.solve(cfg["A"], cfg["b"])
+        x /= np.linalg.norm(x)
+        p = np.vdot(v, v).real
+        errs.append(1 - abs(np.vdot(x, v)) ** 2 / p)
+        assert abs(o.norm2() - 1) < 1e-9
+    assert errs[0] > errs[1] > errs[2], errs
+    assert errs[2] < 5e-3, errs

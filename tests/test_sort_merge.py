@@ -48,7 +48,8 @@ def test_sort_and_bucket_states_bit_identical(sqs, widths, seed, amp32):
     assert all(da[k] == db[k] for k in da)  # exact equality of both components
     sa, sb = a.stats(), b.stats()
     assert sa["steps_hash"] == 0 and sb["steps_sort"] == 0
-    assert sa["steps_sort"] + sa["steps_expand"] == sb["steps_hash"] + sb["steps_expand"]
+    assert (sa["steps_sort"] + sa["steps_expand"] + sa["steps_fold"]
+            == sb["steps_hash"] + sb["steps_expand"] + sb["steps_fold"] + sb["steps_fused"])
     o = oracle.run_circuit(circ)
     f = compare_states(da, o.to_dict(), atol=1e-5 if amp32 else 1e-12,
                        band=1e-5 if amp32 else 1e-12)
