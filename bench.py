@@ -346,6 +346,7 @@ def extra_workloads(stream, flush, args):
             def step():
                 st.reset()
                 st.run(circ)
+                st.flush()  # the operations still queued (and a held run) execute too
 
             for _ in range(args.warmup):
                 step()
@@ -364,11 +365,11 @@ def extra_workloads(stream, flush, args):
             # Interference-step roofline from one traced step.
             st.trace_enable(1 << 16)
             st.trace_read()
+            r0 = st.stats()["runs_fused"]
             step()
             st.sync()
-            r0 = st.stats()["runs_fused"]
-            recs, _ = st.trace_read(cap=1 << 16)
             entry["fused_runs_per_step"] = st.stats()["runs_fused"] - r0
+            recs, _ = st.trace_read(cap=1 << 16)
             # Algorithmic bytes: every interference gate reads its input and
             # writes its output once, (N + M) * Rb, whichever kernels (and
             # however many passes, or one fused run for several gates)
@@ -411,6 +412,7 @@ def learned_walk(stream, flush, args, cfg4):
         def step():
             st.reset()
             st.run(circ)
+            st.flush()  # learned mode: the queued steps execute at the flush
 
         for _ in range(args.warmup):
             step()
@@ -478,6 +480,7 @@ def graph_workloads(stream, stored, cfg5, args):
                 else:
                     st.reset()
                     st.run(circ)
+                    st.flush()  # as the capture's end, which runs what is queued
             b.record(stream)
             torch.cuda.synchronize()
             res[mode] = a.elapsed_time(b) / reps
@@ -527,6 +530,9 @@ def main():
                     help="skip the FP32-storage / learned-sizing comparison")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step and exit (the target of ncu captures)")
+    ap.add_argument("--profile-walk", action="store_true",
+                    help="run |b> and one mid-schedule step of the N = 1024 linear-system walk "
+                         "(fused runs included) and exit (the target of ncu captures)")
     ap.add_argument("--amp32", dest="amp32", action="store_true")
     ap.add_argument("--per-gate", action="store_true",
                     help="per-gate microbenchmark (updates/s and HBM fraction per gate kind and size)")
@@ -552,6 +558,20 @@ def main():
 
     from paper_2503_15118_gb300 import sqs
     sqs.load()
+    if args.profile_walk:
+        from paper_2503_15118_gb300 import qlss
+        cfg4 = W.config4(seed=4)
+        walk = {"widths": cfg4["widths"], "eps": cfg4["eps"], "tables": cfg4["tables"],
+                "gates": cfg4["prep"] + qlss.walk_step(cfg4, cfg4["steps"][cfg4["T"] // 2])}
+        stream = torch.cuda.Stream()
+        st = sqs.State(walk["widths"], capacity_hint=1 << 23, stream=stream.cuda_stream,
+                       eps=walk["eps"])
+        st.run(walk)
+        st.flush()
+        st.sync()
+        print(json.dumps({"profile_walk": st.stats()["runs_fused"], "nnz": st.nnz()}))
+        st.close()
+        return 0
     circ = W.config2(seed=2)
     widths = circ["widths"]
     stream = torch.cuda.Stream()

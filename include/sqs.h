@@ -98,7 +98,17 @@ typedef enum {
                                      one, peak count included.  Runs end at
                                      the next operation of another kind that
                                      must execute, any read, sqs_flush, or
-                                     when they reach 12 steps.               */
+                                     when they reach 12 steps.  A held run
+                                     executes fused when that is estimated to
+                                     move less memory (sort passes plus the
+                                     group pass against a scatter and a merge
+                                     pass per step, one pass per constant-bit
+                                     expansion) on at least 2^14 branches;
+                                     otherwise its steps run one by one.     */
+#define SQS_FUSE_ALWAYS 256u      /* execute every held run of two or more
+                                     steps fused, whatever its size and
+                                     estimated cost (exercises the fused path
+                                     on small states)                        */
 
 /*
  * One control (or predicate) qubit: bit `bit` of register `reg` must equal

@@ -1038,6 +1038,25 @@ sqs_status run_group(sqs_state* st, const std::vector<Gate1>& gates) {
   return SQS_OK;
 }
 
+// Whether a held run is cheaper fused.  In passes over the state: the fused
+// run costs its sort passes, the group count (keys only) and the group pass;
+// the steps one by one cost a scatter and a merge pass each, or one pass for
+// a constant-bit expansion.  Below 2^14 branches every launch is latency
+// bound and the fused run's host wait does not pay.
+bool fuse_pays(const sqs_state* st, const std::vector<Gate1>& gates) {
+  if (st->flags & SQS_FUSE_ALWAYS) return true;
+  if (st->ub < (1ull << 14)) return false;
+  GroupRun run;
+  std::memset(&run, 0, sizeof(run));
+  run.k = (uint32_t)gates.size();
+  run.g[0] = gates[0];
+  for (const Gate1& g : gates) run.tmask[g.t >> 6] |= 1ull << (g.t & 63);
+  double alone = 0.0;
+  for (const Gate1& g : gates) alone += g.no_partners ? 1.0 : 2.0;
+  const double fused = (double)group_shifts(st, run).size() + 1.5;
+  return fused < alone;
+}
+
 // Executes the held run: alone (the per-step dispatch with its shortcuts) or
 // fused.  Operations queued after the run stay queued after it.
 sqs_status flush_run(sqs_state* st) {
@@ -1048,7 +1067,13 @@ sqs_status flush_run(sqs_state* st) {
   after.swap(st->pending);
   st->pending.swap(st->run_pre);
   st->run_tmask[0] = st->run_tmask[1] = st->run_reads[0] = st->run_reads[1] = 0;
-  sqs_status s = gates.size() == 1 ? run_branching(st, gates[0]) : run_group(st, gates);
+  sqs_status s = SQS_OK;
+  if (gates.size() >= 2 && fuse_pays(st, gates)) {
+    s = run_group(st, gates);
+  } else {
+    for (size_t j = 0; j < gates.size() && s == SQS_OK; ++j)
+      s = run_branching(st, gates[j]);  // the queued operations go with the first
+  }
   if (st->pending.empty()) st->pending.swap(after);
   else st->pending.insert(st->pending.end(), after.begin(), after.end());
   return s;
@@ -1292,6 +1317,7 @@ sqs_status issue_branching(sqs_state* st, const Gate1& g_in, uint32_t n_ctrl) {
   g.no_partners = (!plain && b0 >= 0) ? 1u : 0u;
   g.fold_sign = plain ? 0 : st->pair_sign[g.t];
   g.fold_kill = -1;
+  g.fold_twice = 0;
   g.fold_tmax = 0;
   if (g.fold_sign && g.mode == 2 && g.eps > 0.0) {
     // Child r = (U[r][0] + s U[r][1]) a0 vanishes exactly when U[r][0] = -s U[r][1];
@@ -1307,6 +1333,8 @@ sqs_status issue_branching(sqs_state* st, const Gate1& g_in, uint32_t n_ctrl) {
         const double t = std::ldexp(g.eps, 52) / std::fabs(ur0) * (1.0 - 1e-12);
         std::memcpy(&g.fold_tmax, &t, 8);
         g.fold_kill = r;
+        const int k = 1 - r;  // the surviving child
+        g.fold_twice = g.u[2 * (2 * k)] == s * g.u[2 * (2 * k + 1)] ? 1u : 0u;
         break;
       }
     }
@@ -1662,7 +1690,8 @@ sqs_status sqs_state_create(const uint32_t* reg_widths, uint32_t n_regs, uint32_
                             void* cuda_stream, sqs_state** out) {
   if (!out || !reg_widths || n_regs == 0 || n_regs > 128) return SQS_ERR_ARG;
   if (flags & ~(SQS_AMP_FP32 | SQS_SIZING_LEARNED | SQS_MERGE_HASH | SQS_MERGE_SORT |
-                SQS_MERGE_CLUSTER | SQS_MERGE_TUNED | SQS_MERGE_PLAIN | SQS_FUSE_OFF))
+                SQS_MERGE_CLUSTER | SQS_MERGE_TUNED | SQS_MERGE_PLAIN | SQS_FUSE_OFF |
+                SQS_FUSE_ALWAYS))
     return SQS_ERR_ARG;
   uint32_t total = 0;
   for (uint32_t j = 0; j < n_regs; ++j) {

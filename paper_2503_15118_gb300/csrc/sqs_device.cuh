@@ -551,6 +551,33 @@ __device__ __forceinline__ AT child_real(const Gate1& g, int r, AT a0, AT a1) {
   return o;
 }
 
+// 2 x, exactly: one more in the exponent field of a normal x below the
+// largest binade; zeros and subnormals (never amplitudes above the pruning
+// threshold) take an FP64 add.
+__device__ __forceinline__ double twice(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long e = (b >> 52) & 0x7ffull;
+  return e - 1ull < 2045ull ? __longlong_as_double((long long)(b + (1ull << 52))) : x + x;
+}
+
+// The surviving child of a fold whose coefficients agree up to the pair's
+// sign (g.fold_twice): child_real evaluates fma(u, a, round(u a)) per
+// component, which is exactly 2 round(u a) -- the exact value 2 round(u a)
+// - d, |d| <= ulp(round(u a)) / 2, is within a quarter ulp of 2 round(u a)
+// -- so one product and an exponent increment give the same bits.  FP32
+// states keep the general form (their arithmetic is not the bottleneck).
+template <class AT>
+__device__ __forceinline__ AT fold_child(const Gate1& g, int r, AT a0, AT a1) {
+  return child_real<AT>(g, r, a0, a1);
+}
+template <>
+__device__ __forceinline__ double2 fold_child<double2>(const Gate1& g, int r, double2 a0,
+                                                       double2 a1) {
+  if (!g.fold_twice) return child_real<double2>(g, r, a0, a1);
+  const double u = g.u[2 * (2 * r)];
+  return make_double2(twice(__dmul_rn(u, a0.x)), twice(__dmul_rn(u, a0.y)));
+}
+
 // Both components' magnitudes below the bit pattern t (FP64 storage); an
 // FP32 residue is always flushed, so the test passes.
 __device__ __forceinline__ bool below_bits(double2 a, uint64_t t) {

@@ -31,12 +31,11 @@ namespace {
 constexpr int kGroupThreads = 512;
 constexpr uint32_t kNoGroup = 0xffffu;
 
-// Dense area: 2^13 amplitudes for FP64 storage, 2^14 for FP32 (plus one
-// presence byte each); a group of 2^k entries, k <= kMaxRun = 12, always fits
-// twice.
+// Dense area: 2^12 amplitudes (plus one presence byte each), so that a group
+// of 2^k entries, k <= kMaxRun = 12, always fits, and two CTAs share an SM.
 template <class AT>
 struct DenseArea {
-  static constexpr uint32_t n = sizeof(AT) == 16 ? (1u << 13) : (1u << 14);
+  static constexpr uint32_t n = 1u << 12;
 };
 
 // Index of a branch inside its group: bit j = key bit g[j].t.
@@ -54,6 +53,49 @@ __device__ __forceinline__ typename KT<KW>::T group_key(const GroupRun& run,
   for (uint32_t j = 0; j < run.k; ++j)
     if ((x >> j) & 1u) rest |= bit_mask<KW>(run.g[j].t);
   return rest;
+}
+
+// One step's 2x2 on a pair of a group (children(), the merge's form).
+// FP64 storage with a real U: a warp whose lanes mix pairs with both members
+// and pairs with one would issue both FP64 sequences, one after the other.
+// Instead, when any lane of the warp holds both members, every lane takes
+// the two-member form with an absent member read as zero -- fma(u, 0, p) = p
+// and fma(u, a, +-0) = round(u a) give children()'s one-member results
+// exactly, up to the sign of an exact zero -- and otherwise every lane takes
+// the one-member products of the member it holds.  Called by every lane of
+// the warp (the vote).
+template <class AT>
+__device__ __forceinline__ void step_pair(const Gate1& g, uint64_t av, bool act, bool h0, AT a0,
+                                          bool h1, AT a1, AT& o0, AT& o1) {
+  if (act) children<AT>(g, av, h0, a0, h1, a1, o0, o1);
+}
+template <>
+__device__ __forceinline__ void step_pair<double2>(const Gate1& g, uint64_t av, bool act, bool h0,
+                                                   double2 a0, bool h1, double2 a1, double2& o0,
+                                                   double2& o1) {
+  if (g.mode != 2) {
+    if (act) children<double2>(g, av, h0, a0, h1, a1, o0, o1);
+    return;
+  }
+  const bool both = __any_sync(0xffffffffu, act && h0 && h1);
+  if (!act) return;
+  const double u00 = g.u[0], u01 = g.u[2], u10 = g.u[4], u11 = g.u[6];
+  if (both) {
+    if (!h0) a0 = make_double2(0.0, 0.0);
+    if (!h1) a1 = make_double2(0.0, 0.0);
+    const double2 p01 = rmul(u01, a1);
+    o0 = rfma(u00, a0, p01);
+    if (g.reuse & 2u)
+      o1 = (g.reuse & 8u) ? rfms(u10, a0, p01) : rfma(u10, a0, p01);
+    else
+      o1 = rfma(u10, a0, rmul(u11, a1));
+  } else {
+    const double2 a = h0 ? a0 : a1;
+    const bool same = h0 ? (g.reuse & 1u) != 0 : (g.reuse & 2u) != 0;
+    const bool neg = h0 ? (g.reuse & 4u) != 0 : (g.reuse & 8u) != 0;
+    o0 = rmul(h0 ? u00 : u01, a);
+    o1 = same ? (neg ? cneg(o0) : o0) : rmul(h0 ? u10 : u11, a);
+  }
 }
 
 template <int KW>
@@ -87,7 +129,7 @@ __global__ void __launch_bounds__(kStreamThreads)
 //   skey     the tile's keys (kGroupTile)
 //   gidx     u16 per tile branch: its group among the CTA's (kNoGroup: the
 //            branch continues a group of an earlier tile)
-//   gstart   u32 per group: first branch (tile index); one more entry for
+//   gstart   u16 per group: first branch (tile index); one more entry for
 //            the end of the last group, which may lie past the tile
 template <int KW, class AT>
 struct GroupSmem {
@@ -96,12 +138,12 @@ struct GroupSmem {
   static constexpr size_t skey_off = pres_off + DenseArea<AT>::n;
   static constexpr size_t gidx_off = skey_off + (size_t)kGroupTile * sizeof(K);
   static constexpr size_t gstart_off = gidx_off + (size_t)kGroupTile * 2;
-  static constexpr size_t bytes = gstart_off + (size_t)(kGroupTile + 8) * 4;
-  static_assert(bytes <= 227u * 1024u, "one CTA per SM");
+  static constexpr size_t bytes = gstart_off + (size_t)(kGroupTile + 8) * 2;
+  static_assert(bytes <= 112u * 1024u, "two CTAs per SM");
 };
 
 template <int KW, class AT>
-__global__ void __launch_bounds__(kGroupThreads)
+__global__ void __launch_bounds__(kGroupThreads, 2)
     k_group(Ctl* ctl, Arr in, const unsigned long long* n_ptr, uint32_t tile_len, Arr out,
             int out_slot, const __grid_constant__ GroupRun run, uint32_t seq) {
   typedef typename KT<KW>::T K;
@@ -115,7 +157,7 @@ __global__ void __launch_bounds__(kGroupThreads)
   unsigned char* pres = smem + L::pres_off;
   K* skey = (K*)(smem + L::skey_off);
   uint16_t* gidx = (uint16_t*)(smem + L::gidx_off);
-  unsigned int* gstart = (unsigned int*)(smem + L::gstart_off);
+  uint16_t* gstart = (uint16_t*)(smem + L::gstart_off);
 
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[(out_slot + 1) & 3] = 0;
   const uint64_t n = *n_ptr;
@@ -165,7 +207,7 @@ __global__ void __launch_bounds__(kGroupThreads)
     for (uint32_t q = 0; q < 4; ++q) {
       const uint32_t i = threadIdx.x * 4u + q;
       if (i < m) {
-        if (f[q]) gstart[before] = i;
+        if (f[q]) gstart[before] = (uint16_t)i;
         before += f[q];
         gidx[i] = before ? (uint16_t)(before - 1u) : (uint16_t)kNoGroup;
       }
@@ -192,7 +234,7 @@ __global__ void __launch_bounds__(kGroupThreads)
     }
     __syncthreads();
     if (G == 0) continue;  // the tile lies inside a group of an earlier tile
-    if (threadIdx.x == 0) gstart[G] = last_end;
+    if (threadIdx.x == 0) gstart[G] = (uint16_t)last_end;  // < 2048 + 4096
     __syncthreads();
 
     // 3. Batches of whole groups in the dense area.
@@ -216,31 +258,47 @@ __global__ void __launch_bounds__(kGroupThreads)
         const uint32_t low = (1u << j) - 1u;
         unsigned int live = 0;
         if (threadIdx.x == 0) stage_sum = 0;
-        for (uint32_t p = threadIdx.x; p < (nslots >> 1); p += blockDim.x) {
-          const uint32_t grp = p >> (kk - 1u);
-          const uint32_t r = p & (half - 1u);
-          const uint32_t s0 = (grp << kk) | ((r & ~low) << 1) | (r & low);
-          const uint32_t s1 = s0 | (1u << j);
-          const bool h0 = pres[s0] != 0, h1 = pres[s1] != 0;
-          if (!h0 && !h1) continue;
-          const K rest = skey[gstart[g0 + grp]] & ~cm;
-          if ((rest & cmask) != cval) {  // controls not met: the group is unchanged
-            live += (unsigned int)h0 + (unsigned int)h1;
-            continue;
+        // Warp-uniform trip count: step_pair() votes across the warp.
+        const uint32_t npairs = nslots >> 1;
+        for (uint32_t p0 = 0; p0 < npairs; p0 += blockDim.x) {
+          const uint32_t p = p0 + threadIdx.x;
+          bool h0 = false, h1 = false, act = false;
+          uint32_t s0 = 0, s1 = 0;
+          K rest = 0;
+          if (p < npairs) {
+            const uint32_t grp = p >> (kk - 1u);
+            const uint32_t r = p & (half - 1u);
+            s0 = (grp << kk) | ((r & ~low) << 1) | (r & low);
+            s1 = s0 | (1u << j);
+            h0 = pres[s0] != 0;
+            h1 = pres[s1] != 0;
+            if (h0 || h1) {
+              rest = skey[gstart[g0 + grp]] & ~cm;
+              if ((rest & cmask) != cval)  // controls not met: the group is unchanged
+                live += (unsigned int)h0 + (unsigned int)h1;
+              else
+                act = true;
+            }
           }
-          const uint64_t av = g.mode == 1 ? get_field(rest, g.ang_off, g.ang_w) : 0ull;
-          AT a0 = dense[s0], a1 = dense[s1];
-          if (!h0) a0 = a1;  // unread by children(); keeps the operands defined
-          if (!h1) a1 = a0;
-          AT o0, o1;
-          children<AT>(g, av, h0, a0, h1, a1, o0, o1);
-          const bool k0 = keep_amp(o0, g.eps, g.epsf, g.eps2);
-          const bool k1 = keep_amp(o1, g.eps, g.epsf, g.eps2);
-          dense[s0] = o0;
-          dense[s1] = o1;
-          pres[s0] = k0;
-          pres[s1] = k1;
-          live += (unsigned int)k0 + (unsigned int)k1;
+          AT a0, a1, o0, o1;
+          a0.x = a0.y = a1.x = a1.y = 0;
+          if (act) {
+            a0 = dense[s0];
+            a1 = dense[s1];
+            if (!h0) a0 = a1;  // unread for an absent member; keeps the operands defined
+            if (!h1) a1 = a0;
+          }
+          const uint64_t av = act && g.mode == 1 ? get_field(rest, g.ang_off, g.ang_w) : 0ull;
+          step_pair<AT>(g, av, act, h0, a0, h1, a1, o0, o1);
+          if (act) {
+            const bool k0 = keep_amp(o0, g.eps, g.epsf, g.eps2);
+            const bool k1 = keep_amp(o1, g.eps, g.epsf, g.eps2);
+            dense[s0] = o0;
+            dense[s1] = o1;
+            pres[s0] = k0;
+            pres[s1] = k1;
+            live += (unsigned int)k0 + (unsigned int)k1;
+          }
         }
         for (int o = 16; o > 0; o >>= 1) live += __shfl_xor_sync(0xffffffffu, live, o);
         __syncthreads();  // stage_sum reset and every pair of this step done

@@ -125,6 +125,10 @@ struct Gate1 {            // the interference operation of one merge step
   // amplitude are below fold_tmax (bit pattern, FP64 states; FP32 states
   // flush it always).  -1: no child cancels.
   int32_t fold_kill;
+  // The surviving child's two coefficients are equal once the pair's sign is
+  // applied (U[r][0] = fold_sign * U[r][1], H-like): the child
+  // fma(U[r][0], a, round(U[r][0] a)) is exactly 2 round(U[r][0] a).
+  uint32_t fold_twice;
   uint64_t fold_tmax;
   // Mode 1: (cos, sin) of the half angle per 16-bit digit of the angle
   // register's value, digit j at [j << 16, (j + 1) << 16), the offset folded

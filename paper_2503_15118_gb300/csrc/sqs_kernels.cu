@@ -47,22 +47,70 @@ __global__ void k_init(Ctl* ctl, Arr a, int slot) {
 
 // ---------------------------------------------------------------------------
 
+// Op-major over kApplyILP branches per thread: each operation's descriptor
+// is read once for four branches (the interpreter's instruction count, not
+// memory, bounds a long run on a large state).
+constexpr int kApplyILP = 4;
+
 template <int KW, class AT, bool TK, bool TA>
 __global__ void __launch_bounds__(kStreamThreads)
     k_apply_inplace(Ctl* ctl, Arr a, int slot, const __grid_constant__ OpList ops, uint32_t seq) {
+  typedef typename KT<KW>::T K;
   __shared__ AT tab[kTabEntries];
   __shared__ DevOp sops[kMaxOps];
   if (ctl->err) return;
   load_ops(ops, sops, tab);
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, ctl->cnt[slot]);
-  for_each_live(a, ctl->cnt[slot], [&](uint64_t i) {
-    typename KT<KW>::T k = ld_key<KW>(a, i);
-    AT v;
-    if (TA) v = ((const AT*)a.amp)[i];
-    apply_ops<KW, AT>(ops.n, sops, tab, k, v);
-    if (TK) st_key<KW>(a, i, k);
-    if (TA) ((AT*)a.amp)[i] = v;
-  });
+  const uint64_t n_dense = ctl->cnt[slot];
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, n_dense);
+  // Units of kApplyILP * blockDim slots: a slice of a segment, or of the
+  // dense array.
+  const uint32_t unit = kApplyILP * blockDim.x;
+  uint32_t per_seg = 1;
+  uint64_t units;
+  if (a.seg_cnt) {
+    per_seg = ((1u << a.seg_log2) + unit - 1) / unit;
+    units = (uint64_t)a.n_seg * per_seg;
+  } else {
+    units = (n_dense + unit - 1) / unit;
+  }
+  for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    uint64_t base;
+    uint32_t lim;
+    if (a.seg_cnt) {
+      const uint32_t sg = (uint32_t)(u / per_seg);
+      const uint32_t off = (uint32_t)(u - (uint64_t)sg * per_seg) * unit;
+      const uint32_t cnt = a.seg_cnt[sg];
+      if (off >= cnt) continue;
+      base = ((uint64_t)sg << a.seg_log2) + off;
+      lim = cnt - off < unit ? cnt - off : unit;
+    } else {
+      base = u * unit;
+      lim = (uint32_t)(n_dense - base < unit ? n_dense - base : unit);
+    }
+    K k[kApplyILP];
+    AT v[kApplyILP];
+    bool live[kApplyILP];
+#pragma unroll
+    for (int q = 0; q < kApplyILP; ++q) {
+      const uint32_t j = q * blockDim.x + threadIdx.x;
+      live[q] = j < lim;
+      k[q] = 0;
+      v[q].x = v[q].y = 0;
+      if (live[q]) {
+        k[q] = ld_key<KW>(a, base + j);
+        if (TA) v[q] = ((const AT*)a.amp)[base + j];
+      }
+    }
+    apply_ops_n<KW, AT, kApplyILP>(ops.n, sops, tab, k, v, live);
+#pragma unroll
+    for (int q = 0; q < kApplyILP; ++q) {
+      const uint32_t j = q * blockDim.x + threadIdx.x;
+      if (j < lim) {  // no operation of an in-place run drops a branch
+        if (TK) st_key<KW>(a, base + j, k[q]);
+        if (TA) ((AT*)a.amp)[base + j] = v[q];
+      }
+    }
+  }
 }
 
 // Input segment (or dense chunk) c of 2^out.seg_log2 slots is compacted into
@@ -454,10 +502,10 @@ __global__ void __launch_bounds__(kStreamThreads)
                 if (g.fold_kill >= 0 && below_bits(v[q], g.fold_tmax)) {
                   // The cancelling child is a residue the merge would prune.
                   if (g.fold_kill == 1) {
-                    o0[q] = child_real<AT>(g, 0, v[q], a1);
+                    o0[q] = fold_child<AT>(g, 0, v[q], a1);
                     keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
                   } else {
-                    o1[q] = child_real<AT>(g, 1, v[q], a1);
+                    o1[q] = fold_child<AT>(g, 1, v[q], a1);
                     keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
                   }
                 } else {

@@ -19,7 +19,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = 0, -1, -2
 AMP_FP64, AMP_FP32 = 0, 1
 SIZING_EXACT, SIZING_LEARNED = 0, 2
 MERGE_AUTO, MERGE_HASH, MERGE_SORT, MERGE_CLUSTER, MERGE_TUNED, MERGE_PLAIN = 0, 4, 8, 16, 32, 64
-FUSE_OFF = 128
+FUSE_OFF, FUSE_ALWAYS = 128, 256
 (PERM_X, PERM_ADD_REG, PERM_SUB_REG, PERM_ADD_CONST, PERM_SUB_CONST, PERM_SWAP, PERM_MUL_ADD,
  PERM_MUL_CONST, PERM_DIV_XOR) = range(9)
 MAX_CTRL = 8     # controls inline in one permutation operation

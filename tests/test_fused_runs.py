@@ -3,7 +3,8 @@ branches equal on every idle qubit -- transformed as one vector).
 
 A fused run must give the state of its steps run one by one, bit for bit,
 peak count included, in every storage type and key width; these tests run
-the same circuits with fusion on (the default) and off (SQS_FUSE_OFF), check
+the same circuits with every held run fused (SQS_FUSE_ALWAYS) and with
+fusion off (SQS_FUSE_OFF), check
 that fused runs actually happened (stats and trace), and compare both with
 the oracle.  Runs are built to stress the group kernel: the longest run (12
 steps), groups sparse and dense, several batches of groups per bucket,
@@ -33,7 +34,10 @@ def sqs():
 
 
 def _both(sqs, circ, amp32=False, merge=0):
-    on = sqs.State(circ["widths"], amp32=amp32, eps=circ.get("eps", 1e-14), merge=merge)
+    # FUSE_ALWAYS: every held run executes fused, also on states too small
+    # for the cost estimate to choose it.
+    on = sqs.State(circ["widths"], amp32=amp32, eps=circ.get("eps", 1e-14),
+                   merge=merge | sqs.FUSE_ALWAYS)
     on.trace_enable(1 << 14)
     on.run(circ)
     off = sqs.State(circ["widths"], amp32=amp32, eps=circ.get("eps", 1e-14),
@@ -198,12 +202,12 @@ def test_graph_capture_runs_steps_alone(sqs):
     widths = [8, 8, 4]
     circ = _run_circuit(widths, 3, n_runs=3, run_len=6)
     stream = torch.cuda.Stream()
-    g = sqs.State(widths, stream=stream.cuda_stream)
+    g = sqs.State(widths, stream=stream.cuda_stream, merge=sqs.FUSE_ALWAYS)
     graph = g.capture(circ, static_bound=1 << 20)
     assert g.stats()["runs_fused"] == 0
     graph.launch()
     replay = g.to_dict()
-    eager = sqs.run_circuit(circ)
+    eager = sqs.run_circuit(circ, merge=sqs.FUSE_ALWAYS)
     assert eager.stats()["runs_fused"] >= 3
     d = eager.to_dict()
     assert set(replay) == set(d) and all(replay[k] == d[k] for k in d)
@@ -227,3 +231,22 @@ def test_config1_address_superposition_fused(sqs):
     on, off = _both(sqs, stored)
     _identical(on, off)
     assert on.stats()["runs_fused"] >= 1
+
+
+def test_cost_estimate_chooses(sqs):
+    """By default a held run executes fused only when it moves less memory:
+    a run of eight expansions on 2^16 branches over few varying qubits is
+    fused; the same run on a 20-qubit state below 2^14 branches is not."""
+    widths = [16, 8, 8]
+    big = [("h", 0, b, ()) for b in range(16)]              # 2^16 branches
+    big += [("x", 1, 0, ((0, 0, 1),))]                       # ends the run
+    big += [("ry", 2, b, 0.4 + 0.1 * b, ()) for b in range(8)]
+    circ = {"widths": widths, "eps": 1e-14, "tables": [], "gates": big}
+    g = sqs.run_circuit(circ)
+    g.flush()  # the last run is held until something must execute
+    assert g.stats()["runs_fused"] >= 1
+    small = {"widths": [4, 8, 8], "eps": 1e-14, "tables": [],
+             "gates": [("h", 0, b, ()) for b in range(4)]}
+    g = sqs.run_circuit(small)
+    g.flush()
+    assert g.stats()["runs_fused"] == 0
