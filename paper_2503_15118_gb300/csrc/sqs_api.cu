@@ -671,9 +671,10 @@ sqs_status run_hashed(sqs_state* st, const Gate1& g, double est_in, int64_t rec_
   };
   uint64_t B, B1;
   uint64_t need = plan(want, B, B1);
-  if (est_in < 0 && need > st->alt.cap && st->ub > 1) {
-    // The bound outgrew the allocation: learn the exact count first.
-    s = sync_ctl(st);
+  if (need > st->alt.cap && st->ub > 1) {
+    // The bound (exact mode) or the estimate (learned mode) outgrew the
+    // allocation: learn the exact count first.
+    s = est_in < 0 ? sync_ctl(st) : sync_bound(st);
     if (s != SQS_OK) return s;
     want = st->ub;
     need = plan(want, B, B1);
@@ -684,10 +685,14 @@ sqs_status run_hashed(sqs_state* st, const Gate1& g, double est_in, int64_t rec_
     return run_binned(st, g, B1, rec_idx);
   }
   st->stats.steps_hash++;
-  // Learned mode grows buffers straight to the predicted peak (grow_hint_b).
+  // Learned mode grows buffers straight to the predicted peak (grow_hint_b),
+  // or to this step's size when a predicted peak cannot be allocated.
   const uint64_t Bcap = std::max(B, st->grow_hint_b);
-  if ((st->bk.cap < (B << kBucketLog2) && !ensure_store(st, st->bk, Bcap << kBucketLog2)) ||
-      (st->alt.cap < (B << kSegLog2) && !ensure_store(st, st->alt, Bcap << kSegLog2)))
+  auto grow = [&](uint64_t bc) {
+    return (st->bk.cap >= (B << kBucketLog2) || ensure_store(st, st->bk, bc << kBucketLog2)) &&
+           (st->alt.cap >= (B << kSegLog2) || ensure_store(st, st->alt, bc << kSegLog2));
+  };
+  if (!grow(Bcap) && (Bcap == B || !grow(B)))
     return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate %llu branches",
                              (unsigned long long)(B << kSegLog2));
   st->bk.set_segments(kBucketLog2, (uint32_t)B);
@@ -1304,6 +1309,9 @@ void note_branch(sqs_state* st, const Gate1& g) {
   st->last_target = t;
 }
 
+constexpr size_t kLazyMax = 64;  // interference steps queued per learned-sizing flush
+sqs_status run_lazy(sqs_state* st);
+
 // Queues (learned mode) or runs (exact mode) one interference step.
 sqs_status issue_branching(sqs_state* st, const Gate1& g_in, uint32_t n_ctrl) {
   float x[SQS_PRED_FEATURES];
@@ -1362,6 +1370,10 @@ sqs_status issue_branching(sqs_state* st, const Gate1& g_in, uint32_t n_ctrl) {
     q.ops.swap(st->pending);
     std::memcpy(q.x, x, sizeof(x));
     st->lazy.push_back(std::move(q));
+    // Long circuits flush every kLazyMax steps: a misprediction then re-runs
+    // at most that many steps, and the chained estimate restarts from an
+    // exact count.
+    if (st->lazy.size() >= kLazyMax && !st->capturing) return run_lazy(st);
     return SQS_OK;
   }
   if (fusing(st)) return hold_step(st, g);
@@ -1416,7 +1428,18 @@ sqs_status run_lazy(sqs_state* st) {
   // any real count.
   std::vector<double> est(n);
   {
-    const double lmax = (double)std::min<uint32_t>(st->total_bits, 62);
+    // No estimate above what the device could hold: the free memory plus the
+    // state's own buffers, over the three buffers a merge keeps (input,
+    // buckets, output) with the bucket and segment slack.
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      free_b = 0;
+    }
+    const double rb = (double)(8 * st->kw + amp_bytes(st));
+    const double fit = ((double)free_b + (double)st->stats.bytes_live) / (rb * 3.0 * 2.7);
+    const double lmax = std::min<double>((double)std::min<uint32_t>(st->total_bits, 62),
+                                         std::log2(std::max(2.0, fit)));
     double e = (double)st->ub, chain = std::log2(std::max(1.0, (double)st->ub));
     for (size_t i = 0; i < n; ++i) {
       const double cap = std::exp2(std::min(lmax, chain + 1.0 + 0.25 * std::sqrt((double)i)));
@@ -1429,7 +1452,7 @@ sqs_status run_lazy(sqs_state* st) {
     // Buffers that must grow during the flush grow once, to the predicted
     // peak, so that few of them wait in the graveyard.
     const double peak = *std::max_element(est.begin(), est.end());
-    st->grow_hint_b = (uint64_t)(peak * 1.2 / 1536.0) + 1;
+    st->grow_hint_b = (uint64_t)std::min(peak * 1.2 / 1536.0, 0x1p40) + 1;
   }
   for (size_t i = 0; i < n && s == SQS_OK; ++i) {
     snaps[i] = Snap{st->cur, st->alt, st->bk, st->cur_slot, st->seq};

@@ -551,13 +551,20 @@ __device__ __forceinline__ AT child_real(const Gate1& g, int r, AT a0, AT a1) {
   return o;
 }
 
-// 2 x, exactly: one more in the exponent field of a normal x below the
-// largest binade; zeros and subnormals (never amplitudes above the pruning
-// threshold) take an FP64 add.
+// 2 x, exactly, in integer arithmetic on the IEEE encoding (no FP64
+// instruction): one more in the exponent field of a normal x; the magnitude
+// bits shifted left for a zero or subnormal x (the encoding is linear across
+// the subnormal range and into the first normal binade); infinity for a
+// doubling out of the largest binade.
 __device__ __forceinline__ double twice(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned long long e = (b >> 52) & 0x7ffull;
-  return e - 1ull < 2045ull ? __longlong_as_double((long long)(b + (1ull << 52))) : x + x;
+  const unsigned long long sign = b & 0x8000000000000000ull;
+  const unsigned long long mag = b & 0x7fffffffffffffffull;
+  const unsigned long long e = mag >> 52;
+  const unsigned long long r = e == 0ull    ? (sign | (mag << 1))
+                               : e < 2046ull ? b + (1ull << 52)
+                                             : (sign | 0x7ff0000000000000ull);
+  return __longlong_as_double((long long)r);
 }
 
 // The surviving child of a fold whose coefficients agree up to the pair's

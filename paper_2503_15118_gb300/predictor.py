@@ -53,7 +53,7 @@ def trained_predictor(seed=0):
     return p, loss, (X, y)
 
 
-def walk_circuits(seeds=range(100, 132), N=256, steps=2, kappa=10.0):
+def walk_circuits(seeds=range(100, 132), N=1024, steps=2, kappa=10.0):
     """Linear-system walk circuits (config 4's construction) on other seeds:
     the traces the predictor learns config 4 from."""
     from . import qlss
@@ -64,7 +64,7 @@ def walk_circuits(seeds=range(100, 132), N=256, steps=2, kappa=10.0):
     return out
 
 
-def trained_on_walks(seeds=range(100, 132), N=256, steps=2, seed=0):
+def trained_on_walks(seeds=range(100, 132), N=1024, steps=2, seed=0):
     """A predictor trained on walk traces (seeds 100..131 by default)."""
     X, y = collect(walk_circuits(seeds, N, steps))
     p, loss = train(X, y, seed=seed)
