@@ -409,10 +409,14 @@ __global__ void __launch_bounds__(kPairThreads)
 // dense: each block reserves every round's outputs with one atomic.
 constexpr uint32_t kExpandChunkLog2 = 12;
 
-constexpr int kExpandILP = 4;  // branches per thread per round
+// Branches per thread per round.  Two, with at most 64 registers per thread
+// (four CTAs of 256 threads per SM), measured faster on the large random
+// circuit than four branches at 112 registers: more warps hide the FP64 and
+// shared-memory latencies of the fused run.
+constexpr int kExpandILP = 2;
 
 template <int KW, class AT>
-__global__ void __launch_bounds__(kStreamThreads)
+__global__ void __launch_bounds__(kStreamThreads, 4)
     k_expand(Ctl* ctl, Arr in, int in_slot, uint64_t n_chunks, Arr out, int out_slot,
              const __grid_constant__ OpList ops, Gate1 g, uint32_t seq) {
   typedef typename KT<KW>::T K;
