@@ -39,6 +39,19 @@ namespace {
 
 constexpr uint32_t kBucketLog2 = 11;  // branches per merge bucket (shared-memory tile)
 constexpr uint32_t kSegLog2 = 12;     // branches per output segment (2 x bucket)
+// Mean bucket fill of the bucket merge.  Half of the 2048 slots up to 2^26
+// branches: overflow is then about 32 sigma away, and the bucket counters
+// the partition's atomics contend on see fewer branches each (measured 4%
+// faster per step on the large random circuit, 2^24 branches at its peak,
+// than a fill of three quarters).  Three quarters above 2^26 branches, and
+// inside a graph capture, where every step sizes for the static bound: fewer,
+// fuller buckets cost less memory and fewer merge CTAs (overflow about 18
+// sigma away).
+constexpr uint64_t kBucketFill = (1ull << kBucketLog2) / 2;
+constexpr uint64_t kBucketFillLarge = (1ull << kBucketLog2) * 3 / 4;
+uint64_t bucket_fill(uint64_t count_bound) {
+  return count_bound <= (1ull << 26) ? kBucketFill : kBucketFillLarge;
+}
 
 // One branch buffer and its current layout.
 struct Store {
@@ -609,7 +622,7 @@ sqs_status run_binned(sqs_state* st, const Gate1& g, uint64_t B1, int64_t rec_id
   const uint32_t bin_log2 = (uint32_t)sqs::cluster_bin_log2();
   const uint32_t seg_log2 = (uint32_t)sqs::cluster_out_seg_log2();
   const uint64_t ctas = (uint64_t)sqs::cluster_ctas();
-  const uint64_t Bcap = std::max<uint64_t>(B1, (st->grow_hint_b * 1536) >> bin_log2);
+  const uint64_t Bcap = std::max<uint64_t>(B1, (st->grow_hint_b * kBucketFill) >> bin_log2);
   // One extra slice of padding: a bulk copy rounds its size up to 16 bytes.
   const uint64_t bin_need = (B1 << bin_log2) + 4096;
   const uint64_t out_need = (B1 * ctas) << seg_log2;
@@ -654,8 +667,8 @@ sqs_status run_binned(sqs_state* st, const Gate1& g, uint64_t B1, int64_t rec_id
 sqs_status run_hashed(sqs_state* st, const Gate1& g, double est_in, int64_t rec_idx) {
   sqs_status s;
   const OpList& L = st->ops_buf;
-  const uint64_t C = 1ull << kBucketLog2;
-  const uint64_t target = C * 3 / 4;  // mean bucket fill: overflow is ~18 sigma away
+  // A capture sized its buckets for the static bound at the larger fill.
+  const uint64_t target = st->capturing ? kBucketFillLarge : bucket_fill(st->ub);
   uint64_t want =
       est_in < 0 ? st->ub : std::min<uint64_t>(st->ub, (uint64_t)(est_in * 1.2) + 1);
   // The per-CTA bucket merge is the default (measured faster at every size
@@ -1452,7 +1465,8 @@ sqs_status run_lazy(sqs_state* st) {
     // Buffers that must grow during the flush grow once, to the predicted
     // peak, so that few of them wait in the graveyard.
     const double peak = *std::max_element(est.begin(), est.end());
-    st->grow_hint_b = (uint64_t)std::min(peak * 1.2 / 1536.0, 0x1p40) + 1;
+    const double fill = (double)bucket_fill((uint64_t)std::min(peak, 0x1p62));
+    st->grow_hint_b = (uint64_t)std::min(peak * 1.2 / fill, 0x1p40) + 1;
   }
   for (size_t i = 0; i < n && s == SQS_OK; ++i) {
     snaps[i] = Snap{st->cur, st->alt, st->bk, st->cur_slot, st->seq};
@@ -2355,7 +2369,10 @@ sqs_status sqs_capture_begin(sqs_state* st, uint64_t static_bound) {
   if (st->stream == nullptr)
     return fail(st, SQS_ERR_ARG, "graph capture needs a stream other than the legacy default");
   // Buffers for every operation on up to static_bound branches.
-  const uint64_t B = std::max<uint64_t>(1, (static_bound + 1535) / 1536);
+  // Enough buckets for eager issue on the same state as well (the smaller
+  // fill), so that running the circuit eagerly between graph launches does
+  // not move the buffers the graph holds.
+  const uint64_t B = std::max<uint64_t>(1, (static_bound + kBucketFill - 1) / kBucketFill);
   const uint64_t cap = std::max<uint64_t>(B << kSegLog2, 2 * static_bound + 8192);
   if (!ensure_store(st, st->cur, cap) || !ensure_store(st, st->alt, cap) ||
       !ensure_store(st, st->bk, B << kBucketLog2))

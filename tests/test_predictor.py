@@ -137,8 +137,9 @@ def test_learned_sizing_gains_over_exact_bound(S, trained):
         if x[0] in ("h", "ry"):
             ub = min(2 ** 64, 2 * ub)
             peak_ub = max(peak_ub, ub)
-    # Buckets of 2048 slots plus two arrays of 4096-slot segments per bucket.
-    bound_bytes = peak_ub / 1536 * 24 * (2048 + 2 * 4096)
+    # Buckets of 2048 slots (1024 branches each on average) plus two arrays
+    # of 4096-slot segments per bucket.
+    bound_bytes = peak_ub / 1024 * 24 * (2048 + 2 * 4096)
     assert sl["bytes_peak"] < bound_bytes / 100
     print(f"\nexact: {te:.2f} ms, {we} host waits, peak {se['bytes_peak'] / 2**20:.1f} MiB; "
           f"learned: {tl:.2f} ms, {wl} host waits, peak {sl['bytes_peak'] / 2**20:.1f} MiB; "
