@@ -496,6 +496,22 @@ def graph_workloads(stream, stored, cfg5, args):
     return out
 
 
+def slowest_rank_ms(total_ms, dist, device):
+    """The timed region's length on the slowest rank (all ranks call it)."""
+    if not dist:
+        return total_ms
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(world, units_per_step, steps, total_ms):
+    """Whole-job updates/s of N replicas: every rank processes the same
+    units per step, over the slowest rank's time."""
+    return world * units_per_step * steps / (total_ms / 1e3)
+
+
 def run_reference(args, rank):
     if rank != 0:
         return 0
@@ -637,11 +653,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = statistics.mean(step_ms)
     total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * units * args.steps / (total_ms / 1e3)
+    total_ms = slowest_rank_ms(total_ms, dist, "cuda")
+    value = replicas_value(world, units, args.steps, total_ms)
 
     # Dominant kernel (largest share of the traced device time) and the
     # roofline of its largest launch: algorithmic bytes of that launch over
