@@ -286,7 +286,10 @@ sqs_status sqs_peak_nnz(sqs_state* st, uint64_t* out);
 sqs_status sqs_export(sqs_state* st, uint64_t* keys, double* amps, uint64_t cap, uint64_t* n);
 
 /* Replaces the state with n branches from host memory (same layout as
- * sqs_export; keys must be distinct and fit the register widths). */
+ * sqs_export; keys must be distinct and fit the register widths).  Work
+ * issued before and not yet executed (queued operations, a held run of
+ * interference steps, queued learned-sizing steps) is dropped with the old
+ * state; call sqs_flush first to execute it. */
 sqs_status sqs_import(sqs_state* st, const uint64_t* keys, const double* amps, uint64_t n);
 
 /* Executes everything queued and waits; returns any sticky device error. */

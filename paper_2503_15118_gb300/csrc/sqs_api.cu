@@ -2212,7 +2212,12 @@ sqs_status sqs_import(sqs_state* st, const uint64_t* keys, const double* amps, u
     if ((lo & ~m0) || (hi & ~m1)) return fail(st, SQS_ERR_ARG, "key %llu out of range",
                                               (unsigned long long)i);
   }
+  // The imported state replaces the current one: queued operations and a
+  // held run are dropped with it.
   st->pending.clear();
+  st->run_gates.clear();
+  st->run_pre.clear();
+  st->run_tmask[0] = st->run_tmask[1] = st->run_reads[0] = st->run_reads[1] = 0;
   if (!ensure_store(st, st->cur, std::max<uint64_t>(n, 1)))
     return fail(st, SQS_ERR_OOM, "import");
   st->cur.set_dense();
