@@ -380,3 +380,33 @@ def test_arithmetic_oracles_are_bijections_and_invert():
     o.apply(("divxor", 1, 2, 0, ()))           # 3 ^ (7 // 10) = 3
     o.apply(("divxor", 2, 0, 1, ()))           # 7 ^ (10 // 3) = 7 ^ 3 = 4
     assert set(o.to_dict()) == {10 | (3 << 4) | (4 << 8)}
+
+
+def test_sampled_single_gate_matches_oracle_and_brute_force():
+    """The one-by-one evaluator used at full size (oracle/sampled.py) against
+    the std::map oracle's u1q and against a brute-force sum over the input
+    list, on a random sparse state; and its pair-class count against the
+    output size of an unpruned H on a state with no cancellation."""
+    from oracle import sampled
+    rng = np.random.default_rng(11)
+    n = 3000
+    keys = np.unique(rng.integers(0, 1 << 20, size=n, dtype=np.uint64))
+    amps = rng.standard_normal(keys.shape[0]) + 1j * rng.standard_normal(keys.shape[0])
+    z = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+    U, _ = np.linalg.qr(z)
+    t = 7
+    o = oracle.OracleState([20])
+    o.import_(keys, np.zeros_like(keys), amps)
+    o.u1q(0, t, U)
+    ref = o.to_dict()
+    st = sampled.SortedState(keys, amps)
+    xs = np.array(sorted(ref)[:: max(1, len(ref) // 400)], np.uint64)
+    got = sampled.u1q_amplitudes(st, t, U, xs)
+    for x, g in zip(xs.tolist(), got):
+        assert abs(g - ref[x]) < 1e-13
+        # Brute force: sum over every input branch that maps onto x.
+        bf = sum(U[(x >> t) & 1, (k >> t) & 1] * a
+                 for k, a in zip(keys.tolist(), amps) if (k | (1 << t)) == (x | (1 << t)))
+        assert abs(g - bf) < 1e-13
+    # Every pair class yields two outputs (random amplitudes never cancel).
+    assert len(ref) == 2 * sampled.pair_class_count(keys, t)
