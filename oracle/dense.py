@@ -60,7 +60,20 @@ class DenseState:
         self.idx = np.arange(2 ** self.n, dtype=np.int64)
 
     def _field(self, reg):
+        """Value of register reg, or of (first, count): the consecutive
+        registers first .. first + count - 1 read as one number, the first
+        one lowest."""
+        if isinstance(reg, tuple):
+            first, count = reg
+            w = sum(self.widths[first:first + count])
+            return (self.idx >> self.off[first]) & ((1 << w) - 1)
         return (self.idx >> self.off[reg]) & ((1 << self.widths[reg]) - 1)
+
+    def marginal(self, reg):
+        """p(v) = sum of |psi(x)|^2 over the x whose register reg holds v."""
+        p = np.zeros(1 << self.widths[reg])
+        np.add.at(p, self._field(reg), np.abs(self.psi) ** 2)
+        return p
 
     def _ctrl_mask(self, ctrls):
         m = np.ones(self.idx.shape, dtype=bool)

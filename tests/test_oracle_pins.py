@@ -410,3 +410,42 @@ def test_sampled_single_gate_matches_oracle_and_brute_force():
         assert abs(g - bf) < 1e-13
     # Every pair class yields two outputs (random amplitudes never cancel).
     assert len(ref) == 2 * sampled.pair_class_count(keys, t)
+
+
+@pytest.mark.parametrize("seed", [31, 32])
+def test_qram_span_address_matches_dense(seed):
+    """QRAM with an address spanning consecutive registers (the first lowest)
+    against the dense statevector: load, interference, unload."""
+    rng = np.random.default_rng(seed)
+    widths = [3, 2, 4, 3]
+    table = rng.integers(0, 16, size=1 << 5).astype(np.uint8)
+    gates = [("h", 0, b, ()) for b in range(3)] + [("h", 1, 0, ()), ("h", 1, 1, ())]
+    gates += [("qload", (0, 2), 2, 0), ("ry", 3, 0, 0.7, ((2, 1, 1),)),
+              ("h", 3, 1, ((2, 0, 1),)), ("qunload", (0, 2), 2, 0), ("h", 0, 1, ())]
+    circ = {"widths": widths, "eps": 1e-14, "tables": [table], "gates": gates}
+    o = oracle.run_circuit(circ)
+    d = dense.run_dense(circ)
+    ref = {i: complex(a) for i, a in enumerate(d.psi) if abs(a) >= 1e-14}
+    assert compare_states(o.to_dict(), ref) > 1 - 1e-12
+    # The address registers pick each entry: after the load alone, the data
+    # register of every branch is the table entry its (addr0, addr1) select.
+    st = dense.run_dense(dict(circ, gates=gates[:6]))
+    addr = st._field((0, 2))
+    data = st._field(2)
+    live = np.abs(st.psi) > 0
+    assert np.array_equal(data[live], table[addr[live]] & 15)
+
+
+@pytest.mark.parametrize("circ", _circuits_small()[:3], ids=lambda c: c["name"])
+def test_probabilities_match_dense_marginals(circ):
+    """The oracle's marginal distribution of each register against the dense
+    statevector's, and the norm."""
+    o = oracle.run_circuit(circ)
+    d = dense.run_dense(circ)
+    for reg in range(len(circ["widths"])):
+        v, p = o.probabilities(reg)
+        want = d.marginal(reg)
+        got = np.zeros_like(want)
+        got[v.astype(np.int64)] = p
+        assert np.abs(got - want).max() < 1e-12
+    assert abs(o.norm2() - np.sum(np.abs(d.psi) ** 2)) < 1e-12
