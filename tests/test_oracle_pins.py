@@ -449,3 +449,17 @@ def test_probabilities_match_dense_marginals(circ):
         got[v.astype(np.int64)] = p
         assert np.abs(got - want).max() < 1e-12
     assert abs(o.norm2() - np.sum(np.abs(d.psi) ** 2)) < 1e-12
+
+
+@pytest.mark.parametrize("circ", _circuits_small()[:2], ids=lambda c: c["name"])
+def test_peak_is_the_largest_intermediate_count(circ):
+    """The oracle's peak branch count against the dense statevector's count
+    of amplitudes of modulus at least eps after every gate."""
+    o = oracle.run_circuit(circ)
+    counts = [1]
+    st = dense.DenseState(circ["widths"])
+    for g in circ["gates"]:
+        st.apply(g, circ.get("tables", ()))
+        counts.append(int(np.count_nonzero(np.abs(st.psi) >= circ.get("eps", 1e-14))))
+    assert o.peak() == max(counts)
+    assert o.nnz() == counts[-1]
