@@ -322,3 +322,21 @@ def test_nonherm_walk_converges_to_the_solution():
         assert abs(o.norm2() - 1) < 1e-9
     assert errs[0] > errs[1] > errs[2], errs
     assert errs[2] < 5e-3, errs
+
+
+@pytest.mark.parametrize("nonherm", [False, True])
+def test_walk_error_grows_with_condition_number(nonherm):
+    """At a fixed walk length the final error grows with kappa (Sec. III.C:
+    the adiabatic bound scales with kappa), averaged over three systems."""
+    def err(kappa, seed):
+        make = Q.config4_nonherm if nonherm else Q.config4
+        cfg = make(seed=seed, N=4, half_band=2, kappa=kappa, T=100)
+        circ = (Q.walk_circuit_nh if nonherm else Q.walk_circuit)(cfg)
+        o = oracle.run_circuit(circ)
+        v = (Q.solution_block_nh if nonherm else Q.solution_block)(o.to_dict(), cfg)
+        x = np.linalg.solve(cfg["A"], cfg["b"])
+        x /= np.linalg.norm(x)
+        return 1 - abs(np.vdot(x, v)) ** 2 / np.vdot(v, v).real
+    low = np.mean([err(5.0, s) for s in (5, 6, 7)])
+    high = np.mean([err(80.0, s) for s in (5, 6, 7)])
+    assert low < high / 3, (low, high)
