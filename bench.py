@@ -313,16 +313,68 @@ def _interference(g):
     return False
 
 
+def time_workload(sqs, circ, hint, amp32, fuse_off, stream, flush, args, hbm):
+    """Updates/s of one workload in one form (storage type, fused runs on or
+    off), with the HBM-roofline fraction of its interference steps."""
+    st = sqs.State(circ["widths"], capacity_hint=hint, stream=stream.cuda_stream,
+                   eps=circ["eps"], amp32=amp32, merge=fuse_off)
+    try:
+        def step():
+            st.reset()
+            st.run(circ)
+            st.flush()  # the operations still queued (and a held run) execute too
+
+        for _ in range(args.warmup):
+            step()
+        st.sync()
+        st.reset()
+        n_in = []
+        for g in circ["gates"]:
+            n_in.append(st.nnz())
+            st.apply(g, circ["tables"])
+        n_in.append(st.nnz())
+        units = sum(n_in[:-1])
+        ms = _timed_steps(st, step, flush, stream, max(3, args.steps // 2))
+        entry = {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                 "units_per_step": units, "gates": len(circ["gates"]),
+                 "peak_nnz": st.peak_nnz(), "key_words": st.kw}
+        # Interference-step roofline from one traced step.
+        st.trace_enable(1 << 16)
+        st.trace_read()
+        r0 = st.stats()["runs_fused"]
+        step()
+        st.sync()
+        entry["fused_runs_per_step"] = st.stats()["runs_fused"] - r0
+        recs, _ = st.trace_read(cap=1 << 16)
+        # Algorithmic bytes: every interference gate reads its input and
+        # writes its output once, (N + M) * Rb, whichever kernels (and
+        # however many passes, or one fused run for several gates) execute
+        # it; time: every launch of those kernels.
+        rb = 8 * st.kw + (8 if amp32 else 16)
+        byts = sum(float(n_in[i] + n_in[i + 1]) * rb
+                   for i, g in enumerate(circ["gates"]) if _interference(g))
+        tms = sum(kms for kname, _, kms in recs if kname in INTERFERENCE_KERNELS)
+        if tms > 0:
+            gbs = byts / (tms / 1e3) / 1e9
+            entry["interference_roofline"] = {"achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                              "frac": gbs / hbm, "kernel_ms_per_step": tms}
+        return entry
+    finally:
+        st.close()
+
+
 def extra_workloads(stream, flush, args):
     """Updates/s of the other workloads:
     - config 1 batched: 2^16 instances of the 20-qubit circuit in one state,
       each loading its own QRAM table, with the HBM-roofline fraction of its
       interference steps (every expand / merge launch: inputs read plus
       outputs written, over their event-timed duration);
+    - config 3: the QRAM-heavy register workload (two-word keys, 50 rounds);
     - the linear-system walk (one system, N = 1024), 4 walk steps, for a
       positive-definite and for a non-Hermitian A;
     - the batched walk (256 systems of sizes 8..128), 2 walk steps;
-    each in FP64 and FP32 storage."""
+    each in FP64 and FP32 storage.  A workload that fails reports its error
+    instead of a rate."""
     from paper_2503_15118_gb300 import qlss, sqs
     out = {}
     with open(os.path.join(ROOT, "tests", "golden", "config1_seed1_gates.json")) as f:
@@ -330,6 +382,7 @@ def extra_workloads(stream, flush, args):
     cfg4 = W.config4(seed=4)
     cfg5 = qlss.config5(seed=5)
     work = (("config1_batch65536", W.config1_batch(stored, inst_bits=16), 1 << 26),
+            ("config3_qram_a20_r50", W.config3(seed=3), 1 << 25),
             ("qlss_walk_N1024_4steps", qlss.walk_circuit(cfg4, n_steps=4), 1 << 23),
             ("qlss_walk_nonherm_N1024_4steps",
              qlss.walk_circuit_nh(qlss.config4_nonherm(seed=4), n_steps=4), 1 << 24),
@@ -340,51 +393,11 @@ def extra_workloads(stream, flush, args):
         # their fused runs (the reflections about |b>).
         forms = [(False, 0), (True, 0)] + ([(False, sqs.FUSE_OFF)] if name.startswith("qlss") else [])
         for amp32, fuse_off in forms:
-            st = sqs.State(circ["widths"], capacity_hint=hint, stream=stream.cuda_stream,
-                           eps=circ["eps"], amp32=amp32, merge=fuse_off)
-
-            def step():
-                st.reset()
-                st.run(circ)
-                st.flush()  # the operations still queued (and a held run) execute too
-
-            for _ in range(args.warmup):
-                step()
-            st.sync()
-            st.reset()
-            n_in = []
-            for g in circ["gates"]:
-                n_in.append(st.nnz())
-                st.apply(g, circ["tables"])
-            n_in.append(st.nnz())
-            units = sum(n_in[:-1])
-            ms = _timed_steps(st, step, flush, stream, max(3, args.steps // 2))
-            entry = {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-                     "units_per_step": units, "gates": len(circ["gates"]),
-                     "peak_nnz": st.peak_nnz(), "key_words": st.kw}
-            # Interference-step roofline from one traced step.
-            st.trace_enable(1 << 16)
-            st.trace_read()
-            r0 = st.stats()["runs_fused"]
-            step()
-            st.sync()
-            entry["fused_runs_per_step"] = st.stats()["runs_fused"] - r0
-            recs, _ = st.trace_read(cap=1 << 16)
-            # Algorithmic bytes: every interference gate reads its input and
-            # writes its output once, (N + M) * Rb, whichever kernels (and
-            # however many passes, or one fused run for several gates)
-            # execute it; time: every launch of those kernels.
-            rb = 8 * st.kw + (8 if amp32 else 16)
-            byts = sum(float(n_in[i] + n_in[i + 1]) * rb
-                       for i, g in enumerate(circ["gates"]) if _interference(g))
-            tms = sum(kms for kname, _, kms in recs if kname in INTERFERENCE_KERNELS)
-            if tms > 0:
-                gbs = byts / (tms / 1e3) / 1e9
-                entry["interference_roofline"] = {"achieved": gbs, "peak": hbm, "unit": "GB/s",
-                                                  "frac": gbs / hbm,
-                                                  "kernel_ms_per_step": tms}
-            out[name + ("_f32" if amp32 else "_f64") + ("_steps_alone" if fuse_off else "")] = entry
-            st.close()
+            key = name + ("_f32" if amp32 else "_f64") + ("_steps_alone" if fuse_off else "")
+            try:
+                out[key] = time_workload(sqs, circ, hint, amp32, fuse_off, stream, flush, args, hbm)
+            except sqs.SqsError as e:  # reported, not fatal to the benchmark line
+                out[key] = {"error": str(e)}
     try:
         out["qlss_walk_N1024_4steps_learned"] = learned_walk(stream, flush, args, cfg4)
     except sqs.SqsError as e:  # reported, not fatal to the benchmark line

@@ -1,0 +1,122 @@
+"""bench.py's host-side bookkeeping on the CPU, with a stand-in state (the
+kernels are not involved): the workload timing loop, its units, the
+interference-step roofline arithmetic, and error reporting."""
+import os
+import sys
+import types
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+class _Err(RuntimeError):
+    pass
+
+
+class _FakeState:
+    """Counts branches as 1 + the number of interference gates applied."""
+    closed = 0
+
+    def __init__(self, widths, capacity_hint=0, stream=None, eps=None, amp32=False, merge=0):
+        self.kw = 2 if sum(widths) > 64 else 1
+        self.n = 1
+        self.runs = 0
+
+    def reset(self):
+        self.n = 1
+
+    def run(self, circ):
+        for g in circ["gates"]:
+            self.apply(g, circ["tables"])
+
+    def apply(self, g, tables=()):
+        if bench._interference(g):
+            self.n += 1
+
+    def flush(self):
+        self.runs += 1
+
+    def sync(self):
+        pass
+
+    def nnz(self):
+        return self.n
+
+    def peak_nnz(self):
+        return self.n
+
+    def trace_enable(self, cap):
+        pass
+
+    def trace_read(self, cap=0):
+        return [("k_partition", 2, 0.5), ("k_pair", 2, 0.25), ("k_apply_inplace", 3, 9.0)], 3
+
+    def stats(self):
+        return {"runs_fused": self.runs}
+
+    def close(self):
+        _FakeState.closed += 1
+
+
+def _fake_sqs(fail=False):
+    m = types.SimpleNamespace(SqsError=_Err, FUSE_OFF=128)
+
+    def make(*a, **k):
+        if fail:
+            raise _Err("cannot allocate")
+        return _FakeState(*a, **k)
+    m.State = make
+    return m
+
+
+def test_time_workload_units_and_roofline(monkeypatch):
+    calls = []
+
+    def fake_timed(st, step, flush, stream, steps):
+        for _ in range(steps):
+            step()
+        calls.append(steps)
+        return 2.0  # ms per step
+
+    monkeypatch.setattr(bench, "_timed_steps", fake_timed)
+    circ = {"widths": [8, 8], "eps": 1e-14, "tables": [],
+            "gates": [("h", 0, 0, ()), ("x", 1, 0, ()), ("ry", 0, 1, 0.3, ()),
+                      ("u1q", 1, 1, [[1, 0], [0, 1j]], ())]}  # the last one is diagonal
+    args = types.SimpleNamespace(warmup=3, steps=10)
+    e = bench.time_workload(_fake_sqs(), circ, 1 << 10, False, 0, types.SimpleNamespace(cuda_stream=0),
+                            None, args, 1000.0)
+    # Inputs per gate: 1, 2, 2, 3 (the two interference gates add a branch).
+    assert e["units_per_step"] == 1 + 2 + 2 + 3
+    assert e["value"] == pytest.approx(8 / 2e-3)
+    assert calls == [5]
+    # Interference gates h (1 -> 2) and ry (2 -> 3): (1+2 + 2+3) * 24 B over
+    # 0.75 ms of merge kernels; the in-place launch is not counted.
+    r = e["interference_roofline"]
+    assert r["kernel_ms_per_step"] == pytest.approx(0.75)
+    assert r["achieved"] == pytest.approx(8 * 24 / 0.75e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1000.0)
+    assert e["key_words"] == 1
+
+
+def test_time_workload_closes_the_state_and_reports_errors(monkeypatch):
+    monkeypatch.setattr(bench, "_timed_steps", lambda st, step, f, s, n: 1.0)
+    before = _FakeState.closed
+    circ = {"widths": [8], "eps": 1e-14, "tables": [], "gates": [("h", 0, 0, ())]}
+    args = types.SimpleNamespace(warmup=3, steps=4)
+    bench.time_workload(_fake_sqs(), circ, 0, True, 0, types.SimpleNamespace(cuda_stream=0),
+                        None, args, 1.0)
+    assert _FakeState.closed == before + 1
+    with pytest.raises(_Err):
+        bench.time_workload(_fake_sqs(fail=True), circ, 0, True, 0,
+                            types.SimpleNamespace(cuda_stream=0), None, args, 1.0)
+
+
+def test_interference_classification():
+    assert bench._interference(("h", 0, 0, ()))
+    assert bench._interference(("ry_reg", 0, 0, 1, 0.1, 0.0, ()))
+    assert not bench._interference(("u1q", 0, 0, [[0, 1], [1, 0]], ()))  # anti-diagonal
+    assert not bench._interference(("phase", (), 0.3))
+    assert bench._interference(("u1q", 0, 0, [[0.6, 0.8], [0.8, -0.6]], ()))
