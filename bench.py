@@ -31,6 +31,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -128,7 +130,13 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(circ, budget_nnz=1 << 21):
+# Both CPU timings (cpu_baseline in the main line and the reference arm) run
+# the oracle over the same prefix: gates whose inputs hold at most this many
+# branches.
+CPU_BUDGET_NNZ = 1 << 19
+
+
+def cpu_baseline(circ, budget_nnz=CPU_BUDGET_NNZ):
     """Times the oracle (as it stands, one core) on the gate-list prefix whose
     inputs stay at or below budget_nnz branches."""
     import oracle
@@ -167,7 +175,6 @@ def variants(circ, widths, stream, probs, norm, flush, args, st64):
     """The FP32-storage / learned-sizing form against the plain FP64 form on
     the same workload: updates/s of each and the fidelity of the FP32 result
     to the FP64 one."""
-    import numpy as np
 
     from paper_2503_15118_gb300 import predictor, sqs
     units = None
@@ -313,9 +320,73 @@ def _interference(g):
     return False
 
 
-def time_workload(sqs, circ, hint, amp32, fuse_off, stream, flush, args, hbm):
+def _sorted_on_device(lo, hi, amps):
+    """The state's keys (two int64 words) and complex128 amplitudes on the
+    GPU, ordered by (hi, lo)."""
+    import torch
+    dev = torch.device("cuda" if torch.cuda.is_available() else "cpu")
+    tlo = torch.from_numpy(lo.view(np.int64)).to(dev)
+    thi = torch.from_numpy(hi.view(np.int64)).to(dev)
+    ta = torch.from_numpy(np.ascontiguousarray(amps)).to(dev)
+    # Unsigned order from signed words: flip the sign bits.
+    bias = torch.tensor(-(1 << 63), dtype=torch.int64, device=dev)
+    _, o1 = torch.sort(tlo ^ bias, stable=True)
+    _, o2 = torch.sort((thi ^ bias)[o1], stable=True)
+    order = o1[o2]
+    return tlo[order], thi[order], ta[order]
+
+
+def fp32_error(ref, got):
+    """The FP32-storage result against the FP64 one (both as exported
+    (lo, hi, amps)): fidelity |<ref|got>|^2 / (<ref|ref><got|got>), the
+    largest amplitude difference over the keys both hold, and the keys only
+    one of them holds (with their largest |a|).  Computed on the GPU."""
+    import torch
+    rlo, rhi, ra = _sorted_on_device(*ref)
+    glo, ghi, ga = _sorted_on_device(*got)
+    out = {"n_f64": int(rlo.shape[0]), "n_f32": int(glo.shape[0])}
+    if rlo.shape == glo.shape and bool(torch.equal(rlo, glo)) and bool(torch.equal(rhi, ghi)):
+        common_r, common_g = ra, ga
+        out["keys_equal"] = True
+        only_r = only_g = None
+    else:
+        # Keys both hold: merge the two sorted lists and take adjacent equals.
+        tag = torch.cat([torch.zeros_like(rlo), torch.ones_like(glo)])
+        lo = torch.cat([rlo, glo])
+        hi = torch.cat([rhi, ghi])
+        amp = torch.cat([ra, ga])
+        bias = torch.tensor(-(1 << 63), dtype=torch.int64, device=lo.device)
+        _, o1 = torch.sort(lo ^ bias, stable=True)
+        _, o2 = torch.sort((hi ^ bias)[o1], stable=True)
+        o = o1[o2]
+        lo, hi, amp, tag = lo[o], hi[o], amp[o], tag[o]
+        same = (lo[1:] == lo[:-1]) & (hi[1:] == hi[:-1])
+        i = torch.nonzero(same).flatten()
+        first_r = tag[i] == 0
+        common_r = torch.where(first_r, amp[i], amp[i + 1])
+        common_g = torch.where(first_r, amp[i + 1], amp[i])
+        matched = torch.zeros(lo.shape[0], dtype=torch.bool, device=lo.device)
+        matched[i] = True
+        matched[i + 1] = True
+        only_r = amp[(~matched) & (tag == 0)]
+        only_g = amp[(~matched) & (tag == 1)]
+        out["keys_equal"] = False
+        out["only_f64"] = int(only_r.shape[0])
+        out["only_f32"] = int(only_g.shape[0])
+        out["only_max_abs"] = float(max(only_r.abs().max().item() if only_r.numel() else 0.0,
+                                        only_g.abs().max().item() if only_g.numel() else 0.0))
+    ov = torch.sum(torch.conj(common_r) * common_g)
+    n1 = torch.sum(ra.abs() ** 2)
+    n2 = torch.sum(ga.abs() ** 2)
+    out["fidelity_vs_f64"] = float((ov.abs() ** 2 / (n1 * n2)).item())
+    out["max_abs_diff"] = float((common_r - common_g).abs().max().item()) if common_r.numel() else 0.0
+    return out
+
+
+def time_workload(sqs, circ, hint, amp32, fuse_off, stream, flush, args, hbm, keep=False):
     """Updates/s of one workload in one form (storage type, fused runs on or
-    off), with the HBM-roofline fraction of its interference steps."""
+    off), with the HBM-roofline fraction of its interference steps.  With
+    keep, also returns the final state (exported)."""
     st = sqs.State(circ["widths"], capacity_hint=hint, stream=stream.cuda_stream,
                    eps=circ["eps"], amp32=amp32, merge=fuse_off)
     try:
@@ -358,6 +429,8 @@ def time_workload(sqs, circ, hint, amp32, fuse_off, stream, flush, args, hbm):
             gbs = byts / (tms / 1e3) / 1e9
             entry["interference_roofline"] = {"achieved": gbs, "peak": hbm, "unit": "GB/s",
                                               "frac": gbs / hbm, "kernel_ms_per_step": tms}
+        if keep:
+            return entry, st.export()
         return entry
     finally:
         st.close()
@@ -390,14 +463,27 @@ def extra_workloads(stream, flush, args):
     hbm, _ = peaks()
     for name, circ, hint in work:
         # The walks also run with every interference step alone, against
-        # their fused runs (the reflections about |b>).
+        # their fused runs (the reflections about |b>).  The FP32-storage
+        # form reports its error against the FP64 form's final state.
         forms = [(False, 0), (True, 0)] + ([(False, sqs.FUSE_OFF)] if name.startswith("qlss") else [])
+        ref = None
         for amp32, fuse_off in forms:
             key = name + ("_f32" if amp32 else "_f64") + ("_steps_alone" if fuse_off else "")
             try:
-                out[key] = time_workload(sqs, circ, hint, amp32, fuse_off, stream, flush, args, hbm)
+                keep = not fuse_off
+                entry = time_workload(sqs, circ, hint, amp32, fuse_off, stream, flush, args, hbm,
+                                      keep=keep)
+                if keep:
+                    entry, final = entry
+                    if not amp32:
+                        ref = final
+                    elif ref is not None:
+                        entry["fp32_error"] = fp32_error(ref, final)
+                    del final
+                out[key] = entry
             except sqs.SqsError as e:  # reported, not fatal to the benchmark line
                 out[key] = {"error": str(e)}
+        ref = None
     try:
         out["qlss_walk_N1024_4steps_learned"] = learned_walk(stream, flush, args, cfg4)
     except sqs.SqsError as e:  # reported, not fatal to the benchmark line
@@ -535,7 +621,7 @@ def run_reference(args, rank):
         cpu_baseline(circ, budget_nnz=1 << 12)
     vals, secs = [], []
     for _ in range(args.steps):
-        cb, dt = cpu_baseline(circ, budget_nnz=1 << 14)
+        cb, dt = cpu_baseline(circ, budget_nnz=CPU_BUDGET_NNZ)
         vals.append(cb["value"])
         secs.append(dt)
     v = statistics.median(vals)

@@ -51,8 +51,15 @@ typedef enum {
 
 /* State-creation flags. */
 #define SQS_AMP_FP64 0u           /* amplitudes stored as complex<double>       */
-#define SQS_AMP_FP32 1u           /* stored as complex<float>; merge, norm and
-                                     probability arithmetic stays FP64          */
+#define SQS_AMP_FP32 1u           /* stored as complex<float>.  Each child of
+                                     an interference step is evaluated with
+                                     compensated FP32 arithmetic (Dot2, float-
+                                     float coefficients): the FP64 sum rounded
+                                     once to FP32.  A component within rho
+                                     (sqs_set_fp32_cancel) of its terms' size
+                                     is set to zero (a cancellation the stored
+                                     precision cannot resolve).  Norms and
+                                     probabilities accumulate in FP64.          */
 #define SQS_SIZING_EXACT 0u       /* output buffers sized from exact bounds     */
 #define SQS_SIZING_LEARNED 2u     /* sized by the learned capacity predictor;
                                      an overflow is detected on the device and
@@ -145,10 +152,9 @@ typedef struct {
  *   SQS_PERM_ADD_CONST  reg := (reg + constant) mod 2^{w_reg}
  *   SQS_PERM_SUB_CONST  reg := (reg - constant) mod 2^{w_reg}
  *   SQS_PERM_SWAP       exchange reg and src_reg (equal widths)
- * Quantum arithmetic as oracles is stated in Sec. II.D.1 ("addition,
- * multiplication, and division ... implemented by the same method"): the
- * multiply-add, multiply-by-odd-constant and divide-XOR kinds are those oracles
- * in their reversible forms (the sources, and the destination's previous value,
+ * Sec. II.D.1 treats multiplication and division as arithmetic oracles built
+ * the same way as addition: the multiply-add, multiply-by-odd-constant and
+ * divide-XOR kinds are those oracles in their reversible forms (the sources, and the destination's previous value,
  * determine the result, so each map is a bijection on keys).  Sources must be
  * registers other than the destination; controls may not sit inside it. */
 typedef enum {
@@ -193,6 +199,15 @@ void sqs_state_destroy(sqs_state* st);
 /* Resets to |0...0> (one branch, amplitude 1) keeping allocations and any
  * sticky error cleared.  Enqueued; does not wait. */
 sqs_status sqs_state_reset(sqs_state* st);
+
+/* FP32-storage states: the storage-precision cancellation threshold rho.
+ * A component of a child of an interference step whose compensated value
+ * is at most rho times the size of its terms (sum of |coefficient| x
+ * |stored amplitude component|) is set to zero; the child is then pruned
+ * when both components are zero.  Default 2^-19 (32 units of FP32 roundoff);
+ * 0 disables the rule.  SQS_ERR_ARG outside [0, 2^-10].  Takes effect for
+ * operations issued afterwards.  No effect on FP64 states. */
+sqs_status sqs_set_fp32_cancel(sqs_state* st, double rho);
 
 /* Threshold of the pruning step that ends every interference operation
  * (Sec. II.D.2: branches left at zero amplitude are removed).  A branch is
@@ -270,6 +285,21 @@ sqs_status sqs_probabilities(sqs_state* st, uint32_t reg, double* probs, double*
 sqs_status sqs_probabilities_device(sqs_state* st, uint32_t reg, double* probs_dev,
                                     double* norm2_dev);
 
+/* Marginal probabilities of register `reg` in sparse form, for a register of
+ * any width (up to 64 bits): the distinct values v the register holds over
+ * the state's branches, ascending, in values[0..count), and probs[i] = sum
+ * over the branches with reg = values[i] of |a|^2.  Sums are FP64, in a fixed
+ * order (branches sorted by the register, each value's branches in key-sort
+ * order), so repeated calls give identical results.  *count receives the
+ * number of distinct values; when it exceeds cap nothing is copied and
+ * SQS_ERR_ARG is returned (cap = 0 with NULL arrays asks for the count).
+ * norm2 (nullable) receives sum |a|^2 over the whole state.  values and
+ * probs are host memory.  The state must hold fewer than 2^32 branches
+ * (SQS_ERR_CAPACITY otherwise).  Device scratch: a sorted copy of the state
+ * and 16 bytes per branch.  Waits. */
+sqs_status sqs_probabilities_sparse(sqs_state* st, uint32_t reg, uint64_t* values, double* probs,
+                                    uint64_t cap, uint64_t* count, double* norm2);
+
 /* Current branch count.  Waits. */
 sqs_status sqs_nnz(sqs_state* st, uint64_t* out);
 
@@ -277,12 +307,26 @@ sqs_status sqs_nnz(sqs_state* st, uint64_t* out);
  * Table S1).  Waits. */
 sqs_status sqs_peak_nnz(sqs_state* st, uint64_t* out);
 
-/* Copies the branches to host memory in the library's storage order (a set:
- * the order carries no meaning).  keys receives kw words per branch (kw = 1
- * when sum(w) <= 64, else 2: low word first); amps receives (re, im) FP64
- * pairs.  cap is the capacity of the arrays in branches; *n receives the
- * branch count (when it exceeds cap nothing is copied and SQS_ERR_ARG is
- * returned).  Waits. */
+/* Testing hook for the bounded device waits.  The cluster merge
+ * (SQS_MERGE_CLUSTER) loads each CTA's slice of a bin with bulk copies that
+ * complete on an mbarrier; every wait on it polls at most wait_limit times
+ * (0 restores the default, about 6.7e7 polls), then records SQS_ERR_TIMEOUT
+ * in the state, waits (bounded again) for copies in flight and lets the CTA
+ * finish without its slice.  skip_copy_rank >= 0 makes the CTAs of that rank
+ * in every cluster issue no copy, so that their wait runs out (a fault
+ * injected on the host side of the copy, not on the GPU); -1 turns it off.
+ * The next waiting call returns SQS_ERR_TIMEOUT; sqs_state_reset makes the
+ * state usable again.  For tests only. */
+sqs_status sqs_state_set_wait_test(sqs_state* st, uint32_t wait_limit, int32_t skip_copy_rank);
+
+/* Copies the branches to host memory in ascending key order (the canonical
+ * order of a state, which is a set; states of 2^32 or more branches are
+ * copied in storage order).  keys receives kw words per branch (kw = 1 when
+ * sum(w) <= 64, else 2: low word first); amps receives (re, im) FP64 pairs.
+ * cap is the capacity of the arrays in branches; *n receives the branch count
+ * (when it exceeds cap nothing is copied and SQS_ERR_ARG is returned).  The
+ * sort runs on the device into scratch; the state keeps its own order.
+ * Waits. */
 sqs_status sqs_export(sqs_state* st, uint64_t* keys, double* amps, uint64_t cap, uint64_t* n);
 
 /* Replaces the state with n branches from host memory (same layout as

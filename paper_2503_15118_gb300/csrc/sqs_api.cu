@@ -121,6 +121,7 @@ struct sqs_state {
   bool amp32 = false;
   uint32_t flags = 0;
   double eps = 1e-14;
+  float rho32 = 0x1p-19f;  // FP32 storage: cancellation threshold (sqs_set_fp32_cancel)
 
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -184,6 +185,10 @@ struct sqs_state {
   // Radix-sort merge scratch: digit histograms, scan partials, count.
   unsigned char* sort_buf = nullptr;
   size_t sort_bytes = 0;
+  // Bounded device waits: poll limit (0: default) and the testing hook of
+  // sqs_state_set_wait_test.
+  uint32_t wait_limit = 0;
+  int32_t skip_copy_rank = -1;
   // Measured merge choice (SQS_MERGE_TUNED), per size class.
   struct Tune {
     float us_per_slot[2] = {-1.f, -1.f};  // bucket merge, sort merge
@@ -360,6 +365,8 @@ sqs::Launch launch_of(sqs_state* st, uint64_t n_hint) {
   L.sm_count = st->sm_count;
   L.seq = ++st->seq;
   L.n_hint = n_hint;
+  L.wait_limit = st->wait_limit;
+  L.skip_copy_rank = st->skip_copy_rank;
   st->launches++;
   return L;
 }
@@ -600,8 +607,14 @@ sqs_status run_expand(sqs_state* st, const Gate1& g, int64_t rec_idx) {
   cudaError_t e;
   {
     Traced tr(st, g.fold_sign ? SQS_K_FOLD : SQS_K_EXPAND);
-    e = sqs::launch_expand(launch_of(st, in_slots), st->kw, st->amp32, st->ctl, st->cur.view(),
-                           st->cur_slot, chunks, L, g, st->alt.view(), out_slot);
+    const bool fold_only = g.fold_sign != 0 && g.cmask[0] == 0 && g.cmask[1] == 0;
+    e = fold_only
+            ? sqs::launch_fold(launch_of(st, in_slots), st->kw, st->amp32, st->ctl,
+                               st->cur.view(), st->cur_slot, chunks, L, g, st->alt.view(),
+                               out_slot)
+            : sqs::launch_expand(launch_of(st, in_slots), st->kw, st->amp32, st->ctl,
+                                 st->cur.view(), st->cur_slot, chunks, L, g, st->alt.view(),
+                                 out_slot);
   }
   if (e != cudaSuccess) return cuda_fail(st, e, "expand launch");
   if (rec_idx >= 0) {
@@ -760,6 +773,26 @@ std::vector<uint32_t> sort_shifts(const sqs_state* st, const Gate1& g) {
   return shifts;
 }
 
+// Scratch of the radix-sort passes: per-tile digit histograms, scan
+// partials and the device count.
+sqs_status sort_scratch(sqs_state* st, uint64_t tiles, unsigned int*& hist, unsigned int*& part,
+                        unsigned long long*& n_dev) {
+  const uint64_t radix = 1ull << sqs::sort_radix_bits();
+  const size_t hist_bytes = (size_t)(radix * tiles * 4 + 255) & ~(size_t)255;
+  const size_t part_bytes = (sqs::sort_part_entries() * 4 + 255) & ~(size_t)255;
+  const size_t bytes = hist_bytes + part_bytes + 256;
+  if (st->sort_bytes < bytes) {
+    dfree(st, st->sort_buf);
+    st->sort_buf = (unsigned char*)dalloc(st, bytes);
+    st->sort_bytes = st->sort_buf ? bytes : 0;
+    if (!st->sort_buf) return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate sort scratch");
+  }
+  hist = (unsigned int*)st->sort_buf;
+  part = (unsigned int*)(st->sort_buf + hist_bytes);
+  n_dev = (unsigned long long*)(st->sort_buf + hist_bytes + part_bytes);
+  return SQS_OK;
+}
+
 // One interference step on the radix-sort merge: LSD passes ping-pong
 // between the two scratch stores so that the sorted array always ends in
 // st->bk, whose segment counters stay untouched (zero) for the bucket merge;
@@ -789,19 +822,12 @@ sqs_status run_sorted(sqs_state* st, const Gate1& g, int64_t rec_idx) {
     tiles0 = std::max<uint64_t>(1, (st->ub + tile - 1) / tile);
   }
   const uint64_t tilesN = std::max<uint64_t>(1, (st->ub + tile - 1) / tile);
-  const uint64_t radix = 1ull << sqs::sort_radix_bits();
-  const size_t hist_bytes = (size_t)(radix * std::max(tiles0, tilesN) * 4 + 255) & ~(size_t)255;
-  const size_t part_bytes = (sqs::sort_part_entries() * 4 + 255) & ~(size_t)255;
-  const size_t bytes = hist_bytes + part_bytes + 256;
-  if (st->sort_bytes < bytes) {
-    dfree(st, st->sort_buf);
-    st->sort_buf = (unsigned char*)dalloc(st, bytes);
-    st->sort_bytes = st->sort_buf ? bytes : 0;
-    if (!st->sort_buf) return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate sort scratch");
+  unsigned int *hist, *part;
+  unsigned long long* n_dev;
+  {
+    sqs_status s = sort_scratch(st, std::max(tiles0, tilesN), hist, part, n_dev);
+    if (s != SQS_OK) return s;
   }
-  unsigned int* hist = (unsigned int*)st->sort_buf;
-  unsigned int* part = (unsigned int*)(st->sort_buf + hist_bytes);
-  unsigned long long* n_dev = (unsigned long long*)(st->sort_buf + hist_bytes + part_bytes);
   const uint32_t chunk_log2 = sqs::sort_merge_chunk_log2();
   const uint64_t nseg_out = std::max<uint64_t>(1, (st->ub + (1ull << chunk_log2) - 1) >> chunk_log2);
   if (nseg_out > 0xffffffffull) return st->sticky = fail(st, SQS_ERR_CAPACITY, "state too large");
@@ -976,19 +1002,12 @@ sqs_status run_group(sqs_state* st, const std::vector<Gate1>& gates) {
     tiles0 = std::max<uint64_t>(1, (st->ub + tile - 1) / tile);
   }
   const uint64_t tilesN = std::max<uint64_t>(1, (st->ub + tile - 1) / tile);
-  const uint64_t radix = 1ull << sqs::sort_radix_bits();
-  const size_t hist_bytes = (size_t)(radix * std::max(tiles0, tilesN) * 4 + 255) & ~(size_t)255;
-  const size_t part_bytes = (sqs::sort_part_entries() * 4 + 255) & ~(size_t)255;
-  const size_t bytes = hist_bytes + part_bytes + 256;
-  if (st->sort_bytes < bytes) {
-    dfree(st, st->sort_buf);
-    st->sort_buf = (unsigned char*)dalloc(st, bytes);
-    st->sort_bytes = st->sort_buf ? bytes : 0;
-    if (!st->sort_buf) return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate sort scratch");
+  unsigned int *hist, *part;
+  unsigned long long* n_dev;
+  {
+    sqs_status s = sort_scratch(st, std::max(tiles0, tilesN), hist, part, n_dev);
+    if (s != SQS_OK) return s;
   }
-  unsigned int* hist = (unsigned int*)st->sort_buf;
-  unsigned int* part = (unsigned int*)(st->sort_buf + hist_bytes);
-  unsigned long long* n_dev = (unsigned long long*)(st->sort_buf + hist_bytes + part_bytes);
   const uint64_t need_in = std::max<uint64_t>(st->ub, 1);
   if ((st->bk.cap < need_in && !ensure_store(st, st->bk, need_in)) ||
       (st->alt.cap < need_in && !ensure_store(st, st->alt, need_in)))
@@ -1348,9 +1367,9 @@ sqs_status issue_branching(sqs_state* st, const Gate1& g_in, uint32_t n_ctrl) {
     const double s = (double)g.fold_sign;
     for (int r = 0; r < 2; ++r) {
       const double ur0 = g.u[2 * (2 * r)], ur1 = g.u[2 * (2 * r + 1)];
-      // FP32 states flush that residue (below 2^-21 of the summed terms) when
-      // |U[r][0]| <= 1, which every unitary satisfies.
-      if (ur0 == -s * ur1 && ur0 != 0.0 && (!st->amp32 || std::fabs(ur0) <= 1.0)) {
+      // FP32 states evaluate the child with compensated arithmetic, where the
+      // two products cancel exactly: the child is zero and always pruned.
+      if (ur0 == -s * ur1 && ur0 != 0.0) {
         const double t = std::ldexp(g.eps, 52) / std::fabs(ur0) * (1.0 - 1e-12);
         std::memcpy(&g.fold_tmax, &t, 8);
         g.fold_kill = r;
@@ -1581,7 +1600,10 @@ sqs_status apply_1q(sqs_state* st, uint32_t reg, uint32_t bit, const double* m,
   g.cmask[0] = cm[0], g.cmask[1] = cm[1], g.cval[0] = cv[0], g.cval[1] = cv[1];
   if (mode == 0)
     for (int i = 0; i < 8; ++i) g.u[i] = m[i];
-  for (int i = 0; i < 8; ++i) g.uf[i] = (float)g.u[i];
+  for (int i = 0; i < 8; ++i) {
+    g.uf[i] = (float)g.u[i];
+    g.ufl[i] = (float)(g.u[i] - (double)g.uf[i]);
+  }
   if (mode == 0) {
     // Rows of a column equal up to sign share one product per branch.
     auto same = [&](int r0, int r1, double sgn) {
@@ -1617,6 +1639,7 @@ sqs_status apply_1q(sqs_state* st, uint32_t reg, uint32_t bit, const double* m,
   g.eps = st->eps;
   g.eps2 = st->eps * st->eps;
   g.epsf = (float)st->eps;
+  g.rho32 = st->rho32;
   return issue_branching(st, g, n_ctrl);
 }
 
@@ -1717,6 +1740,73 @@ struct sqs_graph {
   HostSnap entry, exit;
   uint64_t launches = 0;
 };
+
+// Sorts the current state (executed: nothing queued; n branches) into one
+// of the two scratch stores, dense and ascending in (key & keep), with LSD
+// passes of the radix sort over the kept bits not known constant.  The
+// state itself is unchanged.  *sorted receives the store, *n_sorted the
+// device count pointer of the sorted copy.  States of 2^32 or more branches
+// are refused (32-bit counts).
+sqs_status sort_copy(sqs_state* st, uint64_t n, const uint64_t keep[2], Store** sorted,
+                     const unsigned long long** n_sorted) {
+  if (n >= (1ull << 32)) return fail(st, SQS_ERR_CAPACITY, "sorting needs fewer than 2^32 branches");
+  const uint32_t D = (uint32_t)sqs::sort_radix_bits();
+  std::vector<uint32_t> shifts;
+  for (uint32_t q = 0; q < st->total_bits;) {
+    const bool kept = (keep[q >> 6] >> (q & 63)) & 1ull;
+    if (!kept || st->const_val[q] >= 0) {
+      ++q;
+      continue;
+    }
+    shifts.push_back(q);
+    q += D;
+  }
+  if (shifts.empty()) shifts.push_back(0);  // one pass still makes the dense copy
+  const uint64_t tile = (uint64_t)sqs::sort_tile();
+  uint32_t per_seg = 1;
+  uint64_t tiles0;
+  if (st->cur.segmented) {
+    per_seg = (uint32_t)std::max<uint64_t>(1, ((1ull << st->cur.seg_log2) + tile - 1) / tile);
+    tiles0 = std::max<uint64_t>(1, (uint64_t)st->cur.n_seg * per_seg);
+  } else {
+    tiles0 = std::max<uint64_t>(1, (n + tile - 1) / tile);
+  }
+  const uint64_t tilesN = std::max<uint64_t>(1, (n + tile - 1) / tile);
+  unsigned int *hist, *part;
+  unsigned long long* n_dev;
+  sqs_status s = sort_scratch(st, std::max(tiles0, tilesN), hist, part, n_dev);
+  if (s != SQS_OK) return s;
+  if ((st->bk.cap < n && !ensure_store(st, st->bk, n)) ||
+      (st->alt.cap < n && !ensure_store(st, st->alt, n)))
+    return st->sticky = fail(st, SQS_ERR_OOM, "cannot allocate %llu branches",
+                             (unsigned long long)n);
+  // Digits of key & keep: the clear mask drops every other bit.  With
+  // nothing to drop, the pair-class key of a bit past the key is the key.
+  uint64_t cm[2] = {~keep[0], ~keep[1]};
+  if (st->kw == 1) cm[1] = 0;
+  const bool whole = cm[0] == 0 && cm[1] == 0;
+  const uint32_t t_none = 64u * (uint32_t)st->kw;
+  Store* buf[2] = {&st->alt, &st->bk};
+  const unsigned long long* n_ptr = &st->ctl->cnt[st->cur_slot];
+  Arr src = st->cur.view();
+  const uint32_t npass = (uint32_t)shifts.size();
+  cudaError_t e = cudaSuccess;
+  for (uint32_t p = 0; p < npass && e == cudaSuccess; ++p) {
+    Store& dst = *buf[p & 1];
+    dst.set_dense();
+    Traced tr(st, SQS_K_SORT);
+    e = sqs::launch_rsort_pass(launch_of(st, n), st->kw, st->amp32, st->ctl, src, n_ptr,
+                               p == 0 ? per_seg : 1u, p == 0 ? tiles0 : tilesN, nullptr, t_none,
+                               shifts[p], hist, part, n_dev, dst.view(), whole ? nullptr : cm);
+    st->launches += 3;
+    src = dst.view();
+    n_ptr = n_dev;
+  }
+  if (e != cudaSuccess) return cuda_fail(st, e, "sort pass launch");
+  *sorted = buf[(npass - 1) & 1];
+  *n_sorted = n_dev;
+  return SQS_OK;
+}
 
 extern "C" {
 
@@ -1826,6 +1916,20 @@ sqs_status sqs_state_reset(sqs_state* st) {
   Traced tr(st, SQS_K_INIT);
   cudaError_t e = sqs::launch_init(launch_of(st, 1), st->ctl, st->cur.view(), 0, st->amp32);
   if (e != cudaSuccess) return cuda_fail(st, e, "reset");
+  return SQS_OK;
+}
+
+sqs_status sqs_state_set_wait_test(sqs_state* st, uint32_t wait_limit, int32_t skip_copy_rank) {
+  if (!st) return SQS_ERR_ARG;
+  if (skip_copy_rank >= sqs::cluster_ctas()) return fail(st, SQS_ERR_ARG, "rank out of range");
+  st->wait_limit = wait_limit;
+  st->skip_copy_rank = skip_copy_rank < 0 ? -1 : skip_copy_rank;
+  return SQS_OK;
+}
+
+sqs_status sqs_set_fp32_cancel(sqs_state* st, double rho) {
+  if (!st || !(rho >= 0.0) || rho > 0x1p-10) return SQS_ERR_ARG;
+  st->rho32 = (float)rho;
   return SQS_OK;
 }
 
@@ -2151,6 +2255,84 @@ sqs_status sqs_peak_nnz(sqs_state* st, uint64_t* out) {
   return SQS_OK;
 }
 
+sqs_status sqs_probabilities_sparse(sqs_state* st, uint32_t reg, uint64_t* values, double* probs,
+                                    uint64_t cap, uint64_t* count, double* norm2) {
+  {
+    sqs_status g = no_capture(st, "sqs_probabilities_sparse");
+    if (g != SQS_OK) return g;
+  }
+  sqs_status s = flush_all(st);
+  if (s != SQS_OK) return s;
+  if (reg >= st->width.size()) return fail(st, SQS_ERR_ARG, "register out of range");
+  if (!count) return fail(st, SQS_ERR_ARG, "null count");
+  if (cap && (!values || !probs)) return fail(st, SQS_ERR_ARG, "null buffers");
+  st->call++;
+  s = sync_ctl(st);
+  if (s != SQS_OK) return s;
+  const uint64_t n = st->ctl_host->cnt[st->cur_slot];
+  const uint32_t off = st->offset[reg], w = st->width[reg];
+  const uint64_t tiles = sqs::run_tiles(n);
+  // Scratch: values, probs (n each), runs, lead sums, lead flags (per tile),
+  // the run total and the norm.
+  const size_t a8 = 255;
+  const size_t b_vals = (n * 8 + a8) & ~a8, b_probs = b_vals;
+  const size_t b_runs = (tiles * 4 + a8) & ~a8, b_lead = (tiles * 8 + a8) & ~a8;
+  const size_t bytes = b_vals + b_probs + 2 * b_runs + b_lead + 256;
+  s = ensure_scratch(st, bytes);
+  if (s != SQS_OK) return s;
+  unsigned char* base = (unsigned char*)st->scratch;
+  uint64_t* d_vals = (uint64_t*)base;
+  double* d_probs = (double*)(base + b_vals);
+  unsigned int* d_runs = (unsigned int*)(base + b_vals + b_probs);
+  unsigned int* d_full = (unsigned int*)(base + b_vals + b_probs + b_runs);
+  double* d_lead = (double*)(base + b_vals + b_probs + 2 * b_runs);
+  unsigned long long* d_total = (unsigned long long*)(base + b_vals + b_probs + 2 * b_runs + b_lead);
+  double* d_norm = (double*)(d_total + 1);
+  cudaError_t e = cudaMemsetAsync(d_total, 0, 16, st->stream);
+  if (e != cudaSuccess) return cuda_fail(st, e, "sparse marginals");
+  if (n) {
+    {
+      Traced tr(st, SQS_K_PROB);
+      e = sqs::launch_probabilities(launch_of(st, st->cur.slots(st->ub)), st->kw, st->amp32,
+                                    st->ctl, st->cur.view(), st->cur_slot, off, w, nullptr, d_norm);
+    }
+    if (e != cudaSuccess) return cuda_fail(st, e, "sparse marginals");
+    uint64_t km[2] = {0ull, 0ull};  // the register's key bits
+    for (uint32_t b = 0; b < w; ++b) km[(off + b) >> 6] |= 1ull << ((off + b) & 63);
+    Store* sorted = nullptr;
+    const unsigned long long* n_sorted = nullptr;
+    s = sort_copy(st, n, km, &sorted, &n_sorted);
+    if (s != SQS_OK) return s;
+    Traced tr(st, SQS_K_PROB);
+    e = sqs::launch_sparse_marginals(launch_of(st, n), st->kw, st->amp32, st->ctl, sorted->view(),
+                                     n_sorted, tiles, off, w, d_runs, d_lead, d_full, d_total,
+                                     d_vals, d_probs);
+    st->launches += 2;
+    if (e != cudaSuccess) return cuda_fail(st, e, "sparse marginals");
+  }
+  unsigned long long head[2] = {0, 0};
+  e = cudaMemcpyAsync(head, d_total, 16, cudaMemcpyDeviceToHost, st->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) return cuda_fail(st, e, "sparse marginals readback");
+  s = sync_ctl(st);
+  if (s != SQS_OK) return s;
+  const uint64_t total = head[0];
+  double nv;
+  std::memcpy(&nv, &head[1], 8);
+  *count = total;
+  if (norm2) *norm2 = nv;
+  if (total > cap)
+    return fail(st, SQS_ERR_ARG, "sparse marginals need %llu entries", (unsigned long long)total);
+  if (total) {
+    e = cudaMemcpyAsync(values, d_vals, total * 8, cudaMemcpyDeviceToHost, st->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(probs, d_probs, total * 8, cudaMemcpyDeviceToHost, st->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+    if (e != cudaSuccess) return cuda_fail(st, e, "sparse marginals readback");
+  }
+  return SQS_OK;
+}
+
 sqs_status sqs_export(sqs_state* st, uint64_t* keys, double* amps, uint64_t cap, uint64_t* n) {
   {
     sqs_status g = no_capture(st, "sqs_export");
@@ -2166,27 +2348,38 @@ sqs_status sqs_export(sqs_state* st, uint64_t* keys, double* amps, uint64_t cap,
   if (cnt > cap) return fail(st, SQS_ERR_ARG, "export needs %llu branches", (unsigned long long)cnt);
   if (cnt == 0) return SQS_OK;
   if (!keys || !amps) return fail(st, SQS_ERR_ARG, "null buffers");
-  s = densify(st);
-  if (s != SQS_OK) return s;
+  // Ascending keys: a sorted copy (the state keeps its own order).  States
+  // of 2^32 or more branches are copied in storage order.
+  Store* src = nullptr;
+  if (cnt < (1ull << 32)) {
+    const uint64_t all[2] = {~0ull, ~0ull};
+    const unsigned long long* n_sorted = nullptr;
+    s = sort_copy(st, cnt, all, &src, &n_sorted);
+    if (s != SQS_OK) return s;
+  } else {
+    s = densify(st);
+    if (s != SQS_OK) return s;
+    src = &st->cur;
+  }
   cudaError_t e;
   if (st->kw == 1) {
-    e = cudaMemcpyAsync(keys, st->cur.k0, cnt * 8, cudaMemcpyDeviceToHost, st->stream);
+    e = cudaMemcpyAsync(keys, src->k0, cnt * 8, cudaMemcpyDeviceToHost, st->stream);
   } else {
-    e = cudaMemcpy2DAsync(keys, 16, st->cur.k0, 8, 8, cnt, cudaMemcpyDeviceToHost, st->stream);
+    e = cudaMemcpy2DAsync(keys, 16, src->k0, 8, 8, cnt, cudaMemcpyDeviceToHost, st->stream);
     if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(keys + 1, 16, st->cur.k1, 8, 8, cnt, cudaMemcpyDeviceToHost,
+      e = cudaMemcpy2DAsync(keys + 1, 16, src->k1, 8, 8, cnt, cudaMemcpyDeviceToHost,
                             st->stream);
   }
   if (e == cudaSuccess) {
     if (st->amp32) {
       s = ensure_scratch(st, cnt * 16);
       if (s != SQS_OK) return s;
-      e = sqs::launch_to_f64(launch_of(st, cnt), st->ctl, st->cur.view(), st->cur_slot,
+      e = sqs::launch_to_f64(launch_of(st, cnt), st->ctl, src->view(), st->cur_slot,
                              st->scratch);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(amps, st->scratch, cnt * 16, cudaMemcpyDeviceToHost, st->stream);
     } else {
-      e = cudaMemcpyAsync(amps, st->cur.amp, cnt * 16, cudaMemcpyDeviceToHost, st->stream);
+      e = cudaMemcpyAsync(amps, src->amp, cnt * 16, cudaMemcpyDeviceToHost, st->stream);
     }
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);

@@ -81,10 +81,11 @@ __device__ __forceinline__ uint64_t khash(u128 k) {
 }
 
 // ---- amplitudes ------------------------------------------------------------
-// Arithmetic runs in the storage type: FP64 states in FP64, FP32 states in
-// FP32 (the FP32 pipe is 64x wider than the FP64 pipe here).  Two-term sums
-// of FP32 products are single FP32 roundings of the exact sum, which is the
-// value an FP64 accumulation rounded to the FP32 store would give.
+// FP64 states compute in FP64.  FP32-storage states keep the non-interference
+// factors (phase tables) in FP32, and evaluate every child of an interference
+// step with compensated FP32 arithmetic (error-free products and sums, below)
+// that matches an FP64 accumulation rounded once to FP32: the FP32 pipe is 64x
+// wider than the FP64 pipe on this GPU.
 // Complex product with one product fused into the sum (two instructions per
 // component): one rounding fewer than the host's complex<double> product.
 // The sign sits on an input of the FMA (a negated multiplicand), never on a
@@ -314,10 +315,12 @@ __device__ __forceinline__ bool apply_ops(uint32_t n_ops, const DevOp* ops, cons
 
 // The same run applied to NI branches at once, operation-major: each
 // operation's descriptor is read from shared memory and dispatched once for
-// the NI branches a thread carries, instead of once per branch.  Per branch
-// the arithmetic and its order are those of apply_ops.  live[q] is cleared
-// for a branch the run prunes; branches already dead are left alone (their
-// QRAM reads are skipped).
+// the NI branches a thread carries, instead of once per branch.  Dispatch is
+// one switch per operation; a run of conditional XORs (X, CNOT, Toffoli, the
+// commonest kind) stays in an inner loop that tests only the next kind.  Per
+// branch the arithmetic and its order are those of apply_ops.  live[q] is
+// cleared for a branch the run prunes; branches already dead are left alone
+// (their QRAM reads are skipped).
 template <int KW, class AT, int NI>
 __device__ __forceinline__ void apply_ops_n(uint32_t n_ops, const DevOp* ops, const AT* tab,
                                             typename KT<KW>::T (&k)[NI], AT (&a)[NI],
@@ -329,83 +332,122 @@ __device__ __forceinline__ void apply_ops_n(uint32_t n_ops, const DevOp* ops, co
 #pragma unroll 1
   for (uint32_t o = 0; o < n_ops; ++o) {
     const DevOp& op = ops[o];
-    const uint32_t kind = op.kind;
-    const K pm = mk<KW>(op.pmask[0], op.pmask[1]);
-    const K pv = mk<KW>(op.pval[0], op.pval[1]);
-    if (kind == OP_XOR) {
-      const K xm = mk<KW>(op.xmask[0], op.xmask[1]);
+    switch (op.kind) {
+      case OP_XOR: {
+#pragma unroll 1
+        for (;;) {
+          const DevOp& x = ops[o];
+          const K pm = mk<KW>(x.pmask[0], x.pmask[1]);
+          const K pv = mk<KW>(x.pval[0], x.pval[1]);
+          const K xm = mk<KW>(x.xmask[0], x.xmask[1]);
 #pragma unroll
-      for (int q = 0; q < NI; ++q)
-        if ((k[q] & pm) == pv) k[q] ^= xm;
-    } else if (kind == OP_MUL || kind == OP_MUL_XOR) {
-      const uint32_t sel = op.sel_bit, sh = op.shift;
-      const K xm = kind == OP_MUL_XOR ? mk<KW>(op.xmask[0], op.xmask[1]) : (K)0;
-#pragma unroll
-      for (int q = 0; q < NI; ++q) {
-        if ((k[q] & pm) == pv) {
-          const uint32_t one = sel < 128 ? (uint32_t)((k[q] >> sel) & (K)1) : 0u;
-          idx[q] |= (1u + one) << sh;
-          k[q] ^= xm;
+          for (int q = 0; q < NI; ++q) k[q] ^= ((k[q] & pm) == pv) ? xm : (K)0;
+          if (o + 1 >= n_ops || ops[o + 1].kind != OP_XOR) break;
+          ++o;
         }
+        break;
       }
-    } else if (kind == OP_ADD_REG || kind == OP_SUB_REG || kind == OP_ADD_CONST) {
-      const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
-      const uint64_t c = op.constant;
+      case OP_MUL:
+      case OP_MUL_XOR: {
+        const K pm = mk<KW>(op.pmask[0], op.pmask[1]);
+        const K pv = mk<KW>(op.pval[0], op.pval[1]);
+        const uint32_t sel = op.sel_bit, sh = op.shift;
+        const K xm = op.kind == OP_MUL_XOR ? mk<KW>(op.xmask[0], op.xmask[1]) : (K)0;
 #pragma unroll
-      for (int q = 0; q < NI; ++q) {
-        if ((k[q] & pm) == pv) {
-          const uint64_t d = get_field(k[q], doff, dw);
-          const uint64_t sv = kind == OP_ADD_CONST ? c : get_field(k[q], soff, sw);
-          k[q] = set_field<K>(k[q], doff, dw, kind == OP_SUB_REG ? d - sv : d + sv);
-        }
-      }
-    } else if (kind == OP_TABLE) {
-      const uint32_t base = op.tab_off;
-#pragma unroll
-      for (int q = 0; q < NI; ++q) {
-        if (idx[q]) a[q] = cmul(a[q], tab[base + idx[q]]);
-        idx[q] = 0;
-      }
-    } else if (kind == OP_QRAM) {
-      const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
-      const uint64_t n_ent = op.n_entries;
-      const uint32_t eb = (uint32_t)op.constant;
-      const void* tbl = op.table;
-#pragma unroll
-      for (int q = 0; q < NI; ++q) {
-        if (live[q] && (k[q] & pm) == pv) {
-          const uint64_t addr = get_field(k[q], soff, sw);
-          uint64_t d = 0;
-          if (addr < n_ent) {
-            switch (eb) {
-              case 1: d = __ldg((const uint8_t*)tbl + addr); break;
-              case 2: d = __ldg((const uint16_t*)tbl + addr); break;
-              case 4: d = __ldg((const uint32_t*)tbl + addr); break;
-              default: d = __ldg((const unsigned long long*)tbl + addr); break;
-            }
+        for (int q = 0; q < NI; ++q) {
+          if ((k[q] & pm) == pv) {
+            const uint32_t one = sel < 128 ? (uint32_t)((k[q] >> sel) & (K)1) : 0u;
+            idx[q] |= (1u + one) << sh;
+            k[q] ^= xm;
           }
-          k[q] = set_field<K>(k[q], doff, dw, get_field(k[q], doff, dw) ^ d);
         }
+        break;
       }
-    } else if (kind == OP_SWAP) {
-      const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
+      case OP_ADD_REG:
+      case OP_SUB_REG:
+      case OP_ADD_CONST: {
+        const K pm = mk<KW>(op.pmask[0], op.pmask[1]);
+        const K pv = mk<KW>(op.pval[0], op.pval[1]);
+        const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
+        const uint64_t c = op.constant;
+        const bool sub = op.kind == OP_SUB_REG, cst = op.kind == OP_ADD_CONST;
 #pragma unroll
-      for (int q = 0; q < NI; ++q) {
-        if ((k[q] & pm) == pv) {
-          const uint64_t v1 = get_field(k[q], doff, dw);
-          const uint64_t v2 = get_field(k[q], soff, sw);
-          k[q] = set_field<K>(set_field<K>(k[q], doff, dw, v2), soff, sw, v1);
+        for (int q = 0; q < NI; ++q) {
+          if ((k[q] & pm) == pv) {
+            const uint64_t d = get_field(k[q], doff, dw);
+            const uint64_t sv = cst ? c : get_field(k[q], soff, sw);
+            k[q] = set_field<K>(k[q], doff, dw, sub ? d - sv : d + sv);
+          }
         }
+        break;
       }
-    } else if (kind == OP_PRUNE) {
-      const double eps = op.eps, eps2 = op.eps2;
+      case OP_TABLE: {
+        const uint32_t base = op.tab_off;
 #pragma unroll
-      for (int q = 0; q < NI; ++q)
-        if (live[q] && !keep_amp(a[q], eps, (float)eps, eps2)) live[q] = false;
-    } else if (kind == OP_MUL_ADD || kind == OP_MUL_CONST || kind == OP_DIV_XOR) {
+        for (int q = 0; q < NI; ++q) {
+          if (idx[q]) a[q] = cmul(a[q], tab[base + idx[q]]);
+          idx[q] = 0;
+        }
+        break;
+      }
+      case OP_QRAM: {
+        const K pm = mk<KW>(op.pmask[0], op.pmask[1]);
+        const K pv = mk<KW>(op.pval[0], op.pval[1]);
+        const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
+        const uint64_t n_ent = op.n_entries;
+        const uint32_t eb = (uint32_t)op.constant;
+        const void* tbl = op.table;
 #pragma unroll
-      for (int q = 0; q < NI; ++q)
-        if ((k[q] & pm) == pv) k[q] = arith_op(op, k[q]);
+        for (int q = 0; q < NI; ++q) {
+          if (live[q] && (k[q] & pm) == pv) {
+            const uint64_t addr = get_field(k[q], soff, sw);
+            uint64_t d = 0;
+            if (addr < n_ent) {
+              switch (eb) {
+                case 1: d = __ldg((const uint8_t*)tbl + addr); break;
+                case 2: d = __ldg((const uint16_t*)tbl + addr); break;
+                case 4: d = __ldg((const uint32_t*)tbl + addr); break;
+                default: d = __ldg((const unsigned long long*)tbl + addr); break;
+              }
+            }
+            k[q] = set_field<K>(k[q], doff, dw, get_field(k[q], doff, dw) ^ d);
+          }
+        }
+        break;
+      }
+      case OP_SWAP: {
+        const K pm = mk<KW>(op.pmask[0], op.pmask[1]);
+        const K pv = mk<KW>(op.pval[0], op.pval[1]);
+        const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
+#pragma unroll
+        for (int q = 0; q < NI; ++q) {
+          if ((k[q] & pm) == pv) {
+            const uint64_t v1 = get_field(k[q], doff, dw);
+            const uint64_t v2 = get_field(k[q], soff, sw);
+            k[q] = set_field<K>(set_field<K>(k[q], doff, dw, v2), soff, sw, v1);
+          }
+        }
+        break;
+      }
+      case OP_PRUNE: {
+        const double eps = op.eps, eps2 = op.eps2;
+#pragma unroll
+        for (int q = 0; q < NI; ++q)
+          if (live[q] && !keep_amp(a[q], eps, (float)eps, eps2)) live[q] = false;
+        break;
+      }
+      case OP_MUL_ADD:
+      case OP_MUL_CONST:
+      case OP_DIV_XOR: {
+        const K pm = mk<KW>(op.pmask[0], op.pmask[1]);
+        const K pv = mk<KW>(op.pval[0], op.pval[1]);
+#pragma unroll
+        for (int q = 0; q < NI; ++q)
+          if ((k[q] & pm) == pv) k[q] = arith_op(op, k[q]);
+        break;
+      }
+      default:
+        break;
     }
   }
 }
@@ -446,15 +488,97 @@ struct Coef<float2> {
   __device__ static float r(const Gate1& g, int e) { return g.uf[2 * e]; }
 };
 
-// FP32 storage: a two-term sum that lands below the rounding noise of its
-// terms (2^-21 of their size, a few units in the last place) is a
-// cancellation that FP64 arithmetic would have made (near) exact; it is
-// flushed to zero so that the pruning step removes it.  FP64 states keep
-// their results as computed.
-__device__ __forceinline__ void flush_residue(double2&, double2, double2) {}
-__device__ __forceinline__ void flush_residue(float2& o, float2 a0, float2 a1) {
-  const float size = fabsf(a0.x) + fabsf(a0.y) + fabsf(a1.x) + fabsf(a1.y);
-  if (fabsf(o.x) + fabsf(o.y) <= size * 4.76837158e-7f) o = make_float2(0.f, 0.f);
+// ---- FP32 storage: compensated evaluation of a child ------------------------
+// A child of an interference step is a short dot product, sum_i u_i a_i, of
+// real coefficients u_i (matrix entries, or their real and imaginary parts)
+// with FP32 amplitude components a_i.  It is evaluated as Dot2 of Ogita, Rump
+// and Oishi (SIAM J. Sci. Comput. 26, 2005): every product split exactly into
+// a rounded part and its error by an FMA (Dekker's two-product), the rounded
+// parts summed with Knuth's error-free two-sum, and all error terms added back
+// before the one final rounding.  The coefficients are carried as float-float
+// pairs (h + l, the FP64 value to about 48 bits), so the result is the
+// FP64-accurate sum of the FP64 coefficients times the stored amplitudes,
+// rounded once to FP32: error at most half an FP32 ulp plus about 2^-46 of
+// sum_i |u_i a_i|.
+//
+// Cancellation at storage precision.  Every stored FP32 component carries the
+// rounding of its own last store, and the roundings of every operation since
+// the branch split from its partner, each up to 2^-24 of its size.  A sum
+// whose exact value is zero in the FP64 method (RY(t) then RY(-t) on the same
+// qubit; a reflection that restores a state) therefore ends up at some units
+// of 2^-24 of the terms' size, far above any pruning threshold, and would
+// never leave the state.  A component whose compensated value is at most
+// rho * sum_i |u_i a_i| carries no significant bit of the stored inputs: it
+// is set to exactly zero, and the pruning test (keep_amp) removes the child
+// when both components are zero.  rho is a per-state setting (Gate1::rho32,
+// default 2^-19 = 32 units of FP32 roundoff, covering circuits where the two
+// members went through a few dozen roundings since their common ancestor).
+// The change to a component is at most rho * sum_i |u_i a_i|: relative to the
+// terms, the same order as the storage rounding the inputs already carry.
+// Single-member children are single products: no cancellation, no flush.
+struct FF {
+  float h, l;  // value h + l, |l| <= ulp(h) / 2
+};
+__device__ __forceinline__ FF ff_neg(FF u) { return FF{-u.h, -u.l}; }
+// FP64 -> float-float (register-valued angles: cos / sin of the half angle).
+__device__ __forceinline__ FF ff_of(double u) {
+  const float h = __double2float_rn(u);
+  return FF{h, __double2float_rn(u - (double)h)};
+}
+
+// Accumulates u * a into (s, c): s the running rounded sum, c the running sum
+// of the error terms.
+__device__ __forceinline__ void dot2_acc(FF u, float a, float& s, float& c) {
+  const float p = __fmul_rn(u.h, a);
+  const float e = __fmaf_rn(u.l, a, __fmaf_rn(u.h, a, -p));  // u a - p, to ~2^-48
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));  // s + p - t
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+__device__ __forceinline__ float dot2_1(FF u, float a) {
+  const float p = __fmul_rn(u.h, a);
+  return __fadd_rn(p, __fmaf_rn(u.l, a, __fmaf_rn(u.h, a, -p)));
+}
+// u0 a0 + u1 a1, with the storage-precision cancellation flush.
+__device__ __forceinline__ float dot2_2(FF u0, float a0, FF u1, float a1, float rho) {
+  float s = __fmul_rn(u0.h, a0);
+  float c = __fmaf_rn(u0.l, a0, __fmaf_rn(u0.h, a0, -s));
+  dot2_acc(u1, a1, s, c);
+  const float r = __fadd_rn(s, c);
+  const float size = __fmaf_rn(fabsf(u0.h), fabsf(a0), __fmul_rn(fabsf(u1.h), fabsf(a1)));
+  return fabsf(r) <= __fmul_rn(rho, size) ? 0.0f : r;
+}
+// u0 a0 + u1 a1 + u2 a2 + u3 a3 (complex coefficients), with the flush.
+__device__ __forceinline__ float dot2_4(FF u0, float a0, FF u1, float a1, FF u2, float a2, FF u3,
+                                        float a3, float rho) {
+  float s = __fmul_rn(u0.h, a0);
+  float c = __fmaf_rn(u0.l, a0, __fmaf_rn(u0.h, a0, -s));
+  dot2_acc(u1, a1, s, c);
+  dot2_acc(u2, a2, s, c);
+  dot2_acc(u3, a3, s, c);
+  const float r = __fadd_rn(s, c);
+  float size = __fmul_rn(fabsf(u0.h), fabsf(a0));
+  size = __fmaf_rn(fabsf(u1.h), fabsf(a1), size);
+  size = __fmaf_rn(fabsf(u2.h), fabsf(a2), size);
+  size = __fmaf_rn(fabsf(u3.h), fabsf(a3), size);
+  return fabsf(r) <= __fmul_rn(rho, size) ? 0.0f : r;
+}
+// u a (complex u, no flush: one member).
+__device__ __forceinline__ float2 cdot2_1(FF ur, FF ui, float2 a) {
+  float s = __fmul_rn(ur.h, a.x);
+  float c = __fmaf_rn(ur.l, a.x, __fmaf_rn(ur.h, a.x, -s));
+  dot2_acc(ff_neg(ui), a.y, s, c);
+  float s2 = __fmul_rn(ur.h, a.y);
+  float c2 = __fmaf_rn(ur.l, a.y, __fmaf_rn(ur.h, a.y, -s2));
+  dot2_acc(ui, a.x, s2, c2);
+  return make_float2(__fadd_rn(s, c), __fadd_rn(s2, c2));
+}
+// The coefficient of entry e (0: U00, 1: U01, 2: U10, 3: U11), part p (0
+// real, 1 imaginary), as float-float (host-rounded pairs in Gate1).
+__device__ __forceinline__ FF ff_coef(const Gate1& g, int e, int p) {
+  return FF{g.uf[2 * e + p], g.ufl[2 * e + p]};
 }
 
 // cos and sin of theta / 2 for theta = scale * v + offset (mode 1).  With a
@@ -482,7 +606,15 @@ __device__ __forceinline__ void half_angle_cs(const Gate1& g, uint64_t v, double
 
 template <class AT>
 __device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, bool has0, AT a0,
-                                         bool has1, AT a1, AT& o0, AT& o1) {
+                                         bool has1, AT a1, AT& o0, AT& o1);
+
+// FP64 storage: FP64 arithmetic, products shared between rows where the host
+// flagged equal coefficients.
+template <>
+__device__ __forceinline__ void children<double2>(const Gate1& g, uint64_t angle_value, bool has0,
+                                                  double2 a0, bool has1, double2 a1, double2& o0,
+                                                  double2& o1) {
+  typedef double2 AT;
   typedef typename Coef<AT>::S S;
   const bool same0 = g.reuse & 1u, neg0 = g.reuse & 4u;  // U10 = +-U00
   const bool same1 = g.reuse & 2u, neg1 = g.reuse & 8u;  // U11 = +-U01
@@ -503,8 +635,6 @@ __device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, b
         o1 = neg1 ? rfms(u10, a0, p01) : rfma(u10, a0, p01);
       else
         o1 = rfma(u10, a0, rmul(u11, a1));
-      flush_residue(o0, a0, a1);
-      flush_residue(o1, a0, a1);
     } else if (has0) {
       o0 = rmul(u00, a0);
       o1 = same0 ? (neg0 ? cneg(o0) : o0) : rmul(u10, a0);
@@ -520,8 +650,6 @@ __device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, b
       const AT p11 = same1 ? (neg1 ? cneg(p01) : p01) : cmul(U11, a1);
       o0 = cfma(U00, a0, p01);
       o1 = cfma(U10, a0, p11);
-      flush_residue(o0, a0, a1);
-      flush_residue(o1, a0, a1);
     } else if (has0) {
       o0 = cmul(U00, a0);
       o1 = same0 ? (neg0 ? cneg(o0) : o0) : cmul(U10, a0);
@@ -532,23 +660,71 @@ __device__ __forceinline__ void children(const Gate1& g, uint64_t angle_value, b
   }
 }
 
+// FP32 storage: every child by the compensated evaluation above.
+template <>
+__device__ __forceinline__ void children<float2>(const Gate1& g, uint64_t angle_value, bool has0,
+                                                 float2 a0, bool has1, float2 a1, float2& o0,
+                                                 float2& o1) {
+  if (g.mode == 2 || g.mode == 1) {
+    FF u00, u01, u10, u11;
+    if (g.mode == 1) {
+      double sn, cs;
+      half_angle_cs(g, angle_value, cs, sn);
+      u00 = ff_of(cs), u10 = ff_of(sn);
+      u01 = ff_neg(u10), u11 = u00;
+    } else {
+      u00 = ff_coef(g, 0, 0), u01 = ff_coef(g, 1, 0), u10 = ff_coef(g, 2, 0),
+      u11 = ff_coef(g, 3, 0);
+    }
+    if (has0 && has1) {
+      const float rho = g.rho32;
+      o0 = make_float2(dot2_2(u00, a0.x, u01, a1.x, rho), dot2_2(u00, a0.y, u01, a1.y, rho));
+      o1 = make_float2(dot2_2(u10, a0.x, u11, a1.x, rho), dot2_2(u10, a0.y, u11, a1.y, rho));
+    } else if (has0) {
+      o0 = make_float2(dot2_1(u00, a0.x), dot2_1(u00, a0.y));
+      o1 = make_float2(dot2_1(u10, a0.x), dot2_1(u10, a0.y));
+    } else {
+      o0 = make_float2(dot2_1(u01, a1.x), dot2_1(u01, a1.y));
+      o1 = make_float2(dot2_1(u11, a1.x), dot2_1(u11, a1.y));
+    }
+  } else {
+    if (has0 && has1) {
+      // Re(U_r0 a0 + U_r1 a1) and Im(...): four real products each.
+      for (int r = 0; r < 2; ++r) {
+        const FF xr = ff_coef(g, 2 * r, 0), xi = ff_coef(g, 2 * r, 1);
+        const FF yr = ff_coef(g, 2 * r + 1, 0), yi = ff_coef(g, 2 * r + 1, 1);
+        const float2 o = make_float2(
+            dot2_4(xr, a0.x, ff_neg(xi), a0.y, yr, a1.x, ff_neg(yi), a1.y, g.rho32),
+            dot2_4(xr, a0.y, xi, a0.x, yr, a1.y, yi, a1.x, g.rho32));
+        if (r == 0) o0 = o; else o1 = o;
+      }
+    } else if (has0) {
+      o0 = cdot2_1(ff_coef(g, 0, 0), ff_coef(g, 0, 1), a0);
+      o1 = cdot2_1(ff_coef(g, 2, 0), ff_coef(g, 2, 1), a0);
+    } else {
+      o0 = cdot2_1(ff_coef(g, 1, 0), ff_coef(g, 1, 1), a1);
+      o1 = cdot2_1(ff_coef(g, 3, 0), ff_coef(g, 3, 1), a1);
+    }
+  }
+}
+
 // One child of a pair whose both members are present, real coefficients
 // (mode 2): the same expression children() evaluates for it.
 template <class AT>
-__device__ __forceinline__ AT child_real(const Gate1& g, int r, AT a0, AT a1) {
-  typedef typename Coef<AT>::S S;
-  const S u00 = Coef<AT>::r(g, 0), u01 = Coef<AT>::r(g, 1), u10 = Coef<AT>::r(g, 2),
-          u11 = Coef<AT>::r(g, 3);
-  const AT p01 = rmul(u01, a1);
-  AT o;
-  if (r == 0) {
-    o = rfma(u00, a0, p01);
-  } else {
-    const bool same1 = g.reuse & 2u, neg1 = g.reuse & 8u;
-    o = same1 ? (neg1 ? rfms(u10, a0, p01) : rfma(u10, a0, p01)) : rfma(u10, a0, rmul(u11, a1));
-  }
-  flush_residue(o, a0, a1);
-  return o;
+__device__ __forceinline__ AT child_real(const Gate1& g, int r, AT a0, AT a1);
+template <>
+__device__ __forceinline__ double2 child_real<double2>(const Gate1& g, int r, double2 a0,
+                                                       double2 a1) {
+  const double u00 = g.u[0], u01 = g.u[2], u10 = g.u[4], u11 = g.u[6];
+  const double2 p01 = rmul(u01, a1);
+  if (r == 0) return rfma(u00, a0, p01);
+  const bool same1 = g.reuse & 2u, neg1 = g.reuse & 8u;
+  return same1 ? (neg1 ? rfms(u10, a0, p01) : rfma(u10, a0, p01)) : rfma(u10, a0, rmul(u11, a1));
+}
+template <>
+__device__ __forceinline__ float2 child_real<float2>(const Gate1& g, int r, float2 a0, float2 a1) {
+  const FF ur0 = ff_coef(g, 2 * r, 0), ur1 = ff_coef(g, 2 * r + 1, 0);
+  return make_float2(dot2_2(ur0, a0.x, ur1, a1.x, g.rho32), dot2_2(ur0, a0.y, ur1, a1.y, g.rho32));
 }
 
 // 2 x, exactly, in integer arithmetic on the IEEE encoding (no FP64
@@ -585,8 +761,9 @@ __device__ __forceinline__ double2 fold_child<double2>(const Gate1& g, int r, do
   return make_double2(twice(__dmul_rn(u, a0.x)), twice(__dmul_rn(u, a0.y)));
 }
 
-// Both components' magnitudes below the bit pattern t (FP64 storage); an
-// FP32 residue is always flushed, so the test passes.
+// Both components' magnitudes below the bit pattern t (FP64 storage).  For
+// FP32 storage the cancelling child of a fold is u a + (-u) a evaluated
+// compensated, which is exactly zero, so the test passes.
 __device__ __forceinline__ bool below_bits(double2 a, uint64_t t) {
   return ((unsigned long long)__double_as_longlong(a.x) & 0x7fffffffffffffffull) < t &&
          ((unsigned long long)__double_as_longlong(a.y) & 0x7fffffffffffffffull) < t;

@@ -349,20 +349,14 @@ template <int KW, class AT>
 cudaError_t group_t(const Launch& L, Ctl* ctl, Arr in, const unsigned long long* n_ptr,
                     uint32_t tile_len, uint64_t n_tiles, Arr out, int out_slot,
                     const GroupRun& run) {
-  static unsigned long long configured = 0;  // opt-in above 48 KB, per device
+  static std::atomic<unsigned long long> configured{0};  // opt-in above 48 KB, per device
   const size_t smem = GroupSmem<KW, AT>::bytes;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && !(configured & (1ull << dev))) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_group<KW, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured |= 1ull << dev;
-  }
+  cudaError_t e = ensure_smem_optin((const void*)k_group<KW, AT>, smem, configured);
+  if (e != cudaSuccess) return e;
   const uint64_t grid = n_tiles < (uint64_t)L.sm_count * 64 ? n_tiles : (uint64_t)L.sm_count * 64;
   k_group<KW, AT><<<(int)(grid ? grid : 1), kGroupThreads, smem, L.stream>>>(
       ctl, in, n_ptr, tile_len, out, out_slot, run, L.seq);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_group_peak<<<1, 32, 0, L.stream>>>(ctl, run.k);
   return cudaGetLastError();

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace sqs {
 
 // ---------------------------------------------------------------------------
@@ -106,7 +108,9 @@ struct Gate1 {            // the interference operation of one merge step
   uint32_t mode;          // 0: complex U, 1: RY from a register value, 2: real U
   uint64_t cmask[2], cval[2];  // controls
   double u[8];            // U row-major (re, im)
-  float uf[8];            // U rounded to FP32 (FP32-storage states)
+  float uf[8];            // U rounded to FP32 (FP32-storage states)...
+  float ufl[8];           // ...and the rest, u - uf rounded to FP32 (float-float)
+  float rho32;            // FP32 storage: cancellation threshold (relative to the terms)
   // Product reuse: bit 0 set when U10 = +-U00 (bit 2: minus), bit 1 when
   // U11 = +-U01 (bit 3: minus); each column then costs one product per branch.
   uint32_t reuse;
@@ -156,6 +160,11 @@ struct Launch {
   int sm_count;
   uint32_t seq;        // launch sequence number (error attribution)
   uint64_t n_hint;     // host-side upper bound of the branches streamed (grid size)
+  // Bounded device waits (cluster merge): polls before giving up (0: the
+  // default), and a testing hook -- a cluster rank whose CTAs issue no bulk
+  // copy, so that their wait runs out (-1: none).
+  uint32_t wait_limit = 0;
+  int32_t skip_copy_rank = -1;
 };
 
 // Launchers (sqs_kernels.cu).  Each returns cudaGetLastError() after enqueueing.
@@ -214,6 +223,11 @@ cudaError_t launch_pair(const Launch& L, int kw, bool amp32, Ctl* ctl, const Gat
 cudaError_t launch_expand(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
                           uint64_t n_chunks, const OpList& ops, const Gate1& g, Arr out,
                           int out_slot);
+// Copy-pair fold of a gate without controls (g.fold_sign != 0, no control
+// bits): only the bit-0 members are read past their key and emit.
+cudaError_t launch_fold(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
+                        uint64_t n_chunks, const OpList& ops, const Gate1& g, Arr out,
+                        int out_slot);
 cudaError_t launch_probabilities(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr a, int slot,
                                  uint32_t off, uint32_t w, double* probs, double* norm2);
 // Copies a segmented array into a dense one given exclusive segment offsets.
@@ -253,6 +267,37 @@ cudaError_t launch_group_count(const Launch& L, int kw, Ctl* ctl, Arr in,
 cudaError_t launch_group(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in,
                          const unsigned long long* n_ptr, uint32_t tile_len, uint64_t n_tiles,
                          Arr out, int out_slot, const GroupRun& run);
+// Raises a kernel's dynamic shared-memory limit to `smem` bytes on the
+// current device, once per device.  The attribute is per device; the
+// bitmask of devices already configured is shared by host threads, so it is
+// updated atomically (two threads that race both set the same attribute,
+// which is harmless).
+inline cudaError_t ensure_smem_optin(const void* func, size_t smem,
+                                     std::atomic<unsigned long long>& configured) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64) return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+  const unsigned long long bit = 1ull << dev;
+  if (configured.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) configured.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
+// Sparse marginals (sqs_readout.cu) over `sorted`: the dense state (count
+// *n_ptr) sorted by the field [off, off + w), ascending.  Writes the distinct
+// field values in ascending order to values[] and the sum of |a|^2 over each
+// value's branches to probs[], and their number to *total.  Scratch: runs[],
+// lead_sum[], lead_full[] of run_tiles(n) entries each.
+uint64_t run_tiles(uint64_t n);
+cudaError_t launch_sparse_marginals(const Launch& L, int kw, bool amp32, const Ctl* ctl, Arr sorted,
+                                    const unsigned long long* n_ptr, uint64_t n_tiles, uint32_t off,
+                                    uint32_t w, unsigned int* runs, double* lead_sum,
+                                    unsigned int* lead_full, unsigned long long* total,
+                                    uint64_t* values, double* probs);
+
 int pair_log2_capacity(int kw, bool amp32);  // log2 branches per bucket
 size_t pair_smem_bytes(int kw, bool amp32);  // dynamic shared memory of one bucket CTA
 

@@ -570,6 +570,207 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
 }
 
 // ---------------------------------------------------------------------------
+// Copy-pair fold without controls: only the bit-0 member of each pair emits
+// (the pair's two children), so the bit-1 members need neither their
+// amplitude nor the fused run.  The run never reads or writes the target bit
+// (the host drops a bit's copy-pair property as soon as an operation touches
+// it), so a member's target bit is already known from its loaded key.
+//
+// Each CTA stages kFoldSub input slots at a time: phase 1 reads every key
+// (coalesced), tests the target bit, loads the amplitudes of the bit-0
+// members only and compacts those members into shared memory; phase 2 runs
+// the fused run and the fold on the compacted list, so every lane of the
+// FP64 sequence holds a member that emits.  The arithmetic per member is the
+// fold branch of k_expand, so the state is bit-identical to it.
+constexpr uint32_t kFoldSub = 2048;
+constexpr int kFoldILP = 2;
+
+template <int KW, class AT>
+constexpr size_t fold_smem_bytes() {
+  return (size_t)kFoldSub * (sizeof(typename KT<KW>::T) + sizeof(AT));
+}
+
+template <int KW, class AT>
+__global__ void __launch_bounds__(kStreamThreads, 3)
+    k_fold(Ctl* ctl, Arr in, int in_slot, uint64_t n_chunks, Arr out, int out_slot,
+           const __grid_constant__ OpList ops, Gate1 g, uint32_t seq) {
+  typedef typename KT<KW>::T K;
+  __shared__ AT tab[kTabEntries];
+  __shared__ DevOp sops[kMaxOps];
+  __shared__ unsigned int wtot[kStreamThreads / 32];
+  __shared__ unsigned long long round_base;
+  __shared__ unsigned int n_act;
+  extern __shared__ __align__(16) unsigned char fold_smem[];
+  K* skey = (K*)fold_smem;
+  AT* samp = (AT*)(fold_smem + (size_t)kFoldSub * sizeof(K));
+  if (ctl->err) return;
+  load_ops(ops, sops, tab);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->cnt[(out_slot + 1) & 3] = 0;
+    atomicMax(&ctl->peak, ctl->cnt[in_slot]);
+  }
+  const uint64_t n_dense = ctl->cnt[in_slot];
+  const uint64_t chunk = 1ull << kExpandChunkLog2;
+  if (!in.seg_cnt && n_dense > (n_chunks << kExpandChunkLog2)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) raise_err(ctl, kErrCapacity, seq, n_dense);
+    return;
+  }
+  const uint32_t cps_log2 = in.seg_cnt ? in.seg_log2 - kExpandChunkLog2 : 0u;
+  const K bmask = bit_mask<KW>(g.t);
+  const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const unsigned int lt = (1u << lane) - 1u;
+  constexpr int kPer = (int)(kFoldSub / kStreamThreads);
+  for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    uint64_t ibase, cnt;
+    if (in.seg_cnt) {
+      const uint64_t sg = c >> cps_log2;
+      const uint64_t off = (c & ((1ull << cps_log2) - 1ull)) << kExpandChunkLog2;
+      const uint64_t n_sg = sg < in.n_seg ? in.seg_cnt[sg] : 0;
+      ibase = (sg << in.seg_log2) + off;
+      cnt = n_sg > off ? (n_sg - off < chunk ? n_sg - off : chunk) : 0;
+    } else {
+      ibase = c << kExpandChunkLog2;
+      cnt = ibase >= n_dense ? 0 : (n_dense - ibase < chunk ? n_dense - ibase : chunk);
+    }
+    for (uint64_t s0 = 0; s0 < cnt; s0 += kFoldSub) {
+      const uint32_t scnt = (uint32_t)(cnt - s0 < kFoldSub ? cnt - s0 : kFoldSub);
+      const uint64_t sbase = ibase + s0;
+      // ---- phase 1: keys, target-bit test, bit-0 amplitudes, compaction ----
+      K kk[kPer];
+      AT av[kPer];
+      unsigned int bal[kPer];
+      unsigned int mine = 0;
+#pragma unroll
+      for (int r = 0; r < kPer; ++r) {
+        const uint32_t j = (uint32_t)r * kStreamThreads + threadIdx.x;
+        bool act = false;
+        kk[r] = 0;
+        if (j < scnt) {
+          kk[r] = ld_key<KW>(in, sbase + j);
+          act = (kk[r] & bmask) == (K)0;
+        }
+        if (act) av[r] = ((const AT*)in.amp)[sbase + j];
+        bal[r] = __ballot_sync(0xffffffffu, act);
+        mine += __popc(bal[r]);
+      }
+      if (lane == 0) wtot[warp] = mine;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned int sum = 0;
+        for (unsigned int w = 0; w < kStreamThreads / 32u; ++w) {
+          const unsigned int t = wtot[w];
+          wtot[w] = sum;
+          sum += t;
+        }
+        n_act = sum;
+      }
+      __syncthreads();
+      {
+        unsigned int pos = wtot[warp];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+          if ((bal[r] >> lane) & 1u) {
+            const unsigned int p = pos + __popc(bal[r] & lt);
+            skey[p] = kk[r];
+            samp[p] = av[r];
+          }
+          pos += __popc(bal[r]);
+        }
+      }
+      __syncthreads();
+      const uint32_t na = n_act;
+      // ---- phase 2: fused run and fold on the compacted bit-0 members ----
+      for (uint32_t r0 = 0; r0 < na; r0 += kFoldILP * kStreamThreads) {
+        K k[kFoldILP];
+        AT v[kFoldILP];
+        bool live[kFoldILP];
+#pragma unroll
+        for (int q = 0; q < kFoldILP; ++q) {
+          const uint32_t i = r0 + (uint32_t)q * kStreamThreads + threadIdx.x;
+          live[q] = i < na;
+          k[q] = 0;
+          v[q].x = v[q].y = 0;
+          if (live[q]) {
+            k[q] = skey[i];
+            v[q] = samp[i];
+          }
+        }
+        apply_ops_n<KW, AT, kFoldILP>(ops.n, sops, tab, k, v, live);
+        K k0[kFoldILP], k1[kFoldILP];
+        AT o0[kFoldILP], o1[kFoldILP];
+        unsigned int b0[kFoldILP], b1[kFoldILP];
+        unsigned int wsum = 0;
+#pragma unroll
+        for (int q = 0; q < kFoldILP; ++q) {
+          bool keep0 = false, keep1 = false;
+          k0[q] = k[q];
+          k1[q] = k[q] | bmask;
+          if (live[q]) {
+            const uint64_t avv = g.mode == 1 ? get_field(k0[q], g.ang_off, g.ang_w) : 0ull;
+            auto fold = [&](const AT& a1) {
+              if (g.fold_kill >= 0 && below_bits(v[q], g.fold_tmax)) {
+                if (g.fold_kill == 1) {
+                  o0[q] = fold_child<AT>(g, 0, v[q], a1);
+                  keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
+                } else {
+                  o1[q] = fold_child<AT>(g, 1, v[q], a1);
+                  keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
+                }
+              } else {
+                children<AT>(g, avv, true, v[q], true, a1, o0[q], o1[q]);
+                keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
+                keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
+              }
+            };
+            if (g.fold_sign > 0)
+              fold(v[q]);
+            else
+              fold(cneg(v[q]));
+          }
+          b0[q] = __ballot_sync(0xffffffffu, keep0);
+          b1[q] = __ballot_sync(0xffffffffu, keep1);
+          wsum += __popc(b0[q]) + __popc(b1[q]);
+        }
+        if (lane == 0) wtot[warp] = wsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          unsigned int sum = 0;
+          for (unsigned int w = 0; w < kStreamThreads / 32u; ++w) {
+            const unsigned int t = wtot[w];
+            wtot[w] = sum;
+            sum += t;
+          }
+          round_base = sum ? atomicAdd(&ctl->cnt[out_slot], (unsigned long long)sum) : 0ull;
+          if (sum && round_base + sum > out.cap)
+            raise_err(ctl, kErrCapacity, seq, round_base + sum);
+        }
+        __syncthreads();
+        uint64_t wb = round_base + wtot[warp];
+#pragma unroll
+        for (int q = 0; q < kFoldILP; ++q) {
+          if ((b0[q] >> lane) & 1u) {
+            const uint64_t pos = wb + __popc(b0[q] & lt);
+            if (pos < out.cap) {
+              st_key<KW>(out, pos, k0[q]);
+              ((AT*)out.amp)[pos] = o0[q];
+            }
+          }
+          if ((b1[q] >> lane) & 1u) {
+            const uint64_t pos = wb + __popc(b0[q]) + __popc(b1[q] & lt);
+            if (pos < out.cap) {
+              st_key<KW>(out, pos, k1[q]);
+              ((AT*)out.amp)[pos] = o1[q];
+            }
+          }
+          wb += __popc(b0[q]) + __popc(b1[q]);
+        }
+        __syncthreads();  // wtot and round_base are reused by the next round
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 constexpr int kProbThreads = 256;
 constexpr uint32_t kSmemBinsLog2 = 11;
 
@@ -852,7 +1053,8 @@ size_t pair_cluster_smem_bytes_t() {
 
 template <int KW, class AT>
 __global__ void __launch_bounds__(kPairCThreads)
-    k_pair_cluster(Ctl* ctl, Gate1 g, Arr bins, Arr out, int out_slot, uint32_t seq) {
+    k_pair_cluster(Ctl* ctl, Gate1 g, Arr bins, Arr out, int out_slot, uint32_t seq,
+                   uint32_t wait_limit, int32_t skip_copy_rank) {
   typedef typename KT<KW>::T K;
   extern __shared__ __align__(128) unsigned char smem_pc[];
   uint64_t* bar = (uint64_t*)smem_pc;
@@ -869,7 +1071,7 @@ __global__ void __launch_bounds__(kPairCThreads)
   const bool dead = ctl->err != 0u;
   const uint32_t n_bin = dead ? 0u : bins.seg_cnt[b];
   const uint32_t lo = r * kSliceCap;
-  const uint32_t n = n_bin > lo ? (n_bin - lo < (uint32_t)kSliceCap ? n_bin - lo : kSliceCap) : 0u;
+  uint32_t n = n_bin > lo ? (n_bin - lo < (uint32_t)kSliceCap ? n_bin - lo : kSliceCap) : 0u;
   const uint64_t src = ((uint64_t)b << bins.seg_log2) + lo;
   if (threadIdx.x == 0) {
     meta[0] = meta[1] = meta[2] = 0u;
@@ -883,7 +1085,8 @@ __global__ void __launch_bounds__(kPairCThreads)
   // Slice r of the bin -> shared memory (both arrays start 16-byte aligned:
   // slices begin at multiples of 4096 branches; sizes round up to 16 bytes
   // inside the bin's capacity).
-  if (threadIdx.x == 0 && n > 0) {
+  const uint32_t limit = wait_limit ? wait_limit : kWaitLimit;
+  if (threadIdx.x == 0 && n > 0 && (int32_t)r != skip_copy_rank) {
     const uint32_t kb = (uint32_t)(((size_t)n * 8 + 15) & ~(size_t)15);
     const uint32_t ab = (uint32_t)(((size_t)n * sizeof(AT) + 15) & ~(size_t)15);
     const uint32_t total = kb * (KW == 2 ? 2u : 1u) + ab;
@@ -901,18 +1104,22 @@ __global__ void __launch_bounds__(kPairCThreads)
   }
   if (n > 0) {
     uint32_t it = 0;
-    while (!mbar_try_wait(bar, 0) && ++it < kWaitLimit) {
+    while (!mbar_try_wait(bar, 0) && ++it < limit) {
     }
-    if (it >= kWaitLimit && threadIdx.x == 0) {
+    if (it >= limit && threadIdx.x == 0) {
       raise_err(ctl, kErrProbe, seq, 0);
       atomicOr(&meta[2], 1u);
       // Let the copies land before the CTA leaves (bounded again).
       uint32_t it2 = 0;
-      while (!mbar_try_wait(bar, 0) && ++it2 < kWaitLimit) {
+      while (!mbar_try_wait(bar, 0) && ++it2 < limit) {
       }
     }
   }
   __syncthreads();
+  // A slice whose copies did not arrive in time takes no part: the CTA still
+  // reaches every cluster barrier, with nothing to insert or emit (its keys
+  // and amplitudes in shared memory are not valid).
+  if (meta[2]) n = 0u;
   if (KW == 2 && n > 0) {
     // skey holds low words [0, n) and high words at byte offset 8 * kSliceCap:
     // rebuild 128-bit keys in place from the top down (each slot i reads
@@ -1151,6 +1358,31 @@ cudaError_t launch_expand(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in,
   return cudaGetLastError();
 }
 
+template <int KW, class AT>
+static cudaError_t fold_t(const Launch& L, Ctl* ctl, Arr in, int in_slot, uint64_t n_chunks,
+                          const OpList& ops, const Gate1& g, Arr out, int out_slot) {
+  const size_t smem = fold_smem_bytes<KW, AT>();
+  static std::atomic<unsigned long long> configured{0};
+  cudaError_t e = ensure_smem_optin((const void*)k_fold<KW, AT>, smem, configured);
+  if (e != cudaSuccess) return e;
+  uint64_t grid = n_chunks < 1 ? 1 : n_chunks;
+  if (grid > (uint64_t)L.sm_count * 12) grid = (uint64_t)L.sm_count * 12;
+  k_fold<KW, AT><<<(int)grid, kStreamThreads, smem, L.stream>>>(ctl, in, in_slot, n_chunks, out,
+                                                                out_slot, ops, g, L.seq);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
+                        uint64_t n_chunks, const OpList& ops, const Gate1& g, Arr out,
+                        int out_slot) {
+  if (g.fold_sign == 0 || g.cmask[0] != 0 || g.cmask[1] != 0) return cudaErrorInvalidValue;
+  if (kw == 1)
+    return amp32 ? fold_t<1, float2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot)
+                 : fold_t<1, double2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot);
+  return amp32 ? fold_t<2, float2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot)
+               : fold_t<2, double2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot);
+}
+
 cudaError_t launch_partition(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
                              const OpList& ops, const Gate1& g, Arr bk) {
   const int grid = stream_grid(L, kStreamThreads);
@@ -1178,15 +1410,9 @@ static cudaError_t pair_t(const Launch& L, Ctl* ctl, const Gate1& g, Arr bk, Arr
                           int out_slot) {
   const size_t smem = pair_smem_bytes(KW, sizeof(AT) == 8);
   // The opt-in to more than 48 KB of dynamic shared memory is per device.
-  static unsigned long long configured = 0;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && !(configured & (1ull << dev))) {
-    cudaError_t e = cudaFuncSetAttribute(k_pair<KW, AT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured |= 1ull << dev;
-  }
+  static std::atomic<unsigned long long> configured{0};
+  cudaError_t e = ensure_smem_optin((const void*)k_pair<KW, AT>, smem, configured);
+  if (e != cudaSuccess) return e;
   k_pair<KW, AT><<<bk.n_seg, kPairThreads, smem, L.stream>>>(ctl, g, bk, out, out_slot, L.seq);
   return cudaGetLastError();
 }
@@ -1254,15 +1480,9 @@ template <int KW, class AT>
 static cudaError_t bin_t(const Launch& L, Ctl* ctl, Arr in, int in_slot, const OpList& ops,
                          const Gate1& g, Arr bins) {
   const size_t smem = sizeof(BinSmem<KW, AT>);
-  static unsigned long long configured = 0;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && !(configured & (1ull << dev))) {
-    cudaError_t e = cudaFuncSetAttribute(k_bin<KW, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured |= 1ull << dev;
-  }
+  static std::atomic<unsigned long long> configured{0};
+  cudaError_t e = ensure_smem_optin((const void*)k_bin<KW, AT>, smem, configured);
+  if (e != cudaSuccess) return e;
   uint64_t tiles = (L.n_hint + kBinTile - 1) / kBinTile;
   if (tiles < 1) tiles = 1;
   const uint64_t cap = (uint64_t)L.sm_count * 2;
@@ -1285,15 +1505,9 @@ template <int KW, class AT>
 static cudaError_t pair_cluster_t(const Launch& L, Ctl* ctl, const Gate1& g, Arr bins, Arr out,
                                   int out_slot) {
   const size_t smem = pair_cluster_smem_bytes_t<KW, AT>();
-  static unsigned long long configured = 0;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && !(configured & (1ull << dev))) {
-    cudaError_t e = cudaFuncSetAttribute(k_pair_cluster<KW, AT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured |= 1ull << dev;
-  }
+  static std::atomic<unsigned long long> configured{0};
+  cudaError_t e = ensure_smem_optin((const void*)k_pair_cluster<KW, AT>, smem, configured);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(bins.n_seg * kClusterCtas);
   cfg.blockDim = dim3(kPairCThreads);
@@ -1306,7 +1520,8 @@ static cudaError_t pair_cluster_t(const Launch& L, Ctl* ctl, const Gate1& g, Arr
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_pair_cluster<KW, AT>, ctl, g, bins, out, out_slot, L.seq);
+  return cudaLaunchKernelEx(&cfg, k_pair_cluster<KW, AT>, ctl, g, bins, out, out_slot, L.seq,
+                            L.wait_limit, L.skip_copy_rank);
 }
 
 cudaError_t launch_pair_cluster(const Launch& L, int kw, bool amp32, Ctl* ctl, const Gate1& g,

@@ -57,10 +57,17 @@ sqs_status say(sqs_status s, const char* msg) {
   return s;
 }
 
-// Clears the control block and the bucket counters, then records the input
-// count: every call starts from zero state whatever the previous call left.
-__global__ void k_noalloc_begin(Ctl* ctl, unsigned int* bucket_cnt, uint32_t B, uint64_t n_in) {
-  for (uint32_t i = threadIdx.x; i < B; i += blockDim.x) bucket_cnt[i] = 0u;
+// Clears the control block, the bucket counters and the output-segment
+// counters, then records the input count: every call starts from zero state
+// whatever the previous call left.  A merge that stops on a device-side error
+// leaves some output segments unwritten; their counters must read zero then,
+// not the previous call's counts, or the final copy would run past out_cap.
+__global__ void k_noalloc_begin(Ctl* ctl, unsigned int* bucket_cnt, unsigned int* seg_cnt,
+                                uint32_t B, uint64_t n_in) {
+  for (uint32_t i = threadIdx.x; i < B; i += blockDim.x) {
+    bucket_cnt[i] = 0u;
+    seg_cnt[i] = 0u;
+  }
   if (threadIdx.x == 0) {
     unsigned long long* w = (unsigned long long*)ctl;
     for (size_t i = 0; i < sizeof(Ctl) / sizeof(unsigned long long); ++i) w[i] = 0ull;
@@ -69,16 +76,22 @@ __global__ void k_noalloc_begin(Ctl* ctl, unsigned int* bucket_cnt, uint32_t B, 
 }
 
 // Exclusive offsets of the output segments and the total count, written to
-// the caller's counter (all-ones when the merge flagged an error).
-__global__ void k_noalloc_offsets(const Ctl* ctl, const unsigned int* seg_cnt, uint32_t B,
-                                  unsigned long long* offsets, unsigned long long* n_out) {
+// the caller's counter (all-ones when the merge flagged an error).  After an
+// error every segment count is zeroed, so the final copy writes nothing into
+// the caller's output arrays.
+__global__ void k_noalloc_offsets(const Ctl* ctl, unsigned int* seg_cnt, uint32_t B,
+                                  uint64_t out_cap, unsigned long long* offsets,
+                                  unsigned long long* n_out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   unsigned long long run = 0;
   for (uint32_t s = 0; s < B; ++s) {
     offsets[s] = run;
     run += seg_cnt[s];
   }
-  *n_out = ctl->err ? ~0ull : run;
+  const bool bad = ctl->err != 0u || run > out_cap;
+  if (bad)
+    for (uint32_t s = 0; s < B; ++s) seg_cnt[s] = 0u;
+  *n_out = bad ? ~0ull : run;
 }
 
 }  // namespace
@@ -129,6 +142,7 @@ extern "C" sqs_status sqs_apply_u1q_noalloc(const uint32_t* reg_widths, uint32_t
       return say(SQS_ERR_ARG, "non-finite matrix entry");
     g.u[i] = m[i];
     g.uf[i] = (float)m[i];
+    g.ufl[i] = (float)(m[i] - (double)g.uf[i]);
   }
   g.t = t;
   g.mode = (m[1] == 0.0 && m[3] == 0.0 && m[5] == 0.0 && m[7] == 0.0) ? 2u : 0u;
@@ -136,6 +150,7 @@ extern "C" sqs_status sqs_apply_u1q_noalloc(const uint32_t* reg_widths, uint32_t
   g.eps = eps;
   g.eps2 = eps * eps;
   g.epsf = (float)eps;
+  g.rho32 = 0x1p-19f;  // unused: FP64 amplitudes
 
   // ---- set-up: the array's device address, once per device ----
   int dev = 0;
@@ -200,12 +215,12 @@ extern "C" sqs_status sqs_apply_u1q_noalloc(const uint32_t* reg_widths, uint32_t
   L.n_hint = n_in;
 
   // ---- the merge: clear, partition, pair, offsets, dense copy ----
-  k_noalloc_begin<<<1, 256, 0, s>>>(ctl, bk.seg_cnt, B, n_in);
+  k_noalloc_begin<<<1, 256, 0, s>>>(ctl, bk.seg_cnt, seg.seg_cnt, B, n_in);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = sqs::launch_partition(L, kw, false, ctl, in, 0, kNoOps, g, bk);
   if (e == cudaSuccess) e = sqs::launch_pair(L, kw, false, ctl, g, bk, seg, 1);
   if (e == cudaSuccess) {
-    k_noalloc_offsets<<<1, 32, 0, s>>>(ctl, seg.seg_cnt, B, offsets,
+    k_noalloc_offsets<<<1, 32, 0, s>>>(ctl, seg.seg_cnt, B, out_cap, offsets,
                                        (unsigned long long*)n_out);
     e = cudaGetLastError();
   }

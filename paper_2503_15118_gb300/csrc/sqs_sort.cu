@@ -397,15 +397,9 @@ cudaError_t pass_t(const Launch& L, Ctl* ctl, Arr in, const unsigned long long* 
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = scatter_smem<KW, AT>();
-  static unsigned long long configured = 0;  // opt-in above 48 KB, per device
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && !(configured & (1ull << dev))) {
-    e = cudaFuncSetAttribute(k_rsort_scatter<KW, AT, FIRST>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured |= 1ull << dev;
-  }
+  static std::atomic<unsigned long long> configured{0};  // opt-in above 48 KB, per device
+  e = ensure_smem_optin((const void*)k_rsort_scatter<KW, AT, FIRST>, smem, configured);
+  if (e != cudaSuccess) return e;
   const int sgrid = (int)std::min<uint64_t>(n_tiles, (uint64_t)L.sm_count * 4);
   k_rsort_scatter<KW, AT, FIRST><<<sgrid, kSortThreads, smem, L.stream>>>(
       ctl, in, n_ptr, per_seg, ops, t, shift, n_tiles, hist, out, cm0, cm1);

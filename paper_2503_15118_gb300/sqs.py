@@ -105,6 +105,9 @@ SIGNATURES = {
     "sqs_prune": (_S, [_P, _dbl, _UP]),
     "sqs_probabilities": (_S, [_P, _u32, _DP, _DP]),
     "sqs_probabilities_device": (_S, [_P, _u32, _P, _P]),
+    "sqs_probabilities_sparse": (_S, [_P, _u32, _UP, _DP, _u64, _UP, _DP]),
+    "sqs_state_set_wait_test": (_S, [_P, _u32, ctypes.c_int32]),
+    "sqs_set_fp32_cancel": (_S, [_P, ctypes.c_double]),
     "sqs_nnz": (_S, [_P, _UP]),
     "sqs_peak_nnz": (_S, [_P, _UP]),
     "sqs_export": (_S, [_P, _UP, _DP, _u64, _UP]),
@@ -239,6 +242,9 @@ class State:
     # --- operations -------------------------------------------------------
     def reset(self):
         self._chk(self.lib.sqs_state_reset(self.h))
+
+    def set_fp32_cancel(self, rho):
+        self._chk(self.lib.sqs_set_fp32_cancel(self.h, float(rho)))
 
     def set_prune_eps(self, eps):
         self._chk(self.lib.sqs_set_prune_eps(self.h, float(eps)))
@@ -384,8 +390,26 @@ class State:
         self._chk(self.lib.sqs_probabilities_device(self.h, reg, ctypes.c_void_p(probs_ptr),
                                                     ctypes.c_void_p(norm_ptr)))
 
+    def probabilities_sparse(self, reg):
+        """(values, probs, norm2): the distinct values of register ``reg``
+        ascending and the summed |a|^2 of each (sqs_probabilities_sparse)."""
+        cnt = ctypes.c_uint64()
+        n2 = ctypes.c_double()
+        st = self.lib.sqs_probabilities_sparse(self.h, reg, None, None, 0, ctypes.byref(cnt),
+                                               ctypes.byref(n2))
+        if st not in (OK, ERR_ARG):
+            self._chk(st)
+        c = int(cnt.value)
+        vals = np.zeros(max(c, 1), np.uint64)
+        probs = np.zeros(max(c, 1), np.float64)
+        self._chk(self.lib.sqs_probabilities_sparse(self.h, reg, vals.ctypes.data_as(_UP),
+                                                    probs.ctypes.data_as(_DP), c,
+                                                    ctypes.byref(cnt), ctypes.byref(n2)))
+        c = int(cnt.value)
+        return vals[:c], probs[:c], float(n2.value)
+
     def export(self):
-        """(lo, hi, amps): key words and complex128 amplitudes, storage order."""
+        """(lo, hi, amps): key words and complex128 amplitudes, ascending keys."""
         n = ctypes.c_uint64()
         st = self.lib.sqs_export(self.h, None, None, 0, ctypes.byref(n))
         if st not in (OK, ERR_ARG):

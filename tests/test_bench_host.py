@@ -120,3 +120,33 @@ def test_interference_classification():
     assert not bench._interference(("u1q", 0, 0, [[0, 1], [1, 0]], ()))  # anti-diagonal
     assert not bench._interference(("phase", (), 0.3))
     assert bench._interference(("u1q", 0, 0, [[0.6, 0.8], [0.8, -0.6]], ()))
+
+
+def test_fp32_error_report():
+    """The FP32-against-FP64 report: equal key sets in different orders
+    give the fidelity and largest difference of the matched amplitudes;
+    differing key sets report the keys only one side holds."""
+    import numpy as np
+    rng = np.random.default_rng(3)
+    n = 1000
+    lo = rng.choice(1 << 40, size=n, replace=False).astype(np.uint64)
+    hi = rng.integers(0, 4, size=n).astype(np.uint64)
+    a = (rng.normal(size=n) + 1j * rng.normal(size=n)) / np.sqrt(2 * n)
+    perm = rng.permutation(n)
+    b = a.copy()
+    b[5] += 1e-7
+    r = bench.fp32_error((lo, hi, a), (lo[perm], hi[perm], b[perm]))
+    assert r["keys_equal"] and r["n_f64"] == r["n_f32"] == n
+    assert abs(r["max_abs_diff"] - 1e-7) < 1e-12
+    ov = np.vdot(a, b)
+    want = abs(ov) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
+    assert abs(r["fidelity_vs_f64"] - want) < 1e-12
+    # Drop one key from the FP32 side and add one it alone holds.
+    keep = np.arange(n) != 7
+    lo2 = np.concatenate([lo[keep], np.array([1 << 41], np.uint64)])
+    hi2 = np.concatenate([hi[keep], np.array([0], np.uint64)])
+    b2 = np.concatenate([a[keep], np.array([0.5j])])
+    r = bench.fp32_error((lo, hi, a), (lo2, hi2, b2))
+    assert not r["keys_equal"] and r["only_f64"] == 1 and r["only_f32"] == 1
+    assert abs(r["only_max_abs"] - max(abs(a[7]), 0.5)) < 1e-15
+    assert r["max_abs_diff"] == 0.0

@@ -87,10 +87,75 @@ def test_config3_full_closed_form(sqs):
             assert st.nnz() == 2 ** 20
     assert st.peak_nnz() == 2 ** 24
     lo, hi, a = st.export()
-    key = (hi.astype(object) << 64) | lo.astype(object)
-    addr = np.array([int(k) & (2 ** 20 - 1) for k in key[:4096]])
-    data = np.array([(int(k) >> 20) & (2 ** 32 - 1) for k in key[:4096]])
-    acc = np.array([(int(k) >> 52) & (2 ** 32 - 1) for k in key[:4096]])
+    assert lo.shape[0] == 2 ** 20
+    # Every key: addr in bits 0..19, data in bits 20..51, acc in bits 52..83.
+    addr = lo & np.uint64(2 ** 20 - 1)
+    data = (lo >> np.uint64(20)) & np.uint64(2 ** 32 - 1)
+    acc = ((lo >> np.uint64(52)) | (hi << np.uint64(12))) & np.uint64(2 ** 32 - 1)
+    assert np.all(hi >> np.uint64(20) == 0)
+    assert np.array_equal(np.sort(addr), np.arange(2 ** 20, dtype=np.uint64))
     assert np.all(data == 0)
-    assert np.all(acc == (50 * table[addr]) % 2 ** 32)
+    assert np.array_equal(acc, (np.uint64(50) * table[addr]) % np.uint64(2 ** 32))
     assert np.max(np.abs(a - 2.0 ** -10)) < 1e-12
+    # Sparse marginals of the 32-bit accumulator: value 50 d_i mod 2^32 with
+    # probability 2^-20 per address holding it.
+    want_v, want_c = np.unique((np.uint64(50) * table) % np.uint64(2 ** 32), return_counts=True)
+    v, p, n2 = st.probabilities_sparse(2)
+    assert np.array_equal(v, want_v)
+    assert np.max(np.abs(p - want_c * 2.0 ** -20)) < 1e-15
+    assert abs(n2 - 1.0) < 1e-12
+    v, p, _ = st.probabilities_sparse(1)  # the data register is 0 everywhere
+    assert list(v) == [0] and abs(p[0] - 1.0) < 1e-12
+
+
+def _golden_config2():
+    import hashlib
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config2_seed2.npz")
+    gold = np.load(path)
+    circ = W.config2(seed=2)
+    digest = hashlib.sha256(repr(circ["gates"]).encode()).hexdigest()
+    assert str(gold["gates_digest"]) == digest, "the config-2 generator changed: rerun the script"
+    return circ, gold
+
+
+def _sorted_export(st):
+    lo, hi, a = st.export()
+    assert not hi.any()
+    order = np.argsort(lo)
+    return lo[order], a[order]
+
+
+@pytest.mark.parametrize("amp32", [False, True])
+def test_config2_full_size_against_oracle_golden(sqs, amp32):
+    """The benchmark circuit at full size, in bench.py's launch configuration
+    (capacity hint 2^25, a side stream), element by element against values
+    the CPU oracle wrote (tests/golden/make_config2_golden.py): 2^17 sampled
+    branches of the 2^23-branch state right after the first cancelling H (the
+    fold that takes the whole 2^24-branch state in), and the whole final
+    state.  FP64: keys bit-exact, amplitudes within 1e-12.  FP32 storage:
+    the same keys, amplitudes within 2e-6, fidelity >= 1 - 1e-6."""
+    import torch
+    circ, gold = _golden_config2()
+    atol = 2e-6 if amp32 else 1e-12
+    stream = torch.cuda.Stream()
+    st = sqs.State(circ["widths"], amp32=amp32, capacity_hint=1 << 25,
+                   stream=stream.cuda_stream, eps=circ["eps"])
+    after = int(gold["after"])
+    st.run(circ, upto=after)
+    lo, a = _sorted_export(st)
+    assert lo.shape[0] == int(gold["mid_n"])
+    pos = np.searchsorted(lo, gold["mid_lo"])
+    assert np.all(pos < lo.shape[0]) and np.array_equal(lo[pos], gold["mid_lo"])
+    assert np.max(np.abs(a[pos] - gold["mid_amp"])) < atol
+    for g in circ["gates"][after:]:
+        st.apply(g, circ["tables"])
+    lo, a = _sorted_export(st)
+    assert np.array_equal(lo, gold["final_lo"])
+    err = np.max(np.abs(a - gold["final_amp"]))
+    assert err < atol, err
+    ref = gold["final_amp"]
+    fid = abs(np.vdot(ref, a)) ** 2 / (np.vdot(ref, ref).real * np.vdot(a, a).real)
+    assert fid >= (1 - 1e-6 if amp32 else 1 - 1e-10)
+    assert st.peak_nnz() == int(gold["peak"])
+    st.close()

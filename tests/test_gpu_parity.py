@@ -2,9 +2,12 @@
 
 FP64 storage: keys bit-exact except branches whose |a| lies within 1e-12 of
 the pruning threshold, amplitudes within 1e-12 absolute, fidelity >= 1-1e-10.
-FP32 storage (FP64 arithmetic): fidelity >= 1-1e-6 and amplitudes within
-2e-6 absolute (a float keeps 24 bits: |a| <= 1 rounds to within 6e-8 per
-stored value, and a step re-rounds once).
+FP32 storage (every child of an interference step evaluated with
+compensated FP32 arithmetic, as accurate as an FP64 sum rounded once to FP32;
+a component below 2^-21 of its terms' size is a storage-precision cancellation
+and set to zero): fidelity >= 1-1e-6 and amplitudes within 2e-6 absolute (a
+float keeps 24 bits: |a| <= 1 rounds to within 6e-8 per stored value, and a
+step re-rounds once).
 """
 import math
 
@@ -132,6 +135,96 @@ def test_single_gate_128bit_keys(sqs, n, gi, amp32, merge):
     gs.apply(g)
     os_.apply(g)
     _check(gs, os_, amp32=amp32)
+
+
+RHO32 = 2.0 ** -19  # default storage-precision cancellation threshold of FP32 states
+
+
+def _fp32_children_expected(lo, amps, bit, m):
+    """For each output key of a single-qubit step: the FP64 value of every
+    component and the size sum_i |u_i a_i| of its terms (the scale of the
+    cancellation rule), from FP32-representable inputs."""
+    m = np.asarray(m, np.complex128).reshape(2, 2)
+    amp = dict(zip(lo.tolist(), amps.tolist()))
+    b = 1 << bit
+    out = {}
+    for k in amp:
+        base = k & ~b
+        a0, a1 = amp.get(base, 0j), amp.get(base | b, 0j)
+        for r in (0, 1):
+            v = m[r, 0] * a0 + m[r, 1] * a1
+            terms = (m[r, 0].real * a0.real, m[r, 0].imag * a0.imag, m[r, 1].real * a1.real,
+                     m[r, 1].imag * a1.imag)
+            sx = sum(abs(t) for t in terms)
+            terms = (m[r, 0].real * a0.imag, m[r, 0].imag * a0.real, m[r, 1].real * a1.imag,
+                     m[r, 1].imag * a1.real)
+            sy = sum(abs(t) for t in terms)
+            out[base | (b if r else 0)] = (v, sx, sy)
+    return out
+
+
+@pytest.mark.parametrize("merge", ["bucket", "sort"])
+@pytest.mark.parametrize("gate", ["h", "ry", "u1q"])
+def test_fp32_children_compensated(sqs, gate, merge):
+    """FP32 storage: each component of each child is the FP64 value of the
+    step on the stored FP32 inputs, rounded once (within one FP32 ulp, plus
+    2^-40 of its terms' size for the float-float coefficients), or exactly
+    zero when it lies within 2^-21 of its terms' size."""
+    widths = [16, 16, 16, 16]
+    bit = 16 + 6
+    ms = {"h": np.array([[1, 1], [1, -1]]) / np.sqrt(2),
+          "ry": np.array([[np.cos(0.35), -np.sin(0.35)], [np.sin(0.35), np.cos(0.35)]]),
+          "u1q": np.array([[0.6, -0.8j], [0.8, 0.6j]])}
+    m = ms[gate]
+    lo, hi, amps = W.random_state(widths, 2049, seed=55, pair_fraction=0.5, target=(1, 6))
+    amps = amps.astype(np.complex64).astype(np.complex128)
+    st = sqs.State(widths, amp32=True, eps=1e-14, merge=MERGES[merge])
+    st.import_(lo, hi, amps)
+    st.u1q(1, 6, m)
+    got = st.to_dict()
+    want = _fp32_children_expected(lo, amps, bit, m)
+    ulp = 2.0 ** -23
+    n_flushed = 0
+    for k, (v, sx, sy) in want.items():
+        g = got.get(k, 0j)
+        for gv, wv, size in ((g.real, v.real, sx), (g.imag, v.imag, sy)):
+            if gv == 0.0 and abs(wv) <= RHO32 * size * (1 + 1e-6):
+                n_flushed += wv != 0.0
+                continue
+            assert abs(gv - wv) <= ulp * abs(wv) + 2.0 ** -40 * size, (k, gv, wv, size)
+    assert set(got) <= set(want)
+
+
+@pytest.mark.parametrize("rho_log2,k,kept", [(-19, 15, True), (-19, 16, True), (-19, 17, True),
+                                               (-19, 19, False), (-19, 21, False),
+                                               (-21, 19, True), (-21, 21, False), (None, 24, True)])
+def test_fp32_cancellation_threshold(sqs, rho_log2, k, kept):
+    """H on |0> (amplitude 1) and |1> (amplitude -(1 - 2^-k)): the bit-0 child
+    is exactly 2^-k / sqrt(2), from terms of size about sqrt(2), so it lies
+    at 2^-(k+1) of its terms' size.  FP32 storage keeps it, accurate to one
+    ulp, above the cancellation threshold rho (default 2^-19; 2^-21 set by
+    sqs_set_fp32_cancel; the rule off with rho = 0) and sets it to zero below
+    (within the rounding the stored inputs carry).  FP64 storage keeps it
+    always (eps = 1e-14)."""
+    H = np.array([[1, 1], [1, -1]]) / np.sqrt(2)
+    a1 = -(1.0 - 2.0 ** -k)
+    true0 = 2.0 ** -k / np.sqrt(2)
+    for amp32 in (True, False):
+        st = sqs.State([8], amp32=amp32, eps=1e-14)
+        if rho_log2 is not None:
+            st.set_fp32_cancel(2.0 ** rho_log2)
+        else:
+            st.set_fp32_cancel(0.0)
+        st.import_(np.array([0, 1], np.uint64), np.zeros(2, np.uint64),
+                   np.array([1.0, a1], np.complex128))
+        st.u1q(0, 0, H)
+        d = st.to_dict()
+        assert abs(d[1] - (1.0 - a1) / np.sqrt(2)) < 1e-7
+        if amp32 and not kept:
+            assert 0 not in d
+        else:
+            assert abs(d[0].real - true0) <= 2.0 ** -23 * true0 and d[0].imag == 0.0
+        st.close()
 
 
 def test_qram_load_unload(sqs):
@@ -439,6 +532,44 @@ def test_fold_takes_config2_cancellations(sqs):
     o = oracle.run_circuit(circ)
     assert fast.nnz() == o.nnz() == 2 ** 10
     assert compare_states(df, o.to_dict()) >= 1 - 1e-12
+
+
+@pytest.mark.parametrize("wide", [False, True])
+@pytest.mark.parametrize("amp32", [False, True])
+@pytest.mark.parametrize("segmented", [False, True])
+def test_uncontrolled_fold_over_many_chunks(sqs, wide, amp32, segmented):
+    """The uncontrolled copy-pair fold (k_fold: bit-1 members skipped, bit-0
+    members compacted) on a ragged state of about 10^5 branches spanning many
+    4096-slot chunks, on a dense input (after an expansion) and a segmented
+    one (after a bucket merge), one- and two-word keys: bit for bit the state
+    of the plain merge, and equal to the oracle."""
+    widths = [16, 8, 40] + ([40] if wide else [])
+    rng = np.random.default_rng(77)
+    table = rng.integers(0, 256, size=1 << 16).astype(np.uint8)
+    gates = [("h", 0, b, ()) for b in range(15)]
+    gates += [("qload", 0, 1, 0),
+              ("h", 2, 0, ((1, 0, 1),)),          # expands about half: ragged count
+              ("h", 0, 15, ())]                   # constant bit: +1 copy pairs on bit 15
+    gates += [("x", 2, 5, ()), ("x", 2, 7, ((1, 2, 1),)), ("add", 2, -1, 12345, ()),
+              ("phase", ((1, 1, 1),), 0.3), ("ry", 2, 9, 0.7, ())]
+    if segmented:
+        gates += [("h", 1, 3, ())]                # no partners: bucket merge, segmented out
+    gates += [("x", 2, 11, ((0, 2, 1),)), ("h", 0, 15, ())]   # the fold
+    circ = {"widths": widths, "eps": 1e-14, "tables": [table], "gates": gates}
+    fast, plain = _plain_and_fast(sqs, circ, amp32)
+    names = [r[0] for r in fast.trace_read()[0]]
+    assert names.count("k_fold") == 1
+    if segmented:
+        assert fast.stats()["steps_hash"] >= 1
+    df, dp = fast.to_dict(), plain.to_dict()
+    assert len(df) > 60000 and len(df) % 2048 != 0
+    assert set(df) == set(dp) and all(df[k] == dp[k] for k in df)
+    o = oracle.run_circuit(circ).to_dict()
+    if amp32:
+        assert compare_states(df, o, atol=ATOL32, band=ATOL32) >= 1 - 1e-6
+    else:
+        assert set(df) == set(o)
+        assert compare_states(df, o) >= 1 - 1e-12
 
 
 def test_config1_batch_sampled_instances(sqs):

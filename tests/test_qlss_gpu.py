@@ -183,3 +183,71 @@ def test_nonherm_full_size_steps_keep_norm(sqs):
     ov = sum(np.conj(v) * d32.get(k, 0) for k, v in d64.items())
     n32 = sum(abs(v) ** 2 for v in d32.values())
     assert abs(ov) ** 2 / (n2 * n32) >= 1 - 1e-6
+
+
+def _flag_error(state, cfg):
+    """Distance between the normalised flagged block of a walk state and
+    x/||x|| for x = A^-1 b (dense solve), after removing the global phase,
+    and the flagged block's probability."""
+    v = Q.solution_block(state, cfg)
+    x = np.linalg.solve(cfg["A"], cfg["b"])
+    x = x / np.linalg.norm(x)
+    pv = float(np.vdot(v, v).real)
+    vn = v / math.sqrt(pv)
+    ph = np.vdot(x, vn)
+    return float(np.linalg.norm(vn * np.conj(ph) / abs(ph) - x)), pv
+
+
+def test_full_length_walk_n16_matches_oracle(sqs):
+    """The whole walk (T = 2000 steps) at N = 16, element by element against
+    the oracle; the flagged block against the dense solve."""
+    cfg = Q.config4(seed=4, N=16, half_band=4, kappa=10.0, T=2000)
+    circ = Q.walk_circuit(cfg)
+    o = oracle.run_circuit(circ)
+    g = sqs.run_circuit(circ)
+    ref = o.to_dict()
+    got = g.to_dict()
+    assert compare_states(got, ref, eps=1e-14, atol=1e-12) >= 1 - 1e-10
+    assert g.peak_nnz() == o.peak()
+    err, p = _flag_error(got, cfg)
+    assert err <= 5 * cfg["kappa"] / cfg["T"] and p >= 0.5
+    g32 = sqs.run_circuit(circ, amp32=True)
+    assert compare_states(g32.to_dict(), ref, atol=1e-5, band=1e-5) >= 1 - 1e-6
+
+
+@pytest.mark.parametrize("kappa", [10.0, 50.0, 100.0])
+def test_full_length_walk_n1024(sqs, kappa):
+    """The specified walk: N = 1024, half-bandwidth 8, T = 2000, condition
+    number kappa, recorded at 10 schedule points.  FP64: the norm stays 1 at
+    every point; the final flagged block approaches x = A^-1 b within the
+    adiabatic error's shape, eps <= C kappa / T (Sec. III.C), C = 5.  FP32
+    storage: fidelity >= 1 - 1e-6 with the FP64 state at every point."""
+    cfg = Q.config4(seed=4, N=1024, half_band=8, kappa=kappa, T=2000)
+    tabs = cfg["tables"]
+    g64 = sqs.State(cfg["widths"], capacity_hint=1 << 23, eps=cfg["eps"])
+    g32 = sqs.State(cfg["widths"], capacity_hint=1 << 23, eps=cfg["eps"], amp32=True)
+    for g in (g64, g32):
+        for gate in cfg["prep"]:
+            g.apply(gate, tabs)
+    done = 0
+    for point in cfg["points"]:
+        for m in range(done, point):
+            gates = Q.walk_step(cfg, cfg["steps"][m])
+            for g in (g64, g32):
+                for gate in gates:
+                    g.apply(gate, tabs)
+        done = point
+        lo, hi, a64 = g64.export()
+        assert abs(np.sum(np.abs(a64) ** 2) - 1.0) < 1e-9
+        lo32, hi32, a32 = g32.export()
+        assert not hi.any() and not hi32.any()
+        _, i64, i32 = np.intersect1d(lo, lo32, assume_unique=True, return_indices=True)
+        ov = np.vdot(a64[i64], a32[i32])
+        fid = abs(ov) ** 2 / (np.sum(np.abs(a64) ** 2) * np.sum(np.abs(a32) ** 2))
+        assert fid >= 1 - 1e-6, (point, fid)
+    final = dict(zip(lo.tolist(), a64.tolist()))
+    err, p = _flag_error(final, cfg)
+    assert p >= 0.5
+    assert err <= 5 * kappa / cfg["T"], err
+    g64.close()
+    g32.close()

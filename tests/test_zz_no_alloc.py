@@ -99,3 +99,45 @@ def test_noalloc_rejects_oversized_input(env):
                                   None, ctypes.c_void_p(1), 1 << 20, ctypes.c_void_p(1), None)
     assert n == sqs.ERR_ARG
     assert "MAX_BRANCHES" in lib.sqs_noalloc_last_error().decode()
+
+
+def test_noalloc_overflow_writes_nothing_past_out_cap(env):
+    """A bucket overflow (here forced by repeated keys, which break the
+    distinct-keys contract) must report an all-ones count and leave the
+    caller's output untouched, even though the previous call left large
+    output-segment counts in the shared scratch."""
+    torch, sqs, lib = env
+    dev = torch.device("cuda")
+    widths = [16, 16, 16, 16]
+    # First call: 65536 unpaired branches, so every output segment is full.
+    lo, hi, amps = W.random_state(widths, 65536, seed=4242, pair_fraction=0.0, target=(2, 5))
+    _noalloc(torch, sqs, lib, widths, lo, hi, amps, 2, 5, H)
+    # Second call: 3073 copies of one key land in one bucket of 2048 slots.
+    n = 2 * 1536 + 1
+    cap = 2 * n
+    guard = 1 << 16
+    k_in = torch.full((n,), 12345, dtype=torch.int64, device=dev)
+    a_in = torch.full((2 * n,), 0.01, dtype=torch.float64, device=dev)
+    o_lo = torch.full((cap + guard,), -7, dtype=torch.int64, device=dev)
+    o_a = torch.full((2 * (cap + guard),), -7.0, dtype=torch.float64, device=dev)
+    n_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    w = (ctypes.c_uint32 * 4)(*widths)
+    flat = np.empty(8, np.float64)
+    flat[0::2], flat[1::2] = H.reshape(-1).real, H.reshape(-1).imag
+    st = lib.sqs_apply_u1q_noalloc(
+        w, 4, 2, 5, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, 0, 1e-14,
+        ctypes.c_void_p(k_in.data_ptr()), None, ctypes.c_void_p(a_in.data_ptr()), n,
+        ctypes.c_void_p(o_lo.data_ptr()), None, ctypes.c_void_p(o_a.data_ptr()), cap,
+        ctypes.c_void_p(n_out.data_ptr()),
+        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0, lib.sqs_noalloc_last_error().decode()
+    torch.cuda.synchronize()
+    assert int(n_out.item()) == -1  # all ones: the device-side check failed
+    assert bool((o_lo == -7).all()), "output keys written after an overflow"
+    assert bool((o_a == -7.0).all()), "output amplitudes written after an overflow"
+    # The scratch is usable again: a valid call right after gives the right result.
+    lo, hi, amps = W.random_state(widths, 3000, seed=4243, pair_fraction=0.5, target=(2, 5))
+    got = _noalloc(torch, sqs, lib, widths, lo, hi, amps, 2, 5, H)
+    ref = _reference(sqs, widths, lo, hi, amps, 2, 5, H)
+    assert set(got) == set(ref)
+    assert compare_states(got, ref, atol=1e-12) > 1 - 1e-10
