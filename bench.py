@@ -296,6 +296,43 @@ def per_gate(args):
                 rows.append({"gate": name, "n": n, "pair_fraction": pf, "n_out": n_out, "ms": ms,
                              "updates_per_s": n / (ms / 1e3), "gb_per_s": gbs,
                              "frac_hbm": gbs / hbm})
+    # The shortcut paths on states built by H on fresh qubits: an H on a
+    # fresh (constant) qubit expands every branch (k_expand); an H on a qubit
+    # expanded earlier and left untouched folds each pair from its bit-0
+    # member (k_fold), alone or after m fused CNOTs on other qubits.
+    for n_log2 in (20, 22, 24):
+        n = 1 << n_log2
+        prep = [("h", q // 16, q % 16, ()) for q in range(n_log2)]
+        cases = [("expand_h", [("h", 3, 15, ())], 2 * n),
+                 ("fold_h", [("h", 0, 0, ())], n // 2)]
+        for m in (4, 16):
+            ops = [("x", 2 + (j % 2), (j * 5) % 16, ((1 + (j % 3) // 2, (j * 7 + 3) % 16, 1),))
+                   for j in range(m)]
+            cases.append((f"fold_h_after_{m}_cnots", ops + [("h", 0, 0, ())], n // 2))
+        for name, gates, n_expect in cases:
+            times, n_out = [], 0
+            for rep in range(reps + 1):
+                st.reset()
+                for gt in prep:
+                    st.apply(gt)
+                st.sync()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for gt in gates:
+                    st.apply(gt)
+                st.flush()
+                b.record(stream)
+                torch.cuda.synchronize()
+                if rep:
+                    times.append(a.elapsed_time(b))
+                n_out = st.nnz()
+            ms = statistics.median(times)
+            byts = (n + n_out) * rb
+            gbs = byts / (ms / 1e3) / 1e9
+            rows.append({"gate": name, "n": n, "pair_fraction": None, "n_out": n_out,
+                         "n_out_expected": n_expect, "ms": ms,
+                         "updates_per_s": n / (ms / 1e3), "gb_per_s": gbs, "frac_hbm": gbs / hbm})
     st.close()
     print(json.dumps({"per_gate": rows, "unit": UNIT, "hbm_gbs": hbm, "reps": reps,
                       "timing": "CUDA events around one gate call and its flush, median"}),
@@ -595,6 +632,46 @@ def graph_workloads(stream, stored, cfg5, args):
     return out
 
 
+def _with_summary(line):
+    """The line with a "summary" of the variants right after "config"."""
+    v = line.get("variants", {})
+
+    def rate(key):
+        e = v.get(key, {})
+        return e.get("value") if isinstance(e, dict) else None
+
+    def frac(key):
+        e = v.get(key, {})
+        r = e.get("interference_roofline", {}) if isinstance(e, dict) else {}
+        return r.get("frac")
+
+    def fid(key):
+        e = v.get(key, {})
+        f = e.get("fp32_error", {}) if isinstance(e, dict) else {}
+        return f.get("fidelity_vs_f64")
+
+    summary = {
+        "config1_batch65536_f64_updates_per_s": rate("config1_batch65536_f64"),
+        "config1_batch65536_interference_frac": frac("config1_batch65536_f64"),
+        "config3_f64_updates_per_s": rate("config3_qram_a20_r50_f64"),
+        "config3_f32_updates_per_s": rate("config3_qram_a20_r50_f32"),
+        "config3_f32_fidelity_vs_f64": fid("config3_qram_a20_r50_f32"),
+        "walk_N1024_f64_updates_per_s": rate("qlss_walk_N1024_4steps_f64"),
+        "walk_N1024_f32_fidelity_vs_f64": fid("qlss_walk_N1024_4steps_f32"),
+        "batch256_f64_updates_per_s": rate("qlss_batch256_2steps_f64"),
+        "config2_f32_vs_f64_ms": [v.get("f32_exact", {}).get("ms_per_step"),
+                                  v.get("f64_exact", {}).get("ms_per_step")],
+        "config2_f32_learned_vs_f64_exact_ms": [v.get("f32_learned", {}).get("ms_per_step"),
+                                                v.get("f64_exact", {}).get("ms_per_step")],
+    }
+    out = {}
+    for k, val in line.items():
+        out[k] = val
+        if k == "config":
+            out["summary"] = summary
+    return out
+
+
 def slowest_rank_ms(total_ms, dist, device):
     """The timed region's length on the slowest rank (all ranks call it)."""
     if not dist:
@@ -800,6 +877,11 @@ def main():
     e2e_s = statistics.median(e2e_times)
     d2h = 8 * (2 ** widths[PROB_REG]) + 8
 
+    # The headline steps are issued back to back: the host issues step i + 1
+    # while the device runs step i.  The same steps with a host sync after
+    # each (host issue exposed):
+    sync_ms = _timed_steps(st, step, flush, stream, args.steps)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -809,7 +891,11 @@ def main():
         "config": {"workload": WORKLOAD, "parallelism": f"replicas{world}",
                    "l2": "L2 flushed (512 MB write) between steps; peak state 402 MB",
                    "units_per_step": units, "peak_nnz": peak, "final_nnz": n_final,
-                   "gates": len(gates)},
+                   "gates": len(gates),
+                   "step_issue": "steps issued back to back without a host sync between "
+                                 "them (the host issues the next step while the device runs "
+                                 "this one); synchronised steps in sync_ms_per_step"},
+        "sync_ms_per_step": sync_ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "kernel": dom,
                      "launch": f"gate {big_call - 2} ({n_in[big_call - 2]} branches in)",
@@ -826,6 +912,9 @@ def main():
     if not args.no_variants:
         line["variants"] = variants(circ, widths, stream, probs, norm, flush, args, st)
         line["variants"].update(extra_workloads(stream, flush, args))
+        # The figures read most, placed early in the line (a reader that keeps
+        # only the tail of a long line still has the headline keys).
+        line = _with_summary(line)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, _ = cpu_baseline(circ)
         line["cpu_baseline"] = cb

@@ -116,6 +116,25 @@ typedef enum {
                                      steps fused, whatever its size and
                                      estimated cost (exercises the fused path
                                      on small states)                        */
+#define SQS_AUTOTUNE 512u         /* measure and pick, per (GPU, operation kind,
+                                     key words, amplitude type, log2 of the
+                                     branch count, bits to sort or run length):
+                                     the radix digit width of every sort (6, 8,
+                                     10 or 11 bits) and the tile size of fused
+                                     runs.  Each candidate is timed twice with
+                                     CUDA events on real steps (results do not
+                                     depend on the choice), then the fastest
+                                     median is kept.  Choices persist through
+                                     sqs_tune_export / sqs_tune_import, or the
+                                     file named by the environment variable
+                                     SQS_TUNE_CACHE (read when the state is
+                                     created, written when it is destroyed).
+                                     Without this flag: 8-bit digits and the
+                                     default tile rule.  The environment
+                                     variable SQS_SORT_BITS (6, 8, 10 or 11),
+                                     read when a state is created, forces one
+                                     digit width for every sort of the state
+                                     (tests, experiments).                    */
 
 /*
  * One control (or predicate) qubit: bit `bit` of register `reg` must equal
@@ -307,6 +326,19 @@ sqs_status sqs_nnz(sqs_state* st, uint64_t* out);
  * Table S1).  Waits. */
 sqs_status sqs_peak_nnz(sqs_state* st, uint64_t* out);
 
+/* Autotuner choices of the state (SQS_AUTOTUNE) as JSON text:
+ * {"gpu": "<device name>", "entries": [{"site": "sort_bits" | "group_slots",
+ * "kw": 1|2, "amp32": 0|1, "n_log2": L, "extra": E, "choice": V,
+ * "cand": [...], "median_ms": [...]}, ...]} -- one entry per measured key, V
+ * the value kept (-1 while still measuring).  Writes at most cap bytes
+ * (including the terminating zero) to buf and the full length to *len;
+ * SQS_ERR_ARG when it does not fit. */
+sqs_status sqs_tune_export(const sqs_state* st, char* buf, uint64_t cap, uint64_t* len);
+/* Loads choices from JSON text of the export's format; entries measured on a
+ * GPU of another name are ignored.  Loaded choices are used without new
+ * measurements when SQS_AUTOTUNE is set. */
+sqs_status sqs_tune_import(sqs_state* st, const char* json);
+
 /* Testing hook for the bounded device waits.  The cluster merge
  * (SQS_MERGE_CLUSTER) loads each CTA's slice of a bin with bulk copies that
  * complete on an mbarrier; every wait on it polls at most wait_limit times
@@ -370,7 +402,10 @@ uint64_t sqs_launch_count(const sqs_state* st);
 #define SQS_K_GROUP 14u     /* fused run: every group transformed in shared memory */
 typedef struct {
   uint32_t kernel; /* SQS_K_*                          */
-  uint32_t call;   /* API call index since enabling     */
+  uint32_t call;   /* API call index (numbered from the last reset) that
+                      issued the launch's work: a held interference step,
+                      run when a later call closes its run, keeps its own
+                      call's index                                          */
   float ms;        /* device time between the events    */
   uint32_t pad;
 } sqs_trace_record;
@@ -477,6 +512,9 @@ typedef struct {
   uint64_t steps_fold;       /*   copy-pair fold                               */
   uint64_t runs_fused;       /* fused runs executed (SQS_FUSE_OFF unset)      */
   uint64_t steps_fused;      /*   interference steps inside them              */
+  uint64_t ops_deferred;     /* queued operations kept queued past a step that
+                                only merges (copy-pair target), applied later
+                                to the smaller state                          */
 } sqs_stats;
 sqs_status sqs_state_stats(const sqs_state* st, sqs_stats* out);
 

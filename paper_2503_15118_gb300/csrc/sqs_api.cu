@@ -13,9 +13,13 @@
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <map>
+#include <sstream>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -198,6 +202,27 @@ struct sqs_state {
   };
   std::map<uint32_t, Tune> tune;
 
+  // Autotuner (SQS_AUTOTUNE): per key, the candidates, their timed samples
+  // and the value kept; one measurement in flight per key.
+  struct TuneKey {
+    uint32_t site, kw, amp32, n_log2, extra;
+    bool operator<(const TuneKey& o) const {
+      return std::tie(site, kw, amp32, n_log2, extra) <
+             std::tie(o.site, o.kw, o.amp32, o.n_log2, o.extra);
+    }
+  };
+  struct TuneEntry {
+    std::vector<int> cand;
+    std::vector<std::vector<float>> ms;
+    int choice = -1;   // value kept (-1: still measuring)
+    int pending = -1;  // index of the candidate whose events are in flight
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+  };
+  std::map<TuneKey, TuneEntry> tuner;
+  std::string gpu_name;
+  int forced_sort_bits = 0;  // SQS_SORT_BITS: one digit width for every sort
+  uint32_t trace_call = 0;   // when set, the call launches are attributed to
+
   // Half-angle tables of register-valued rotations, per (scale, offset,
   // digits); kept for the state's lifetime (queued steps may point to them).
   struct AngTab {
@@ -351,7 +376,8 @@ struct Traced {
       return;
     }
     idx = (int)used;
-    st->trace.push_back(sqs_trace_record{kernel, st->call, 0.f, 0u});
+    st->trace.push_back(
+        sqs_trace_record{kernel, st->trace_call ? st->trace_call : st->call, 0.f, 0u});
     cudaEventRecord(st->ev[2 * idx], st->stream);
   }
   ~Traced() {
@@ -730,7 +756,7 @@ sqs_status run_hashed(sqs_state* st, const Gate1& g, double est_in, int64_t rec_
   {
     Traced tr(st, SQS_K_PARTITION);
     e = sqs::launch_partition(launch_of(st, in_slots), st->kw, st->amp32, st->ctl,
-                              st->cur.view(), st->cur_slot, L, g, st->bk.view());
+                              st->cur.view(), st->cur_slot, L, g, st->bk.view(), (uint32_t)target);
   }
   if (e != cudaSuccess) return cuda_fail(st, e, "partition launch");
   {
@@ -753,9 +779,9 @@ sqs_status run_hashed(sqs_state* st, const Gate1& g, double est_in, int64_t rec_
 // Digit windows of the radix-sort merge: start positions (in the pair-class
 // key, the key with bit t deleted) of 8-bit digits covering every bit not
 // known constant.  Known-constant bits order nothing and are skipped.
-std::vector<uint32_t> sort_shifts(const sqs_state* st, const Gate1& g) {
+std::vector<uint32_t> sort_shifts(const sqs_state* st, const Gate1& g,
+                                  uint32_t D = (uint32_t)sqs::sort_radix_bits()) {
   const uint32_t nb = st->total_bits;  // the class key has nb - 1 bits
-  const uint32_t D = (uint32_t)sqs::sort_radix_bits();
   auto varying = [&](uint32_t q) {  // bit q of the class key
     const uint32_t kb = q < g.t ? q : q + 1;
     return ((g.vary[kb >> 6] >> (kb & 63)) & 1ull) != 0ull;
@@ -776,8 +802,8 @@ std::vector<uint32_t> sort_shifts(const sqs_state* st, const Gate1& g) {
 // Scratch of the radix-sort passes: per-tile digit histograms, scan
 // partials and the device count.
 sqs_status sort_scratch(sqs_state* st, uint64_t tiles, unsigned int*& hist, unsigned int*& part,
-                        unsigned long long*& n_dev) {
-  const uint64_t radix = 1ull << sqs::sort_radix_bits();
+                        unsigned long long*& n_dev, int radix_bits) {
+  const uint64_t radix = 1ull << radix_bits;
   const size_t hist_bytes = (size_t)(radix * tiles * 4 + 255) & ~(size_t)255;
   const size_t part_bytes = (sqs::sort_part_entries() * 4 + 255) & ~(size_t)255;
   const size_t bytes = hist_bytes + part_bytes + 256;
@@ -791,6 +817,186 @@ sqs_status sort_scratch(sqs_state* st, uint64_t tiles, unsigned int*& hist, unsi
   part = (unsigned int*)(st->sort_buf + hist_bytes);
   n_dev = (unsigned long long*)(st->sort_buf + hist_bytes + part_bytes);
   return SQS_OK;
+}
+
+// ---- autotuner (SQS_AUTOTUNE) ---------------------------------------------------
+// Bits a sort orders: the positions in `keep` not known constant.
+uint32_t bits_to_sort(const sqs_state* st, const uint64_t keep[2]) {
+  uint32_t n = 0;
+  for (uint32_t q = 0; q < st->total_bits; ++q)
+    if (((keep[q >> 6] >> (q & 63)) & 1ull) && st->const_val[q] < 0) ++n;
+  return n;
+}
+
+constexpr uint32_t kTuneSortBits = 1;    // radix digit width of a sort
+constexpr uint32_t kTuneGroupSlots = 2;  // output slots per CTA tile of a fused run
+constexpr int kTuneSamples = 2;          // timed runs per candidate
+
+uint32_t log2_ceil(uint64_t v) {
+  uint32_t lg = 0;
+  while (lg < 63 && (1ull << lg) < v) ++lg;
+  return lg;
+}
+
+// Picks the value for `key` among `cand` (cand[0] is the default, used when
+// tuning is off).  While measuring, returns the candidate with the fewest
+// samples and sets `timed`: the caller brackets its launches with
+// tune_begin / tune_end.  A measurement still in flight is collected once its
+// end event has completed (never waiting for it).
+int tune_pick(sqs_state* st, const sqs_state::TuneKey& key, const std::vector<int>& cand,
+              bool& timed) {
+  timed = false;
+  if (!(st->flags & SQS_AUTOTUNE) || st->capturing) {
+    auto it = st->tuner.find(key);
+    return (it != st->tuner.end() && it->second.choice >= 0) ? it->second.choice : cand[0];
+  }
+  sqs_state::TuneEntry& E = st->tuner[key];
+  if (E.choice >= 0) return E.choice;
+  if (E.cand.empty()) {
+    E.cand = cand;
+    E.ms.assign(cand.size(), {});
+  }
+  if (E.pending >= 0) {
+    if (cudaEventQuery(E.ev[1]) != cudaSuccess) {
+      cudaGetLastError();
+      return E.cand[0];  // the last measurement is still running
+    }
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, E.ev[0], E.ev[1]) == cudaSuccess)
+      E.ms[E.pending].push_back(ms);
+    cudaGetLastError();
+    E.pending = -1;
+  }
+  size_t pick = 0;
+  for (size_t i = 1; i < E.cand.size(); ++i)
+    if (E.ms[i].size() < E.ms[pick].size()) pick = i;
+  if (E.ms[pick].size() >= (size_t)kTuneSamples) {
+    double best = 1e300;
+    for (size_t i = 0; i < E.cand.size(); ++i) {
+      std::vector<float> v = E.ms[i];
+      std::sort(v.begin(), v.end());
+      const double med = v[v.size() / 2];
+      if (med < best) {
+        best = med;
+        E.choice = E.cand[i];
+      }
+    }
+    return E.choice;
+  }
+  if (!E.ev[0] && (cudaEventCreate(&E.ev[0]) != cudaSuccess ||
+                   cudaEventCreate(&E.ev[1]) != cudaSuccess)) {
+    cudaGetLastError();
+    return E.cand[0];
+  }
+  E.pending = (int)pick;
+  timed = true;
+  return E.cand[pick];
+}
+void tune_begin(sqs_state* st, const sqs_state::TuneKey& key) {
+  cudaEventRecord(st->tuner[key].ev[0], st->stream);
+}
+void tune_end(sqs_state* st, const sqs_state::TuneKey& key) {
+  cudaEventRecord(st->tuner[key].ev[1], st->stream);
+}
+
+// Digit width of a sort over the kept, varying key bits (tuned per key
+// words, amplitude type, size and number of bits to sort).
+int pick_sort_bits(sqs_state* st, uint64_t n, uint32_t bits_to_sort, sqs_state::TuneKey& key,
+                   bool& timed) {
+  key = sqs_state::TuneKey{kTuneSortBits, (uint32_t)st->kw, st->amp32 ? 1u : 0u, log2_ceil(n),
+                           bits_to_sort};
+  if (st->forced_sort_bits) {
+    timed = false;
+    return st->forced_sort_bits;
+  }
+  return tune_pick(st, key, {sqs::sort_radix_bits(), 10, 11, 6}, timed);
+}
+
+std::string tune_json(const sqs_state* st) {
+  std::ostringstream o;
+  o << "{\"gpu\": \"" << st->gpu_name << "\", \"entries\": [";
+  bool first = true;
+  for (const auto& kv : st->tuner) {
+    const auto& k = kv.first;
+    const auto& E = kv.second;
+    if (E.cand.empty()) continue;
+    o << (first ? "" : ", ") << "{\"site\": \""
+      << (k.site == kTuneSortBits ? "sort_bits" : "group_slots") << "\", \"kw\": " << k.kw
+      << ", \"amp32\": " << k.amp32 << ", \"n_log2\": " << k.n_log2 << ", \"extra\": " << k.extra
+      << ", \"choice\": " << E.choice << ", \"cand\": [";
+    for (size_t i = 0; i < E.cand.size(); ++i) o << (i ? ", " : "") << E.cand[i];
+    o << "], \"median_ms\": [";
+    for (size_t i = 0; i < E.cand.size(); ++i) {
+      std::vector<float> v = E.ms[i];
+      std::sort(v.begin(), v.end());
+      o << (i ? ", " : "") << (v.empty() ? -1.0 : (double)v[v.size() / 2]);
+    }
+    o << "]}";
+    first = false;
+  }
+  o << "]}";
+  return o.str();
+}
+
+// Integer value of "name": in [p, end) of one entry.
+bool json_int(const char* p, const char* end, const char* name, long long& v) {
+  const std::string pat = std::string("\"") + name + "\":";
+  const char* q = std::search(p, end, pat.begin(), pat.end());
+  if (q == end) return false;
+  q += pat.size();
+  while (q < end && *q == ' ') ++q;
+  char* stop = nullptr;
+  v = std::strtoll(q, &stop, 10);
+  return stop != q;
+}
+
+// Loads entries measured on this GPU (the export's format).
+void tune_load(sqs_state* st, const char* json) {
+  const char* end = json + std::strlen(json);
+  const std::string gpat = "\"gpu\": \"";
+  const char* g = std::search(json, end, gpat.begin(), gpat.end());
+  if (g == end) return;
+  g += gpat.size();
+  const char* ge = std::find(g, end, '"');
+  if (std::string(g, ge) != st->gpu_name) return;
+  const std::string epat = "{\"site\": \"";
+  for (const char* p = std::search(ge, end, epat.begin(), epat.end()); p != end;) {
+    const char* q = p + epat.size();
+    const char* e = std::find(q, end, '}');
+    const char* next = std::search(e, end, epat.begin(), epat.end());
+    const std::string site(q, std::find(q, e, '"'));
+    long long kw, amp32, nl, extra, choice;
+    if (json_int(q, e, "kw", kw) && json_int(q, e, "amp32", amp32) &&
+        json_int(q, e, "n_log2", nl) && json_int(q, e, "extra", extra) &&
+        json_int(q, e, "choice", choice) && choice >= 0) {
+      const uint32_t s = site == "sort_bits" ? kTuneSortBits
+                         : site == "group_slots" ? kTuneGroupSlots : 0u;
+      if (s && (s != kTuneSortBits || sqs::sort_radix_bits_ok((int)choice))) {
+        sqs_state::TuneEntry& E = st->tuner[sqs_state::TuneKey{
+            s, (uint32_t)kw, (uint32_t)amp32, (uint32_t)nl, (uint32_t)extra}];
+        E.choice = (int)choice;
+        // The candidate list, kept for the export ("cand": [a, b, ...]).
+        E.cand.clear();
+        const std::string cpat = "\"cand\": [";
+        const char* c = std::search(q, e, cpat.begin(), cpat.end());
+        if (c != e) {
+          c += cpat.size();
+          const char* ce = std::find(c, e, ']');
+          while (c < ce) {
+            char* stop = nullptr;
+            const long v = std::strtol(c, &stop, 10);
+            if (stop == c) break;
+            E.cand.push_back((int)v);
+            c = stop;
+            while (c < ce && (*c == ',' || *c == ' ')) ++c;
+          }
+        }
+        if (E.cand.empty()) E.cand.push_back((int)choice);
+        E.ms.assign(E.cand.size(), {});
+      }
+    }
+    p = next;
+  }
 }
 
 // One interference step on the radix-sort merge: LSD passes ping-pong
@@ -809,7 +1015,12 @@ sqs_status run_sorted(sqs_state* st, const Gate1& g, int64_t rec_idx) {
       if (s != SQS_OK) return s;
     }
   }
-  const std::vector<uint32_t> shifts = sort_shifts(st, g);
+  uint64_t all_bits[2] = {~0ull, ~0ull};
+  all_bits[g.t >> 6] &= ~(1ull << (g.t & 63));
+  sqs_state::TuneKey tkey;
+  bool timed = false;
+  const int rb = pick_sort_bits(st, st->ub, bits_to_sort(st, all_bits), tkey, timed);
+  const std::vector<uint32_t> shifts = sort_shifts(st, g, (uint32_t)rb);
   const uint32_t npass = (uint32_t)shifts.size();
   const uint64_t tile = (uint64_t)sqs::sort_tile();
   const uint64_t in_slots = st->cur.slots(st->ub);
@@ -825,7 +1036,7 @@ sqs_status run_sorted(sqs_state* st, const Gate1& g, int64_t rec_idx) {
   unsigned int *hist, *part;
   unsigned long long* n_dev;
   {
-    sqs_status s = sort_scratch(st, std::max(tiles0, tilesN), hist, part, n_dev);
+    sqs_status s = sort_scratch(st, std::max(tiles0, tilesN), hist, part, n_dev, rb);
     if (s != SQS_OK) return s;
   }
   const uint32_t chunk_log2 = sqs::sort_merge_chunk_log2();
@@ -844,6 +1055,7 @@ sqs_status run_sorted(sqs_state* st, const Gate1& g, int64_t rec_idx) {
   const unsigned long long* n_ptr = &st->ctl->cnt[st->cur_slot];
   Arr src = st->cur.view();
   cudaError_t e = cudaSuccess;
+  if (timed) tune_begin(st, tkey);
   for (uint32_t p = 0; p < npass && e == cudaSuccess; ++p) {
     Store& dst = *buf[p & 1];
     dst.set_dense();
@@ -851,11 +1063,12 @@ sqs_status run_sorted(sqs_state* st, const Gate1& g, int64_t rec_idx) {
     e = sqs::launch_rsort_pass(launch_of(st, in_slots), st->kw, st->amp32, st->ctl, src, n_ptr,
                                p == 0 ? per_seg : 1u, p == 0 ? tiles0 : tilesN,
                                p == 0 ? &L : nullptr, g.t, shifts[p], hist, part, n_dev,
-                               dst.view());
+                               dst.view(), nullptr, rb);
     st->launches += 3;  // a pass is four kernels: histogram, two scan steps, scatter
     src = dst.view();
     n_ptr = n_dev;
   }
+  if (timed) tune_end(st, tkey);
   if (e != cudaSuccess) return cuda_fail(st, e, "sort pass launch");
   const int out_slot = (st->cur_slot + 1) & 3;
   st->alt.set_segments(chunk_log2 + 1, (uint32_t)nseg_out);
@@ -909,10 +1122,31 @@ int tuned_path(sqs_state* st, uint32_t key, bool& timed) {
   return T.us_per_slot[1] < T.us_per_slot[0] ? 1 : 0;
 }
 
+// Attributes the launches of a step to the API call that issued it while in
+// scope (a held step runs during a later call).
+struct TraceCall {
+  sqs_state* st;
+  uint32_t saved;
+  TraceCall(sqs_state* s, uint32_t call) : st(s), saved(s->trace_call) {
+    if (call) st->trace_call = call;
+  }
+  ~TraceCall() { st->trace_call = saved; }
+};
+
 sqs_status run_branching(sqs_state* st, const Gate1& g, double est_in = -1.0,
                          int64_t rec_idx = -1) {
-  sqs_status s = run_pending(st, true);  // leaves the fused tail in ops_buf
-  if (s != SQS_OK) return st->sticky = s;
+  TraceCall attribution(st, g.issue_call);
+  sqs_status s = SQS_OK;
+  if (g.defer_ops && st->run_gates.empty()) {
+    // The queued operations stay queued past this step (defer_ops_ok).
+    st->ops_buf.n = 0;
+    st->ops_buf.n_tab = 0;
+    st->ops_buf.touches_keys = st->ops_buf.touches_amps = st->ops_buf.drops = 0;
+    st->stats.ops_deferred += st->pending.size();
+  } else {
+    s = run_pending(st, true);  // leaves the fused tail in ops_buf
+    if (s != SQS_OK) return st->sticky = s;
+  }
   if (g.no_partners || g.fold_sign) {
     if (g.fold_sign) st->stats.steps_fold++;
     else st->stats.steps_expand++;
@@ -952,8 +1186,8 @@ sqs_status run_branching(sqs_state* st, const Gate1& g, double est_in = -1.0,
 // Digit windows of a fused run's sort: 8-bit windows over the key bits that
 // are neither targets of the run nor known constant (the sort key is the key
 // with the targets cleared; constant bits order nothing).
-std::vector<uint32_t> group_shifts(const sqs_state* st, const GroupRun& run) {
-  const uint32_t D = (uint32_t)sqs::sort_radix_bits();
+std::vector<uint32_t> group_shifts(const sqs_state* st, const GroupRun& run,
+                                   uint32_t D = (uint32_t)sqs::sort_radix_bits()) {
   std::vector<uint32_t> shifts;
   for (uint32_t q = 0; q < st->total_bits;) {
     const bool target = (run.tmask[q >> 6] >> (q & 63)) & 1ull;
@@ -975,6 +1209,7 @@ std::vector<uint32_t> group_shifts(const sqs_state* st, const GroupRun& run) {
 // most 2^k branches per group), then every group transformed at once.
 // Bit-identical to the k steps one by one.
 sqs_status run_group(sqs_state* st, const std::vector<Gate1>& gates) {
+  TraceCall attribution(st, gates.empty() ? 0u : gates[0].issue_call);
   sqs_status s = run_pending(st, true);  // leaves the fused operations in ops_buf
   if (s != SQS_OK) return st->sticky = s;
   const OpList& L = st->ops_buf;
@@ -989,7 +1224,11 @@ sqs_status run_group(sqs_state* st, const std::vector<Gate1>& gates) {
     s = sync_bound(st);  // tiles and buffers follow the bound: exact count first
     if (s != SQS_OK) return s;
   }
-  const std::vector<uint32_t> shifts = group_shifts(st, run);
+  uint64_t keep_bits[2] = {~run.tmask[0], ~run.tmask[1]};
+  sqs_state::TuneKey tkey;
+  bool timed = false;
+  const int rb = pick_sort_bits(st, st->ub, bits_to_sort(st, keep_bits), tkey, timed);
+  const std::vector<uint32_t> shifts = group_shifts(st, run, (uint32_t)rb);
   const uint32_t npass = (uint32_t)shifts.size();
   const uint64_t tile = (uint64_t)sqs::sort_tile();
   const uint64_t in_slots = st->cur.slots(st->ub);
@@ -1005,7 +1244,7 @@ sqs_status run_group(sqs_state* st, const std::vector<Gate1>& gates) {
   unsigned int *hist, *part;
   unsigned long long* n_dev;
   {
-    sqs_status s = sort_scratch(st, std::max(tiles0, tilesN), hist, part, n_dev);
+    sqs_status s = sort_scratch(st, std::max(tiles0, tilesN), hist, part, n_dev, rb);
     if (s != SQS_OK) return s;
   }
   const uint64_t need_in = std::max<uint64_t>(st->ub, 1);
@@ -1020,6 +1259,7 @@ sqs_status run_group(sqs_state* st, const std::vector<Gate1>& gates) {
   const unsigned long long* n_ptr = &st->ctl->cnt[st->cur_slot];
   Arr src = st->cur.view();
   cudaError_t e = cudaSuccess;
+  if (timed) tune_begin(st, tkey);
   for (uint32_t p = 0; p < npass && e == cudaSuccess; ++p) {
     Store& dst = *buf[p & 1];
     dst.set_dense();
@@ -1027,11 +1267,12 @@ sqs_status run_group(sqs_state* st, const std::vector<Gate1>& gates) {
     e = sqs::launch_rsort_pass(launch_of(st, in_slots), st->kw, st->amp32, st->ctl, src, n_ptr,
                                p == 0 ? per_seg : 1u, p == 0 ? tiles0 : tilesN,
                                p == 0 ? &L : nullptr, gates[0].t, shifts[p], hist, part, n_dev,
-                               dst.view(), run.tmask);
+                               dst.view(), run.tmask, rb);
     st->launches += 3;  // a pass is four kernels: histogram, two scan steps, scatter
     src = dst.view();
     n_ptr = n_dev;
   }
+  if (timed) tune_end(st, tkey);
   if (e != cudaSuccess) return cuda_fail(st, e, "sort pass launch");
   e = cudaMemsetAsync(&st->ctl->groups, 0,
                       sizeof(st->ctl->groups) + sizeof(st->ctl->items) + sizeof(st->ctl->stage),
@@ -1049,9 +1290,15 @@ sqs_status run_group(sqs_state* st, const std::vector<Gate1>& gates) {
   const uint64_t cap_all = max_branches(st);
   const uint64_t out_need = std::max<uint64_t>(1, G >= (cap_all >> run.k) ? cap_all : G << run.k);
   // Tiles short enough that groups which grow (up to 2^k branches each from
-  // few) spread over many CTAs: about 2^15 output slots per tile.
+  // few) spread over many CTAs: about `slots` output slots per tile (2^15 by
+  // default; tuned per run length and size under SQS_AUTOTUNE).
+  const sqs_state::TuneKey gkey{kTuneGroupSlots, (uint32_t)st->kw, st->amp32 ? 1u : 0u,
+                                log2_ceil(std::max<uint64_t>(n, 1)), run.k};
+  bool gtimed = false;
+  const int slots = tune_pick(st, gkey, {32768, 8192, 16384, 65536}, gtimed);
   uint32_t tile_len = sqs::kGroupTile;
-  while (tile_len > 32 && (double)tile_len * (double)out_need > 32768.0 * (double)std::max<uint64_t>(n, 1))
+  while (tile_len > 32 &&
+         (double)tile_len * (double)out_need > (double)slots * (double)std::max<uint64_t>(n, 1))
     tile_len >>= 1;
   const uint64_t n_tiles = std::max<uint64_t>(1, (n + tile_len - 1) / tile_len);
   if (st->alt.cap < out_need && !ensure_store(st, st->alt, out_need))
@@ -1061,8 +1308,10 @@ sqs_status run_group(sqs_state* st, const std::vector<Gate1>& gates) {
   const int out_slot = (st->cur_slot + 1) & 3;
   {
     Traced tr(st, SQS_K_GROUP);
+    if (gtimed) tune_begin(st, gkey);
     e = sqs::launch_group(launch_of(st, n), st->kw, st->amp32, st->ctl, st->bk.view(), n_dev,
                           tile_len, n_tiles, st->alt.view(), out_slot, run);
+    if (gtimed) tune_end(st, gkey);
     st->launches++;  // the peak update after the run
   }
   if (e != cudaSuccess) return cuda_fail(st, e, "group launch");
@@ -1341,6 +1590,62 @@ void note_branch(sqs_state* st, const Gate1& g) {
   st->last_target = t;
 }
 
+// Whether the operations queued before interference step g may stay queued
+// past it.  The step must be one that can only merge: the copy-pair property
+// of its target (every branch's partner present with +-1 times its
+// amplitude, tracked the same way whatever merge path runs), which also
+// guarantees that no queued operation reads or writes the target.  The
+// queued operations must not write a control bit or an angle bit of the
+// step, and none may prune.  The step is linear on the amplitudes of each
+// pair and the operations permute keys and multiply amplitudes without
+// touching the pair's bit, so the two orders give the same state; applied
+// after the step, the operations stream half as many branches or fewer.
+// Off in learned-sizing mode, whose queued steps carry their own operations.
+bool defer_ops_ok(const sqs_state* st, const Gate1& g) {
+  // The operations queued now are those between this step and anything held
+  // before it (a held run keeps its own preceding operations), whatever the
+  // merge path, so the decision is the same in every mode.
+  if (st->pair_sign[g.t] == 0 || st->pending.empty()) return false;
+  if (st->flags & SQS_SIZING_LEARNED) return false;
+  uint64_t guard[2] = {g.cmask[0], g.cmask[1]};
+  if (g.mode == 1)
+    for (uint32_t b = 0; b < g.ang_w; ++b) {
+      const uint32_t q = g.ang_off + b;
+      if (q < 128) guard[q >> 6] |= 1ull << (q & 63);
+    }
+  auto field = [](uint64_t m[2], uint32_t off, uint32_t w) {
+    for (uint32_t b = 0; b < w; ++b) {
+      const uint32_t q = off + b;
+      if (q < 128) m[q >> 6] |= 1ull << (q & 63);
+    }
+  };
+  for (const HostOp& h : st->pending) {
+    const sqs::DevOp& d = h.d;
+    uint64_t w[2] = {0ull, 0ull};
+    switch (d.kind) {
+      case sqs::OP_PRUNE:
+        return false;
+      case sqs::OP_XOR:
+      case sqs::OP_MUL_XOR:
+        w[0] = d.xmask[0];
+        w[1] = d.xmask[1];
+        break;
+      case sqs::OP_SWAP:
+        field(w, d.dst_off, d.dst_w);
+        field(w, d.src_off, d.src_w);
+        break;
+      case sqs::OP_MUL:
+      case sqs::OP_TABLE:
+        break;
+      default:  // arithmetic and QRAM write their destination field
+        field(w, d.dst_off, d.dst_w);
+        break;
+    }
+    if ((w[0] & guard[0]) || (w[1] & guard[1])) return false;
+  }
+  return true;
+}
+
 constexpr size_t kLazyMax = 64;  // interference steps queued per learned-sizing flush
 sqs_status run_lazy(sqs_state* st);
 
@@ -1356,6 +1661,8 @@ sqs_status issue_branching(sqs_state* st, const Gate1& g_in, uint32_t n_ctrl) {
   const int8_t b0 = st->const_val[g.t];
   g.no_partners = (!plain && b0 >= 0) ? 1u : 0u;
   g.fold_sign = plain ? 0 : st->pair_sign[g.t];
+  g.defer_ops = defer_ops_ok(st, g) ? 1u : 0u;
+  g.issue_call = st->call;
   g.fold_kill = -1;
   g.fold_twice = 0;
   g.fold_tmax = 0;
@@ -1382,7 +1689,7 @@ sqs_status issue_branching(sqs_state* st, const Gate1& g_in, uint32_t n_ctrl) {
   // An expansion that always acts (no controls that can fail) with
   // U[1][b0] = +-U[0][b0] leaves every branch paired with +-1 times itself.
   int8_t new_sign = 0;
-  if (!plain && b0 >= 0 && g.mode != 1 && predicate_known(st, g.cmask, g.cval) == 1) {
+  if (b0 >= 0 && g.mode != 1 && predicate_known(st, g.cmask, g.cval) == 1) {
     // Compared as numbers (0.0 == -0.0): the children U[r][b0] * a then
     // agree, or agree after a sign flip, in every nonzero component, and a
     // signed zero sums like an unsigned one.
@@ -1750,7 +2057,10 @@ struct sqs_graph {
 sqs_status sort_copy(sqs_state* st, uint64_t n, const uint64_t keep[2], Store** sorted,
                      const unsigned long long** n_sorted) {
   if (n >= (1ull << 32)) return fail(st, SQS_ERR_CAPACITY, "sorting needs fewer than 2^32 branches");
-  const uint32_t D = (uint32_t)sqs::sort_radix_bits();
+  sqs_state::TuneKey tkey;
+  bool timed = false;
+  const int rb = pick_sort_bits(st, n, bits_to_sort(st, keep), tkey, timed);
+  const uint32_t D = (uint32_t)rb;
   std::vector<uint32_t> shifts;
   for (uint32_t q = 0; q < st->total_bits;) {
     const bool kept = (keep[q >> 6] >> (q & 63)) & 1ull;
@@ -1774,7 +2084,7 @@ sqs_status sort_copy(sqs_state* st, uint64_t n, const uint64_t keep[2], Store** 
   const uint64_t tilesN = std::max<uint64_t>(1, (n + tile - 1) / tile);
   unsigned int *hist, *part;
   unsigned long long* n_dev;
-  sqs_status s = sort_scratch(st, std::max(tiles0, tilesN), hist, part, n_dev);
+  sqs_status s = sort_scratch(st, std::max(tiles0, tilesN), hist, part, n_dev, rb);
   if (s != SQS_OK) return s;
   if ((st->bk.cap < n && !ensure_store(st, st->bk, n)) ||
       (st->alt.cap < n && !ensure_store(st, st->alt, n)))
@@ -1791,17 +2101,20 @@ sqs_status sort_copy(sqs_state* st, uint64_t n, const uint64_t keep[2], Store** 
   Arr src = st->cur.view();
   const uint32_t npass = (uint32_t)shifts.size();
   cudaError_t e = cudaSuccess;
+  if (timed) tune_begin(st, tkey);
   for (uint32_t p = 0; p < npass && e == cudaSuccess; ++p) {
     Store& dst = *buf[p & 1];
     dst.set_dense();
     Traced tr(st, SQS_K_SORT);
     e = sqs::launch_rsort_pass(launch_of(st, n), st->kw, st->amp32, st->ctl, src, n_ptr,
                                p == 0 ? per_seg : 1u, p == 0 ? tiles0 : tilesN, nullptr, t_none,
-                               shifts[p], hist, part, n_dev, dst.view(), whole ? nullptr : cm);
+                               shifts[p], hist, part, n_dev, dst.view(), whole ? nullptr : cm,
+                               rb);
     st->launches += 3;
     src = dst.view();
     n_ptr = n_dev;
   }
+  if (timed) tune_end(st, tkey);
   if (e != cudaSuccess) return cuda_fail(st, e, "sort pass launch");
   *sorted = buf[(npass - 1) & 1];
   *n_sorted = n_dev;
@@ -1818,7 +2131,7 @@ sqs_status sqs_state_create(const uint32_t* reg_widths, uint32_t n_regs, uint32_
   if (!out || !reg_widths || n_regs == 0 || n_regs > 128) return SQS_ERR_ARG;
   if (flags & ~(SQS_AMP_FP32 | SQS_SIZING_LEARNED | SQS_MERGE_HASH | SQS_MERGE_SORT |
                 SQS_MERGE_CLUSTER | SQS_MERGE_TUNED | SQS_MERGE_PLAIN | SQS_FUSE_OFF |
-                SQS_FUSE_ALWAYS))
+                SQS_FUSE_ALWAYS | SQS_AUTOTUNE))
     return SQS_ERR_ARG;
   uint32_t total = 0;
   for (uint32_t j = 0; j < n_regs; ++j) {
@@ -1847,11 +2160,27 @@ sqs_status sqs_state_create(const uint32_t* reg_widths, uint32_t n_regs, uint32_
   cudaError_t e = cudaGetDevice(&st->device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&st->sm_count, cudaDevAttrMultiProcessorCount, st->device);
+  cudaDeviceProp prop;
+  if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, st->device);
   if (e != cudaSuccess) {
     sqs_status s = SQS_ERR_CUDA;
     delete st;
     cudaGetLastError();
     return s;
+  }
+  st->gpu_name = prop.name;
+  if (const char* rb = std::getenv("SQS_SORT_BITS")) {
+    const int v = std::atoi(rb);
+    if (sqs::sort_radix_bits_ok(v)) st->forced_sort_bits = v;
+  }
+  // Autotuner choices from an earlier run on this GPU (SQS_TUNE_CACHE).
+  if (const char* path = std::getenv("SQS_TUNE_CACHE")) {
+    std::ifstream f(path);
+    if (f) {
+      std::stringstream buf;
+      buf << f.rdbuf();
+      tune_load(st, buf.str().c_str());
+    }
   }
   e = cudaMallocHost((void**)&st->ctl_host, sizeof(Ctl));
   if (e != cudaSuccess) {
@@ -1875,6 +2204,39 @@ sqs_status sqs_state_create(const uint32_t* reg_widths, uint32_t n_regs, uint32_
 void sqs_state_destroy(sqs_state* st) {
   if (!st) return;
   cudaStreamSynchronize(st->stream);
+  // Autotuner choices to the cache file: merged with entries other states
+  // wrote (this state's measured keys win), written through a temporary file.
+  if (const char* path = std::getenv("SQS_TUNE_CACHE")) {
+    bool any = false;
+    for (auto& kv : st->tuner) {
+      // Collect a last measurement that has completed by now.
+      sqs_state::TuneEntry& E = kv.second;
+      bool t = false;
+      if (E.choice < 0 && !E.cand.empty()) tune_pick(st, kv.first, E.cand, t);
+      any |= E.choice >= 0;
+    }
+    if (any) {
+      sqs_state merged;
+      merged.gpu_name = st->gpu_name;
+      std::ifstream f(path);
+      if (f) {
+        std::stringstream buf;
+        buf << f.rdbuf();
+        tune_load(&merged, buf.str().c_str());
+      }
+      for (const auto& kv : st->tuner)
+        if (kv.second.choice >= 0) {
+          merged.tuner[kv.first] = kv.second;
+          merged.tuner[kv.first].ev[0] = merged.tuner[kv.first].ev[1] = nullptr;
+        }
+      const std::string tmp = std::string(path) + ".tmp";
+      {
+        std::ofstream o(tmp);
+        o << tune_json(&merged);
+      }
+      std::rename(tmp.c_str(), path);
+    }
+  }
   free_store(st, st->cur);
   free_store(st, st->alt);
   free_store(st, st->bk);
@@ -1884,6 +2246,9 @@ void sqs_state_destroy(sqs_state* st) {
   dfree(st, st->sort_buf);
   for (auto& t : st->ang_tabs) dfree(st, t.dev);
   for (auto& kv : st->tune)
+    for (cudaEvent_t e : kv.second.ev)
+      if (e) cudaEventDestroy(e);
+  for (auto& kv : st->tuner)
     for (cudaEvent_t e : kv.second.ev)
       if (e) cudaEventDestroy(e);
   for (sqs_table* t : st->tables) {
@@ -1916,6 +2281,21 @@ sqs_status sqs_state_reset(sqs_state* st) {
   Traced tr(st, SQS_K_INIT);
   cudaError_t e = sqs::launch_init(launch_of(st, 1), st->ctl, st->cur.view(), 0, st->amp32);
   if (e != cudaSuccess) return cuda_fail(st, e, "reset");
+  return SQS_OK;
+}
+
+sqs_status sqs_tune_export(const sqs_state* st, char* buf, uint64_t cap, uint64_t* len) {
+  if (!st || !len) return SQS_ERR_ARG;
+  const std::string j = tune_json(st);
+  *len = j.size();
+  if (!buf || cap < j.size() + 1) return SQS_ERR_ARG;
+  std::memcpy(buf, j.c_str(), j.size() + 1);
+  return SQS_OK;
+}
+
+sqs_status sqs_tune_import(sqs_state* st, const char* json) {
+  if (!st || !json) return SQS_ERR_ARG;
+  tune_load(st, json);
   return SQS_OK;
 }
 

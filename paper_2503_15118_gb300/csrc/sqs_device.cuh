@@ -315,12 +315,10 @@ __device__ __forceinline__ bool apply_ops(uint32_t n_ops, const DevOp* ops, cons
 
 // The same run applied to NI branches at once, operation-major: each
 // operation's descriptor is read from shared memory and dispatched once for
-// the NI branches a thread carries, instead of once per branch.  Dispatch is
-// one switch per operation; a run of conditional XORs (X, CNOT, Toffoli, the
-// commonest kind) stays in an inner loop that tests only the next kind.  Per
-// branch the arithmetic and its order are those of apply_ops.  live[q] is
-// cleared for a branch the run prunes; branches already dead are left alone
-// (their QRAM reads are skipped).
+// the NI branches a thread carries, instead of once per branch.  Per branch
+// the arithmetic and its order are those of apply_ops.  live[q] is cleared
+// for a branch the run prunes; branches already dead are left alone (their
+// QRAM reads are skipped).
 template <int KW, class AT, int NI>
 __device__ __forceinline__ void apply_ops_n(uint32_t n_ops, const DevOp* ops, const AT* tab,
                                             typename KT<KW>::T (&k)[NI], AT (&a)[NI],
@@ -332,122 +330,83 @@ __device__ __forceinline__ void apply_ops_n(uint32_t n_ops, const DevOp* ops, co
 #pragma unroll 1
   for (uint32_t o = 0; o < n_ops; ++o) {
     const DevOp& op = ops[o];
-    switch (op.kind) {
-      case OP_XOR: {
-#pragma unroll 1
-        for (;;) {
-          const DevOp& x = ops[o];
-          const K pm = mk<KW>(x.pmask[0], x.pmask[1]);
-          const K pv = mk<KW>(x.pval[0], x.pval[1]);
-          const K xm = mk<KW>(x.xmask[0], x.xmask[1]);
+    const uint32_t kind = op.kind;
+    const K pm = mk<KW>(op.pmask[0], op.pmask[1]);
+    const K pv = mk<KW>(op.pval[0], op.pval[1]);
+    if (kind == OP_XOR) {
+      const K xm = mk<KW>(op.xmask[0], op.xmask[1]);
 #pragma unroll
-          for (int q = 0; q < NI; ++q) k[q] ^= ((k[q] & pm) == pv) ? xm : (K)0;
-          if (o + 1 >= n_ops || ops[o + 1].kind != OP_XOR) break;
-          ++o;
+      for (int q = 0; q < NI; ++q)
+        if ((k[q] & pm) == pv) k[q] ^= xm;
+    } else if (kind == OP_MUL || kind == OP_MUL_XOR) {
+      const uint32_t sel = op.sel_bit, sh = op.shift;
+      const K xm = kind == OP_MUL_XOR ? mk<KW>(op.xmask[0], op.xmask[1]) : (K)0;
+#pragma unroll
+      for (int q = 0; q < NI; ++q) {
+        if ((k[q] & pm) == pv) {
+          const uint32_t one = sel < 128 ? (uint32_t)((k[q] >> sel) & (K)1) : 0u;
+          idx[q] |= (1u + one) << sh;
+          k[q] ^= xm;
         }
-        break;
       }
-      case OP_MUL:
-      case OP_MUL_XOR: {
-        const K pm = mk<KW>(op.pmask[0], op.pmask[1]);
-        const K pv = mk<KW>(op.pval[0], op.pval[1]);
-        const uint32_t sel = op.sel_bit, sh = op.shift;
-        const K xm = op.kind == OP_MUL_XOR ? mk<KW>(op.xmask[0], op.xmask[1]) : (K)0;
+    } else if (kind == OP_ADD_REG || kind == OP_SUB_REG || kind == OP_ADD_CONST) {
+      const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
+      const uint64_t c = op.constant;
 #pragma unroll
-        for (int q = 0; q < NI; ++q) {
-          if ((k[q] & pm) == pv) {
-            const uint32_t one = sel < 128 ? (uint32_t)((k[q] >> sel) & (K)1) : 0u;
-            idx[q] |= (1u + one) << sh;
-            k[q] ^= xm;
-          }
+      for (int q = 0; q < NI; ++q) {
+        if ((k[q] & pm) == pv) {
+          const uint64_t d = get_field(k[q], doff, dw);
+          const uint64_t sv = kind == OP_ADD_CONST ? c : get_field(k[q], soff, sw);
+          k[q] = set_field<K>(k[q], doff, dw, kind == OP_SUB_REG ? d - sv : d + sv);
         }
-        break;
       }
-      case OP_ADD_REG:
-      case OP_SUB_REG:
-      case OP_ADD_CONST: {
-        const K pm = mk<KW>(op.pmask[0], op.pmask[1]);
-        const K pv = mk<KW>(op.pval[0], op.pval[1]);
-        const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
-        const uint64_t c = op.constant;
-        const bool sub = op.kind == OP_SUB_REG, cst = op.kind == OP_ADD_CONST;
+    } else if (kind == OP_TABLE) {
+      const uint32_t base = op.tab_off;
 #pragma unroll
-        for (int q = 0; q < NI; ++q) {
-          if ((k[q] & pm) == pv) {
-            const uint64_t d = get_field(k[q], doff, dw);
-            const uint64_t sv = cst ? c : get_field(k[q], soff, sw);
-            k[q] = set_field<K>(k[q], doff, dw, sub ? d - sv : d + sv);
-          }
-        }
-        break;
+      for (int q = 0; q < NI; ++q) {
+        if (idx[q]) a[q] = cmul(a[q], tab[base + idx[q]]);
+        idx[q] = 0;
       }
-      case OP_TABLE: {
-        const uint32_t base = op.tab_off;
+    } else if (kind == OP_QRAM) {
+      const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
+      const uint64_t n_ent = op.n_entries;
+      const uint32_t eb = (uint32_t)op.constant;
+      const void* tbl = op.table;
 #pragma unroll
-        for (int q = 0; q < NI; ++q) {
-          if (idx[q]) a[q] = cmul(a[q], tab[base + idx[q]]);
-          idx[q] = 0;
-        }
-        break;
-      }
-      case OP_QRAM: {
-        const K pm = mk<KW>(op.pmask[0], op.pmask[1]);
-        const K pv = mk<KW>(op.pval[0], op.pval[1]);
-        const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
-        const uint64_t n_ent = op.n_entries;
-        const uint32_t eb = (uint32_t)op.constant;
-        const void* tbl = op.table;
-#pragma unroll
-        for (int q = 0; q < NI; ++q) {
-          if (live[q] && (k[q] & pm) == pv) {
-            const uint64_t addr = get_field(k[q], soff, sw);
-            uint64_t d = 0;
-            if (addr < n_ent) {
-              switch (eb) {
-                case 1: d = __ldg((const uint8_t*)tbl + addr); break;
-                case 2: d = __ldg((const uint16_t*)tbl + addr); break;
-                case 4: d = __ldg((const uint32_t*)tbl + addr); break;
-                default: d = __ldg((const unsigned long long*)tbl + addr); break;
-              }
+      for (int q = 0; q < NI; ++q) {
+        if (live[q] && (k[q] & pm) == pv) {
+          const uint64_t addr = get_field(k[q], soff, sw);
+          uint64_t d = 0;
+          if (addr < n_ent) {
+            switch (eb) {
+              case 1: d = __ldg((const uint8_t*)tbl + addr); break;
+              case 2: d = __ldg((const uint16_t*)tbl + addr); break;
+              case 4: d = __ldg((const uint32_t*)tbl + addr); break;
+              default: d = __ldg((const unsigned long long*)tbl + addr); break;
             }
-            k[q] = set_field<K>(k[q], doff, dw, get_field(k[q], doff, dw) ^ d);
           }
+          k[q] = set_field<K>(k[q], doff, dw, get_field(k[q], doff, dw) ^ d);
         }
-        break;
       }
-      case OP_SWAP: {
-        const K pm = mk<KW>(op.pmask[0], op.pmask[1]);
-        const K pv = mk<KW>(op.pval[0], op.pval[1]);
-        const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
+    } else if (kind == OP_SWAP) {
+      const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
 #pragma unroll
-        for (int q = 0; q < NI; ++q) {
-          if ((k[q] & pm) == pv) {
-            const uint64_t v1 = get_field(k[q], doff, dw);
-            const uint64_t v2 = get_field(k[q], soff, sw);
-            k[q] = set_field<K>(set_field<K>(k[q], doff, dw, v2), soff, sw, v1);
-          }
+      for (int q = 0; q < NI; ++q) {
+        if ((k[q] & pm) == pv) {
+          const uint64_t v1 = get_field(k[q], doff, dw);
+          const uint64_t v2 = get_field(k[q], soff, sw);
+          k[q] = set_field<K>(set_field<K>(k[q], doff, dw, v2), soff, sw, v1);
         }
-        break;
       }
-      case OP_PRUNE: {
-        const double eps = op.eps, eps2 = op.eps2;
+    } else if (kind == OP_PRUNE) {
+      const double eps = op.eps, eps2 = op.eps2;
 #pragma unroll
-        for (int q = 0; q < NI; ++q)
-          if (live[q] && !keep_amp(a[q], eps, (float)eps, eps2)) live[q] = false;
-        break;
-      }
-      case OP_MUL_ADD:
-      case OP_MUL_CONST:
-      case OP_DIV_XOR: {
-        const K pm = mk<KW>(op.pmask[0], op.pmask[1]);
-        const K pv = mk<KW>(op.pval[0], op.pval[1]);
+      for (int q = 0; q < NI; ++q)
+        if (live[q] && !keep_amp(a[q], eps, (float)eps, eps2)) live[q] = false;
+    } else if (kind == OP_MUL_ADD || kind == OP_MUL_CONST || kind == OP_DIV_XOR) {
 #pragma unroll
-        for (int q = 0; q < NI; ++q)
-          if ((k[q] & pm) == pv) k[q] = arith_op(op, k[q]);
-        break;
-      }
-      default:
-        break;
+      for (int q = 0; q < NI; ++q)
+        if ((k[q] & pm) == pv) k[q] = arith_op(op, k[q]);
     }
   }
 }
@@ -464,6 +423,40 @@ __device__ __forceinline__ void load_ops(const OpList& L, DevOp* ops, AT* tab) {
   for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
   for (uint32_t i = threadIdx.x; i < L.n_tab; i += blockDim.x) to_amp(tab[i], L.tab[i]);
   __syncthreads();
+}
+
+// ---- bulk copies (TMA engine) into shared memory, completed on an mbarrier --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Global -> shared bulk copy: both addresses 16-byte aligned, bytes a
+// multiple of 16; completion counted on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
 }
 
 constexpr int kStreamThreads = 256;

@@ -97,6 +97,7 @@ struct Ctl {
   unsigned long long groups;     // fused run: coherent groups of its input
   unsigned long long items;      // fused run: branches of its input (after the queued run)
   unsigned long long stage[16];  // fused run: branches after each of its operations
+  unsigned int buckets;          // bucket merge: buckets the partition filled
 };
 
 constexpr unsigned int kErrCapacity = 1u;  // output array too small
@@ -119,6 +120,10 @@ struct Gate1 {            // the interference operation of one merge step
   double eps, eps2;       // pruning threshold and its square (|a| < eps removes)
   float epsf;             // eps rounded to FP32
   uint32_t no_partners;   // the target bit is constant over the state: expand only
+  // Host only: the operations queued before this step commute with it and
+  // stay queued past it (the step can only merge: every partner exists).
+  uint32_t defer_ops;
+  uint32_t issue_call;  // host only: the API call that issued the step (trace attribution)
   uint64_t vary[2];       // key bits not known constant over the state (sort digits)
   // Copy-pair fold: +1 / -1 when every branch's partner across the target bit
   // is known to exist with amplitude exactly +1 / -1 times its own; 0 otherwise.
@@ -181,8 +186,12 @@ cudaError_t launch_apply_compact(const Launch& L, int kw, bool amp32, Ctl* ctl, 
 // Streams `in` through the run and scatters every branch into the hash bucket
 // of its pair class (key with the target bit cleared).  bk is segmented with
 // bk.n_seg buckets of 2^bk.seg_log2 slots, counters zero on entry.
+// Buckets follow the device count: ceil(count / fill_target) of them, at
+// most bk.n_seg (the host's bound; fill_target 0 keeps bk.n_seg); the pair
+// kernel leaves the others empty.
 cudaError_t launch_partition(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
-                             const OpList& ops, const Gate1& g, Arr bk);
+                             const OpList& ops, const Gate1& g, Arr bk, uint32_t fill_target);
+
 // Radix-sort merge (sqs_sort.cu).  One LSD pass: digit `shift` of the
 // pair-class key (key with bit t deleted) of `in` -> `out` (dense), stable.
 // With first_ops the fused run is applied on the way (in is the state as it
@@ -190,7 +199,9 @@ cudaError_t launch_partition(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr 
 // holds 2^8 * n_tiles counters, part sort_part_entries(); the pass stores the
 // number of branches written in *n_dev.
 int sort_tile();
-int sort_radix_bits();
+int sort_radix_bits();                // default digit width (8)
+int sort_radix_bits_max();            // widest digit supported (11)
+bool sort_radix_bits_ok(int rb);      // a supported width: 6, 8, 10 or 11
 uint32_t sort_merge_chunk_log2();
 size_t sort_part_entries();
 // With clear_mask (two words, non-zero) the sort key is the key with those
@@ -201,7 +212,7 @@ cudaError_t launch_rsort_pass(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr
                               uint64_t n_tiles, const OpList* first_ops, uint32_t t,
                               uint32_t shift, unsigned int* hist, unsigned int* part,
                               unsigned long long* n_dev, Arr out,
-                              const uint64_t* clear_mask = nullptr);
+                              const uint64_t* clear_mask = nullptr, int radix_bits = 8);
 // Combines neighbours of the sorted array `in` (*n_ptr branches): chunk c of
 // 2^sort_merge_chunk_log2() branches becomes segment c of `out` (twice the
 // size).  Adds the count into cnt[out_slot], clears cnt[(out_slot + 1) & 3].

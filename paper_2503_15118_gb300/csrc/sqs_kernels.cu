@@ -184,14 +184,24 @@ constexpr int kPartILP = 4;
 template <int KW, class AT>
 __global__ void __launch_bounds__(kStreamThreads)
     k_partition(Ctl* ctl, Arr in, int in_slot, const __grid_constant__ OpList ops, Gate1 g,
-                Arr bk, uint32_t seq) {
+                Arr bk, uint32_t seq, uint32_t fill_target) {
   typedef typename KT<KW>::T K;
   __shared__ AT tab[kTabEntries];
   __shared__ DevOp sops[kMaxOps];
   if (ctl->err) return;
   load_ops(ops, sops, tab);
   const uint64_t n_dense = ctl->cnt[in_slot];
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, n_dense);
+  // Buckets from the device count, ceil(count / fill_target), at most the
+  // host's bucket count (a bound, which may be far above the count, as
+  // inside a captured graph); fill_target 0 keeps the host's count.
+  uint64_t nb = fill_target ? (n_dense + fill_target - 1) / fill_target : bk.n_seg;
+  if (nb < 1) nb = 1;
+  if (nb > bk.n_seg) nb = bk.n_seg;
+  const uint32_t n_buckets = (uint32_t)nb;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicMax(&ctl->peak, n_dense);
+    ctl->buckets = n_buckets;
+  }
   const K bmask = bit_mask<KW>(g.t);
   const uint32_t C = 1u << bk.seg_log2;
   // Units of kPartILP * blockDim slots: a slice of a segment, or of the dense
@@ -240,7 +250,7 @@ __global__ void __launch_bounds__(kStreamThreads)
     for (int q = 0; q < kPartILP; ++q) {
       if (live[q]) {
         const uint64_t h = khash(k[q] & ~bmask);
-        bkt[q] = (uint32_t)(((h >> 32) * (uint64_t)bk.n_seg) >> 32);
+        bkt[q] = (uint32_t)(((h >> 32) * (uint64_t)n_buckets) >> 32);
         pos[q] = atomicAdd(&bk.seg_cnt[bkt[q]], 1u);
       }
     }
@@ -278,6 +288,10 @@ __global__ void __launch_bounds__(kPairThreads)
 
   const uint32_t b = blockIdx.x;
   if (b == 0 && threadIdx.x == 0) ctl->cnt[(out_slot + 1) & 3] = 0;
+  if (b >= ctl->buckets) {  // a bucket the partition did not use
+    if (threadIdx.x == 0) out.seg_cnt[b] = 0u;
+    return;
+  }
   const uint32_t n = bk.seg_cnt[b];
   if (n > C) return;  // overflow already flagged by the partition
   const uint64_t base = (uint64_t)b << bk.seg_log2;
@@ -705,27 +719,29 @@ __global__ void __launch_bounds__(kStreamThreads, 3)
           bool keep0 = false, keep1 = false;
           k0[q] = k[q];
           k1[q] = k[q] | bmask;
-          if (live[q]) {
-            const uint64_t avv = g.mode == 1 ? get_field(k0[q], g.ang_off, g.ang_w) : 0ull;
-            auto fold = [&](const AT& a1) {
-              if (g.fold_kill >= 0 && below_bits(v[q], g.fold_tmax)) {
-                if (g.fold_kill == 1) {
-                  o0[q] = fold_child<AT>(g, 0, v[q], a1);
-                  keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
-                } else {
-                  o1[q] = fold_child<AT>(g, 1, v[q], a1);
-                  keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
-                }
-              } else {
-                children<AT>(g, avv, true, v[q], true, a1, o0[q], o1[q]);
-                keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
-                keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
-              }
-            };
-            if (g.fold_sign > 0)
-              fold(v[q]);
-            else
-              fold(cneg(v[q]));
+          const AT a1 = g.fold_sign > 0 ? v[q] : cneg(v[q]);
+          // The cancelling child is a residue the merge would prune whenever
+          // the member's magnitude is below fold_tmax (every amplitude of a
+          // normalised state): then only the surviving child is evaluated.
+          // The general 2x2 sits in a separate warp-uniform branch, so that
+          // its FP64 products are never issued for lanes that do not need them.
+          const bool kill = live[q] && g.fold_kill >= 0 && below_bits(v[q], g.fold_tmax);
+          if (kill) {
+            if (g.fold_kill == 1) {
+              o0[q] = fold_child<AT>(g, 0, v[q], a1);
+              keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
+            } else {
+              o1[q] = fold_child<AT>(g, 1, v[q], a1);
+              keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
+            }
+          }
+          if (__any_sync(0xffffffffu, live[q] && !kill)) {
+            if (live[q] && !kill) {
+              const uint64_t avv = g.mode == 1 ? get_field(k0[q], g.ang_off, g.ang_w) : 0ull;
+              children<AT>(g, avv, true, v[q], true, a1, o0[q], o1[q]);
+              keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
+              keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
+            }
           }
           b0[q] = __ballot_sync(0xffffffffu, keep0);
           b1[q] = __ballot_sync(0xffffffffu, keep1);
@@ -768,6 +784,513 @@ __global__ void __launch_bounds__(kStreamThreads, 3)
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Staged input stream (TMA bulk copies, double-buffered).  The input is
+// walked in units of kUnit slots: slice (G & 3) of chunk (G >> 2) of
+// 2^kExpandChunkLog2 slots (a dense range, or a slice of one segment).  A
+// CTA takes units G = blockIdx.x, + gridDim.x, ...; one elected thread copies
+// unit i + 2 into the stage buffer unit i has just released, with
+// cp.async.bulk on that buffer's mbarrier, while every thread computes on
+// unit i + 1's buffer: the loads of the next units overlap the arithmetic of
+// this one and no thread stalls on a global load.
+constexpr uint32_t kWaitLimit = 1u << 26;  // bounded mbarrier wait (try_wait polls)
+constexpr uint32_t kUnitLog2 = 10;
+constexpr uint32_t kUnit = 1u << kUnitLog2;
+constexpr uint32_t kUnitsPerChunkLog2 = kExpandChunkLog2 - kUnitLog2;
+
+struct UnitRange {
+  uint64_t base;
+  uint32_t cnt;
+};
+
+__device__ __forceinline__ UnitRange unit_range(const Arr& in, uint64_t n_dense, uint32_t cps_log2,
+                                                uint64_t G) {
+  const uint64_t c = G >> kUnitsPerChunkLog2;
+  const uint64_t chunk = 1ull << kExpandChunkLog2;
+  uint64_t ibase, cnt;
+  if (in.seg_cnt) {
+    const uint64_t sg = c >> cps_log2;
+    const uint64_t off = (c & ((1ull << cps_log2) - 1ull)) << kExpandChunkLog2;
+    const uint64_t n_sg = sg < in.n_seg ? in.seg_cnt[sg] : 0;
+    ibase = (sg << in.seg_log2) + off;
+    cnt = n_sg > off ? (n_sg - off < chunk ? n_sg - off : chunk) : 0;
+  } else {
+    ibase = c << kExpandChunkLog2;
+    cnt = ibase >= n_dense ? 0 : (n_dense - ibase < chunk ? n_dense - ibase : chunk);
+  }
+  const uint64_t off = (G & ((1ull << kUnitsPerChunkLog2) - 1ull)) << kUnitLog2;
+  UnitRange r;
+  r.base = ibase + off;
+  r.cnt = (uint32_t)(cnt > off ? (cnt - off < kUnit ? cnt - off : kUnit) : 0);
+  return r;
+}
+
+template <int KW, class AT>
+struct StageBuf {
+  uint64_t k0[kUnit];
+  uint64_t k1[KW == 2 ? kUnit : 2];
+  AT amp[kUnit];
+};
+
+template <int KW>
+__device__ __forceinline__ typename KT<KW>::T stage_key(const uint64_t* k0, const uint64_t* k1,
+                                                        uint32_t j) {
+  return mk<KW>(k0[j], KW == 2 ? k1[j] : 0ull);
+}
+
+// Thread 0: copies unit r into buffer b, arriving on `bar` with the byte
+// count.  Bulk copies need 16-byte multiples: with 8-byte elements and an odd
+// count the last element is read with a plain load instead (never past the
+// unit).  A unit with nothing to copy arrives with zero bytes, so every
+// unit completes one phase of its barrier.
+template <int KW, class AT>
+__device__ __forceinline__ void stage_issue(StageBuf<KW, AT>& b, uint64_t* bar, const Arr& in,
+                                            UnitRange r) {
+  const uint32_t even = r.cnt & ~1u;
+  const uint32_t na = sizeof(AT) == 16 ? r.cnt : even;
+  const uint32_t bytes = even * 8u * (uint32_t)KW + na * (uint32_t)sizeof(AT);
+  mbar_expect_tx(bar, bytes);
+  if (even) {
+    bulk_g2s(b.k0, in.k0 + r.base, even * 8u, bar);
+    if (KW == 2) bulk_g2s(b.k1, in.k1 + r.base, even * 8u, bar);
+  }
+  if (na) bulk_g2s(b.amp, (const AT*)in.amp + r.base, na * (uint32_t)sizeof(AT), bar);
+  if (even < r.cnt) {
+    const uint64_t t = r.base + even;
+    b.k0[even] = in.k0[t];
+    if (KW == 2) b.k1[even] = in.k1[t];
+    if (na < r.cnt) b.amp[even] = ((const AT*)in.amp)[t];
+  }
+}
+
+// Bounded wait on one phase of a stage barrier (every thread polls).
+__device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t it = 0;
+  while (!mbar_try_wait(bar, parity))
+    if (++it >= kWaitLimit) return false;
+  return true;
+}
+
+// Drives the staged stream over this CTA's units: waits for each unit's
+// buffer, calls unit(buffer, range) -- which must end with a __syncthreads
+// after its last read of the buffer -- then refills the buffer with the unit
+// two steps ahead.  smem: two barriers (first 16 bytes of a 128-byte
+// header), then the two buffers.  Returns false when a bounded wait ran out
+// (the error is raised; copies still in flight have been waited for).
+template <int KW, class AT, class F>
+__device__ __forceinline__ bool staged_stream(Ctl* ctl, const Arr& in, uint64_t n_dense,
+                                              uint64_t n_chunks, uint32_t seq,
+                                              unsigned char* smem, unsigned int* abort_flag,
+                                              F&& unit) {
+  uint64_t* bar = (uint64_t*)smem;
+  StageBuf<KW, AT>* stage = (StageBuf<KW, AT>*)(smem + 128);
+  const uint32_t cps_log2 = in.seg_cnt ? in.seg_log2 - kExpandChunkLog2 : 0u;
+  // A dense input covers only the units its device count reaches (the host
+  // sized n_chunks from a bound, which may be far above it, as in a graph).
+  uint64_t n_units = n_chunks << kUnitsPerChunkLog2;
+  if (!in.seg_cnt) {
+    const uint64_t need = (n_dense + kUnit - 1) >> kUnitLog2;
+    if (need < n_units) n_units = need;
+  }
+  // Units with no live slot (the tails of segments that are not full) are
+  // skipped: every thread walks the same sequence of non-empty units.
+  auto next_unit = [&](uint64_t G) {
+    for (; G < n_units; G += gridDim.x)
+      if (unit_range(in, n_dense, cps_log2, G).cnt) return G;
+    return n_units;
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    *abort_flag = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint64_t g_cur = next_unit(blockIdx.x);
+  uint64_t g_nxt = g_cur < n_units ? next_unit(g_cur + gridDim.x) : n_units;
+  if (threadIdx.x == 0) {
+    if (g_cur < n_units)
+      stage_issue<KW, AT>(stage[0], &bar[0], in, unit_range(in, n_dense, cps_log2, g_cur));
+    if (g_nxt < n_units)
+      stage_issue<KW, AT>(stage[1], &bar[1], in, unit_range(in, n_dense, cps_log2, g_nxt));
+  }
+  for (uint32_t i = 0; g_cur < n_units; ++i) {
+    const uint32_t bi = i & 1u;
+    if (!stage_wait(&bar[bi], (i >> 1) & 1u)) atomicOr(abort_flag, 1u);
+    __syncthreads();
+    if (*abort_flag) {
+      // Copies may still be landing in this CTA's buffers: let them finish
+      // (bounded again) before the CTA's shared memory is released.
+      if (threadIdx.x == 0) {
+        raise_err(ctl, kErrProbe, seq, 0);
+        stage_wait(&bar[bi], (i >> 1) & 1u);
+        if (g_nxt < n_units) stage_wait(&bar[bi ^ 1u], ((i + 1) >> 1) & 1u);
+      }
+      return false;
+    }
+    unit(stage[bi], unit_range(in, n_dense, cps_log2, g_cur));
+    const uint64_t g_after = g_nxt < n_units ? next_unit(g_nxt + gridDim.x) : n_units;
+    if (threadIdx.x == 0 && g_after < n_units)
+      stage_issue<KW, AT>(stage[bi], &bar[bi], in, unit_range(in, n_dense, cps_log2, g_after));
+    g_cur = g_nxt;
+    g_nxt = g_after;
+  }
+  return true;
+}
+
+template <int KW, class AT>
+constexpr size_t stream_smem_bytes() {
+  return 128 + 2 * sizeof(StageBuf<KW, AT>);
+}
+
+// Resident CTAs per SM of a staged-stream kernel (cached per device).
+template <class Kern>
+static cudaError_t resident_per_sm(Kern kern, size_t smem, int* per_sm_cache, int& occ) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  occ = dev < 64 ? per_sm_cache[dev] : 0;
+  if (occ == 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kStreamThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    if (dev < 64) per_sm_cache[dev] = occ;
+  }
+  return cudaSuccess;
+}
+
+
+// ---------------------------------------------------------------------------
+// Staged variants of k_expand and k_fold, for launches with no fused
+// operation (measured faster there: the input arrives by bulk copy while the
+// previous unit computes; with a long fused run the per-unit barriers cost
+// more than the loads they hide, and the register-fed kernels above win).
+// Constant target bit: no branch has a partner, so each controlled branch
+// expands into its two children directly (no partition, no pairing).
+// Copy-pair fold with controls (g.fold_sign != 0): every controlled branch has
+// its partner, holding fold_sign times its amplitude, so the bit-0 member
+// alone emits the pair's two children and the bit-1 member emits nothing;
+// branches whose controls fail pass unchanged.  Input through the staged
+// stream; the output is dense: each block reserves every round's outputs with
+// one atomic.
+template <int KW, class AT>
+__global__ void __launch_bounds__(kStreamThreads, 3)
+    k_expand_staged(Ctl* ctl, Arr in, int in_slot, uint64_t n_chunks, Arr out, int out_slot,
+             const __grid_constant__ OpList ops, Gate1 g, uint32_t seq) {
+  typedef typename KT<KW>::T K;
+  __shared__ AT tab[kTabEntries];
+  __shared__ DevOp sops[kMaxOps];
+  __shared__ unsigned int wtot[kStreamThreads / 32];
+  __shared__ unsigned long long round_base;
+  __shared__ unsigned int abort_flag;
+  extern __shared__ __align__(128) unsigned char exp_smem[];
+  if (ctl->err) return;
+  load_ops(ops, sops, tab);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->cnt[(out_slot + 1) & 3] = 0;
+    atomicMax(&ctl->peak, ctl->cnt[in_slot]);
+  }
+  const uint64_t n_dense = ctl->cnt[in_slot];
+  // A dense input longer than the chunks the host sized from its bound (a
+  // static bound the state outgrew) is an error, never a partial pass.
+  if (!in.seg_cnt && n_dense > (n_chunks << kExpandChunkLog2)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) raise_err(ctl, kErrCapacity, seq, n_dense);
+    return;
+  }
+  const K bmask = bit_mask<KW>(g.t);
+  const K cmask = mk<KW>(g.cmask[0], g.cmask[1]);
+  const K cval = mk<KW>(g.cval[0], g.cval[1]);
+  const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const unsigned int lt = (1u << lane) - 1u;
+  auto unit = [&](StageBuf<KW, AT>& sb, const UnitRange r) {
+    for (uint32_t r0 = 0; r0 < r.cnt; r0 += kExpandILP * kStreamThreads) {
+      K k[kExpandILP];
+      AT v[kExpandILP];
+      bool live[kExpandILP];
+#pragma unroll
+      for (int q = 0; q < kExpandILP; ++q) {
+        const uint32_t j = r0 + (uint32_t)q * kStreamThreads + threadIdx.x;
+        live[q] = j < r.cnt;
+        k[q] = 0;
+        v[q].x = v[q].y = 0;
+        if (live[q]) {
+          k[q] = stage_key<KW>(sb.k0, sb.k1, j);
+          v[q] = sb.amp[j];
+        }
+      }
+      if (__any_sync(0xffffffffu, live[0])) apply_ops_n<KW, AT, kExpandILP>(ops.n, sops, tab, k, v, live);
+      K k0[kExpandILP], k1[kExpandILP];
+      AT o0[kExpandILP], o1[kExpandILP];
+      unsigned int b0[kExpandILP], b1[kExpandILP];
+      unsigned int wsum = 0;
+#pragma unroll
+      for (int q = 0; q < kExpandILP; ++q) {
+        bool keep0 = false, keep1 = false;
+        k0[q] = k1[q] = 0;
+        if (live[q]) {
+          if ((k[q] & cmask) != cval) {
+            keep0 = true;  // controls not met: the branch is unchanged
+            k0[q] = k[q];
+            o0[q] = v[q];
+          } else {
+            const bool kt = (k[q] & bmask) != (K)0;
+            k0[q] = k[q] & ~bmask;
+            k1[q] = k[q] | bmask;
+            const uint64_t av = g.mode == 1 ? get_field(k0[q], g.ang_off, g.ang_w) : 0ull;
+            if (g.fold_sign == 0) {
+              if (!kt)
+                children<AT>(g, av, true, v[q], false, v[q], o0[q], o1[q]);
+              else
+                children<AT>(g, av, false, v[q], true, v[q], o0[q], o1[q]);
+              keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
+              keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
+            } else if (!kt) {
+              // The partner holds exactly fold_sign * v: the pair's 2x2 as the
+              // merge evaluates it, without looking the partner up.
+              auto fold = [&](const AT& a1) {
+                if (g.fold_kill >= 0 && below_bits(v[q], g.fold_tmax)) {
+                  // The cancelling child is a residue the merge would prune.
+                  if (g.fold_kill == 1) {
+                    o0[q] = fold_child<AT>(g, 0, v[q], a1);
+                    keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
+                  } else {
+                    o1[q] = fold_child<AT>(g, 1, v[q], a1);
+                    keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
+                  }
+                } else {
+                  children<AT>(g, av, true, v[q], true, a1, o0[q], o1[q]);
+                  keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
+                  keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
+                }
+              };
+              if (g.fold_sign > 0)
+                fold(v[q]);
+              else
+                fold(cneg(v[q]));
+            }
+          }
+        }
+        b0[q] = __ballot_sync(0xffffffffu, keep0);
+        b1[q] = __ballot_sync(0xffffffffu, keep1);
+        wsum += __popc(b0[q]) + __popc(b1[q]);
+      }
+      // Dense output: the block reserves the round's outputs with one atomic
+      // on the output count; each warp writes its items in (item, lane) order.
+      if (lane == 0) wtot[warp] = wsum;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned int sum = 0;
+        for (unsigned int w = 0; w < kStreamThreads / 32u; ++w) {
+          const unsigned int t = wtot[w];
+          wtot[w] = sum;
+          sum += t;
+        }
+        round_base = sum ? atomicAdd(&ctl->cnt[out_slot], (unsigned long long)sum) : 0ull;
+        if (sum && round_base + sum > out.cap)
+          raise_err(ctl, kErrCapacity, seq, round_base + sum);
+      }
+      __syncthreads();
+      uint64_t wb = round_base + wtot[warp];
+#pragma unroll
+      for (int q = 0; q < kExpandILP; ++q) {
+        if ((b0[q] >> lane) & 1u) {
+          const uint64_t pos = wb + __popc(b0[q] & lt);
+          if (pos < out.cap) {
+            st_key<KW>(out, pos, k0[q]);
+            ((AT*)out.amp)[pos] = o0[q];
+          }
+        }
+        if ((b1[q] >> lane) & 1u) {
+          const uint64_t pos = wb + __popc(b0[q]) + __popc(b1[q] & lt);
+          if (pos < out.cap) {
+            st_key<KW>(out, pos, k1[q]);
+            ((AT*)out.amp)[pos] = o1[q];
+          }
+        }
+        wb += __popc(b0[q]) + __popc(b1[q]);
+      }
+      __syncthreads();  // wtot, round_base and the buffer are reused next
+    }
+    __syncthreads();  // an empty unit: the buffer is released all the same
+  };
+  staged_stream<KW, AT>(ctl, in, n_dense, n_chunks, seq, exp_smem, &abort_flag, unit);
+}
+
+// ---------------------------------------------------------------------------
+// Copy-pair fold without controls: only the bit-0 member of each pair emits
+// (the pair's two children), so the bit-1 members need neither the fused run
+// nor any arithmetic.  The run never reads or writes the target bit (the
+// host drops a bit's copy-pair property as soon as an operation touches it),
+// so a member's target bit is already known from its loaded key.
+//
+// Input through the staged stream above.  Per unit: the bit-0 members are
+// compacted into a list (warp ballots), then the fused run and the fold run
+// on the list, so every lane of the FP64 sequence holds a member that emits.
+// The arithmetic per member is the fold branch of k_expand, so the state is
+// bit-identical to it.
+template <int KW, class AT>
+constexpr size_t fold_staged_smem_bytes() {
+  return stream_smem_bytes<KW, AT>() + kUnit * sizeof(uint16_t);
+}
+
+template <int KW, class AT>
+__global__ void __launch_bounds__(kStreamThreads, 3)
+    k_fold_staged(Ctl* ctl, Arr in, int in_slot, uint64_t n_chunks, Arr out, int out_slot,
+           const __grid_constant__ OpList ops, Gate1 g, uint32_t seq) {
+  typedef typename KT<KW>::T K;
+  __shared__ AT tab[kTabEntries];
+  __shared__ DevOp sops[kMaxOps];
+  __shared__ unsigned int wtot[kStreamThreads / 32];
+  __shared__ unsigned long long round_base;
+  __shared__ unsigned int n_act, abort_flag;
+  extern __shared__ __align__(128) unsigned char fold_smem[];
+  uint16_t* list = (uint16_t*)(fold_smem + stream_smem_bytes<KW, AT>());
+  if (ctl->err) return;
+  load_ops(ops, sops, tab);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->cnt[(out_slot + 1) & 3] = 0;
+    atomicMax(&ctl->peak, ctl->cnt[in_slot]);
+  }
+  const uint64_t n_dense = ctl->cnt[in_slot];
+  if (!in.seg_cnt && n_dense > (n_chunks << kExpandChunkLog2)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) raise_err(ctl, kErrCapacity, seq, n_dense);
+    return;
+  }
+  const K bmask = bit_mask<KW>(g.t);
+  const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const unsigned int lt = (1u << lane) - 1u;
+  constexpr int kPer = (int)(kUnit / kStreamThreads);
+  auto unit = [&](StageBuf<KW, AT>& sb, const UnitRange r) {
+    // ---- compaction of the bit-0 members ----
+    unsigned int bal[kPer];
+    unsigned int mine = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const uint32_t j = (uint32_t)q * kStreamThreads + threadIdx.x;
+      const bool act = j < r.cnt && (stage_key<KW>(sb.k0, sb.k1, j) & bmask) == (K)0;
+      bal[q] = __ballot_sync(0xffffffffu, act);
+      mine += __popc(bal[q]);
+    }
+    if (lane == 0) wtot[warp] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned int sum = 0;
+      for (unsigned int w = 0; w < kStreamThreads / 32u; ++w) {
+        const unsigned int t = wtot[w];
+        wtot[w] = sum;
+        sum += t;
+      }
+      n_act = sum;
+    }
+    __syncthreads();
+    {
+      unsigned int pos = wtot[warp];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        if ((bal[q] >> lane) & 1u)
+          list[pos + __popc(bal[q] & lt)] = (uint16_t)((uint32_t)q * kStreamThreads + threadIdx.x);
+        pos += __popc(bal[q]);
+      }
+    }
+    __syncthreads();
+    const uint32_t na = n_act;
+    // ---- fused run and fold on the compacted members ----
+    for (uint32_t r0 = 0; r0 < na; r0 += kFoldILP * kStreamThreads) {
+      K k[kFoldILP];
+      AT v[kFoldILP];
+      bool live[kFoldILP];
+#pragma unroll
+      for (int q = 0; q < kFoldILP; ++q) {
+        const uint32_t li = r0 + (uint32_t)q * kStreamThreads + threadIdx.x;
+        live[q] = li < na;
+        k[q] = 0;
+        v[q].x = v[q].y = 0;
+        if (live[q]) {
+          const uint32_t j = list[li];
+          k[q] = stage_key<KW>(sb.k0, sb.k1, j);
+          v[q] = sb.amp[j];
+        }
+      }
+      K k1[kFoldILP];
+      AT o0[kFoldILP], o1[kFoldILP];
+      unsigned int b0[kFoldILP], b1[kFoldILP];
+      unsigned int wsum = 0;
+      // A warp with no member this round skips the arithmetic (it still takes
+      // part in the round's barriers).
+      if (__any_sync(0xffffffffu, live[0])) apply_ops_n<KW, AT, kFoldILP>(ops.n, sops, tab, k, v, live);
+#pragma unroll
+      for (int q = 0; q < kFoldILP; ++q) {
+        bool keep0 = false, keep1 = false;
+        k1[q] = k[q] | bmask;
+        const AT a1 = g.fold_sign > 0 ? v[q] : cneg(v[q]);
+        // The cancelling child is a residue the merge would prune whenever
+        // the member's magnitude is below fold_tmax (every amplitude of a
+        // normalised state): then only the surviving child is evaluated.  The
+        // general 2x2 runs in a separate, warp-uniform branch, so that its
+        // FP64 products are never issued for lanes that do not need them.
+        const bool kill = live[q] && g.fold_kill >= 0 && below_bits(v[q], g.fold_tmax);
+        if (kill) {
+          if (g.fold_kill == 1) {
+            o0[q] = fold_child<AT>(g, 0, v[q], a1);
+            keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
+          } else {
+            o1[q] = fold_child<AT>(g, 1, v[q], a1);
+            keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
+          }
+        }
+        if (__any_sync(0xffffffffu, live[q] && !kill)) {
+          if (live[q] && !kill) {
+            const uint64_t avv = g.mode == 1 ? get_field(k[q], g.ang_off, g.ang_w) : 0ull;
+            children<AT>(g, avv, true, v[q], true, a1, o0[q], o1[q]);
+            keep0 = keep_amp(o0[q], g.eps, g.epsf, g.eps2);
+            keep1 = keep_amp(o1[q], g.eps, g.epsf, g.eps2);
+          }
+        }
+        b0[q] = __ballot_sync(0xffffffffu, keep0);
+        b1[q] = __ballot_sync(0xffffffffu, keep1);
+        wsum += __popc(b0[q]) + __popc(b1[q]);
+      }
+      if (lane == 0) wtot[warp] = wsum;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned int sum = 0;
+        for (unsigned int w = 0; w < kStreamThreads / 32u; ++w) {
+          const unsigned int t = wtot[w];
+          wtot[w] = sum;
+          sum += t;
+        }
+        round_base = sum ? atomicAdd(&ctl->cnt[out_slot], (unsigned long long)sum) : 0ull;
+        if (sum && round_base + sum > out.cap)
+          raise_err(ctl, kErrCapacity, seq, round_base + sum);
+      }
+      __syncthreads();
+      uint64_t wb = round_base + wtot[warp];
+#pragma unroll
+      for (int q = 0; q < kFoldILP; ++q) {
+        if ((b0[q] >> lane) & 1u) {
+          const uint64_t pos = wb + __popc(b0[q] & lt);
+          if (pos < out.cap) {
+            st_key<KW>(out, pos, k[q]);
+            ((AT*)out.amp)[pos] = o0[q];
+          }
+        }
+        if ((b1[q] >> lane) & 1u) {
+          const uint64_t pos = wb + __popc(b0[q]) + __popc(b1[q] & lt);
+          if (pos < out.cap) {
+            st_key<KW>(out, pos, k1[q]);
+            ((AT*)out.amp)[pos] = o1[q];
+          }
+        }
+        wb += __popc(b0[q]) + __popc(b1[q]);
+      }
+      __syncthreads();  // wtot, round_base, the list and the buffer are reused next
+    }
+    // With no member the last barrier above is the compaction's: every read
+    // of the buffer is done either way.
+  };
+  staged_stream<KW, AT>(ctl, in, n_dense, n_chunks, seq, fold_smem, &abort_flag, unit);
 }
 
 // ---------------------------------------------------------------------------
@@ -993,9 +1516,6 @@ __global__ void __launch_bounds__(kBinThreads)
   }
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -1012,38 +1532,10 @@ __device__ __forceinline__ T* map_rank(T* p, uint32_t rank) {
   asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"((uint64_t)p), "r"(rank));
   return (T*)out;
 }
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0u;
-}
 
 // Slot tag: (CTA rank << 12 | index) + 1; 0 marks an empty slot.
 __device__ __forceinline__ uint32_t ctag(uint32_t r, uint32_t i) { return ((r << kSliceLog2) | i) + 1u; }
 
-constexpr uint32_t kWaitLimit = 1u << 26;  // bounded mbarrier wait (try_wait loop)
 
 template <int KW, class AT>
 size_t pair_cluster_smem_bytes_t() {
@@ -1345,9 +1837,59 @@ cudaError_t launch_angle_table(cudaStream_t s, double2* tab, uint32_t digits, do
   return cudaGetLastError();
 }
 
+// The staged variants: one wave of resident CTAs, each streaming its units.
+template <int KW, class AT>
+static cudaError_t expand_staged_t(const Launch& L, Ctl* ctl, Arr in, int in_slot,
+                                   uint64_t n_chunks, const OpList& ops, const Gate1& g, Arr out,
+                                   int out_slot) {
+  const size_t smem = stream_smem_bytes<KW, AT>();
+  static std::atomic<unsigned long long> configured{0};
+  cudaError_t e = ensure_smem_optin((const void*)k_expand_staged<KW, AT>, smem, configured);
+  if (e != cudaSuccess) return e;
+  static int per_sm[64] = {0};
+  int occ = 1;
+  e = resident_per_sm(k_expand_staged<KW, AT>, smem, per_sm, occ);
+  if (e != cudaSuccess) return e;
+  const uint64_t units = n_chunks << kUnitsPerChunkLog2;
+  uint64_t grid = (uint64_t)L.sm_count * (uint64_t)occ;
+  if (grid > units) grid = units;
+  if (grid < 1) grid = 1;
+  k_expand_staged<KW, AT><<<(int)grid, kStreamThreads, smem, L.stream>>>(
+      ctl, in, in_slot, n_chunks, out, out_slot, ops, g, L.seq);
+  return cudaGetLastError();
+}
+
+template <int KW, class AT>
+static cudaError_t fold_staged_t(const Launch& L, Ctl* ctl, Arr in, int in_slot,
+                                 uint64_t n_chunks, const OpList& ops, const Gate1& g, Arr out,
+                                 int out_slot) {
+  const size_t smem = fold_staged_smem_bytes<KW, AT>();
+  static std::atomic<unsigned long long> configured{0};
+  cudaError_t e = ensure_smem_optin((const void*)k_fold_staged<KW, AT>, smem, configured);
+  if (e != cudaSuccess) return e;
+  static int per_sm[64] = {0};
+  int occ = 1;
+  e = resident_per_sm(k_fold_staged<KW, AT>, smem, per_sm, occ);
+  if (e != cudaSuccess) return e;
+  const uint64_t units = n_chunks << kUnitsPerChunkLog2;
+  uint64_t grid = (uint64_t)L.sm_count * (uint64_t)occ;
+  if (grid > units) grid = units;
+  if (grid < 1) grid = 1;
+  k_fold_staged<KW, AT><<<(int)grid, kStreamThreads, smem, L.stream>>>(
+      ctl, in, in_slot, n_chunks, out, out_slot, ops, g, L.seq);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_expand(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
                           uint64_t n_chunks, const OpList& ops, const Gate1& g, Arr out,
                           int out_slot) {
+  if (ops.n == 0) {
+    if (kw == 1)
+      return amp32 ? expand_staged_t<1, float2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot)
+                   : expand_staged_t<1, double2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot);
+    return amp32 ? expand_staged_t<2, float2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot)
+                 : expand_staged_t<2, double2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot);
+  }
   uint64_t grid = n_chunks < 1 ? 1 : n_chunks;
   if (grid > (uint64_t)L.sm_count * 8) grid = (uint64_t)L.sm_count * 8;
 #define SQS_EX(KW_, AT_)                                                                  \
@@ -1376,6 +1918,13 @@ cudaError_t launch_fold(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, i
                         uint64_t n_chunks, const OpList& ops, const Gate1& g, Arr out,
                         int out_slot) {
   if (g.fold_sign == 0 || g.cmask[0] != 0 || g.cmask[1] != 0) return cudaErrorInvalidValue;
+  if (ops.n == 0) {
+    if (kw == 1)
+      return amp32 ? fold_staged_t<1, float2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot)
+                   : fold_staged_t<1, double2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot);
+    return amp32 ? fold_staged_t<2, float2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot)
+                 : fold_staged_t<2, double2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot);
+  }
   if (kw == 1)
     return amp32 ? fold_t<1, float2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot)
                  : fold_t<1, double2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot);
@@ -1384,11 +1933,11 @@ cudaError_t launch_fold(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, i
 }
 
 cudaError_t launch_partition(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, int in_slot,
-                             const OpList& ops, const Gate1& g, Arr bk) {
+                             const OpList& ops, const Gate1& g, Arr bk, uint32_t fill_target) {
   const int grid = stream_grid(L, kStreamThreads);
 #define SQS_PT(KW_, AT_)                                                                \
   k_partition<KW_, AT_><<<grid, kStreamThreads, 0, L.stream>>>(ctl, in, in_slot, ops, g, \
-                                                               bk, L.seq)
+                                                               bk, L.seq, fill_target)
   SQS_DISPATCH(kw, amp32, SQS_PT);
 #undef SQS_PT
   return cudaGetLastError();

@@ -217,7 +217,7 @@ extern "C" sqs_status sqs_apply_u1q_noalloc(const uint32_t* reg_widths, uint32_t
   // ---- the merge: clear, partition, pair, offsets, dense copy ----
   k_noalloc_begin<<<1, 256, 0, s>>>(ctl, bk.seg_cnt, seg.seg_cnt, B, n_in);
   e = cudaGetLastError();
-  if (e == cudaSuccess) e = sqs::launch_partition(L, kw, false, ctl, in, 0, kNoOps, g, bk);
+  if (e == cudaSuccess) e = sqs::launch_partition(L, kw, false, ctl, in, 0, kNoOps, g, bk, 0u);
   if (e == cudaSuccess) e = sqs::launch_pair(L, kw, false, ctl, g, bk, seg, 1);
   if (e == cudaSuccess) {
     k_noalloc_offsets<<<1, 32, 0, s>>>(ctl, seg.seg_cnt, B, out_cap, offsets,

@@ -12,8 +12,10 @@
 // where it lies (dense or segmented); later passes are dense.  Digits are 8
 // bits wide and their windows skip key bits the host knows to be constant
 // over the whole state, so a state over few varying qubits sorts in few
-// passes.  Counts are 32-bit: the host routes states of 2^32 or more
-// branches to the hash merge.
+// passes.  The digit width is a template parameter (6, 8, 10 or 11 bits):
+// wider digits mean fewer passes but larger per-tile histograms and scans; the
+// host picks it (autotuned when asked).  Counts are 32-bit: the host routes
+// states of 2^32 or more branches to the hash merge.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,12 +32,11 @@ constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 8;                         // branches per thread
 constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 branches per tile
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
+constexpr int kRadixBitsDefault = 8;
+constexpr int kRadixBitsMax = 11;
 constexpr int kScanThreads = 1024;
 constexpr int kScanBlocks = 256;
 constexpr uint32_t kMergeChunkLog2 = 12;  // input slots per output segment
-static_assert(kRadix == kSortThreads, "one digit per thread in the tile scan");
 
 // The pair-class key: bit t deleted, the bits above it shifted down by one.
 template <class K>
@@ -50,10 +51,10 @@ __device__ __forceinline__ uint32_t umin32(uint32_t a, uint32_t b) { return a < 
 // The digit of the sort key: the pair-class key, or (a fused run: cm set)
 // the key with the run's targets cleared, whose groups the sort makes
 // contiguous.
-template <class K>
+template <int RB, class K>
 __device__ __forceinline__ uint32_t digit_of(K k, uint32_t t, uint32_t shift, K cm) {
   const K c = cm != (K)0 ? (k & ~cm) : drop_bit(k, t);
-  return (uint32_t)(c >> shift) & (uint32_t)(kRadix - 1);
+  return (uint32_t)(c >> shift) & ((1u << RB) - 1u);
 }
 
 // Tile `tile` of the input: a slice of one segment, or of the dense array.
@@ -72,16 +73,17 @@ __device__ __forceinline__ void tile_range(const Arr& in, uint64_t n_dense, uint
 }
 
 // Digit counts of every tile: hist[d * n_tiles + tile].
-template <int KW, class AT, bool FIRST>
+template <int KW, class AT, bool FIRST, int RB>
 __global__ void __launch_bounds__(kSortThreads)
     k_rsort_hist(Ctl* ctl, Arr in, const unsigned long long* n_ptr, uint32_t per_seg,
                  const __grid_constant__ OpList ops, uint32_t t, uint32_t shift,
                  uint64_t n_tiles, unsigned int* hist, uint64_t cm0, uint64_t cm1) {
   typedef typename KT<KW>::T K;
+  constexpr uint32_t R = 1u << RB;
   const K cm = mk<KW>(cm0, cm1);
   __shared__ AT tab[FIRST ? kTabEntries : 1];
   __shared__ DevOp sops[FIRST ? kMaxOps : 1];
-  __shared__ unsigned int h[kRadix];
+  __shared__ unsigned int h[R];
   if (ctl->err) return;
   if (FIRST) {
     load_ops(ops, sops, tab);
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(kSortThreads)
     return;
   }
   for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    h[threadIdx.x] = 0u;
+    for (uint32_t d = threadIdx.x; d < R; d += blockDim.x) h[d] = 0u;
     uint64_t base;
     uint32_t lim;
     tile_range(in, n_dense, tile, per_seg, base, lim);
@@ -109,10 +111,10 @@ __global__ void __launch_bounds__(kSortThreads)
           a.x = a.y = 0;  // only pruning reads the amplitude
         live = apply_ops<KW, AT>(ops.n, sops, tab, k, a);
       }
-      if (live) atomicAdd(&h[digit_of(k, t, shift, cm)], 1u);
+      if (live) atomicAdd(&h[digit_of<RB>(k, t, shift, cm)], 1u);
     }
     __syncthreads();
-    hist[(uint64_t)threadIdx.x * n_tiles + tile] = h[threadIdx.x];
+    for (uint32_t d = threadIdx.x; d < R; d += blockDim.x) hist[(uint64_t)d * n_tiles + tile] = h[d];
     __syncthreads();
   }
 }
@@ -188,23 +190,26 @@ __global__ void __launch_bounds__(kScanThreads)
 // [w * 256, (w + 1) * 256) in order, 32 per round; ranks across warps and
 // digits come from shared-memory scans; the tile is then laid out in sorted
 // order in shared memory and written digit run by digit run.
-template <int KW, class AT, bool FIRST>
+template <int KW, class AT, bool FIRST, int RB>
 __global__ void __launch_bounds__(kSortThreads)
     k_rsort_scatter(Ctl* ctl, Arr in, const unsigned long long* n_ptr, uint32_t per_seg,
                     const __grid_constant__ OpList ops, uint32_t t, uint32_t shift,
                     uint64_t n_tiles, const unsigned int* offs, Arr out, uint64_t cm0,
                     uint64_t cm1) {
   typedef typename KT<KW>::T K;
+  constexpr uint32_t R = 1u << RB;
+  // Digits each thread scans: one when R <= 256 (threads past R hold none).
+  constexpr uint32_t kDpt = R > (uint32_t)kSortThreads ? R / (uint32_t)kSortThreads : 1u;
   const K cm = mk<KW>(cm0, cm1);
   extern __shared__ __align__(16) unsigned char smem[];
   K* skey = (K*)smem;
   AT* samp = (AT*)(smem + (size_t)kSortTile * sizeof(K));
-  unsigned char* sdig = (unsigned char*)(samp + kSortTile);
+  unsigned int* whist = (unsigned int*)(samp + kSortTile);  // [kSortWarps][R]
+  unsigned int* tbase = whist + kSortWarps * R;
+  unsigned int* gofs = tbase + R;
+  uint16_t* sdig = (uint16_t*)(gofs + R);
   __shared__ AT tab[FIRST ? kTabEntries : 1];
   __shared__ DevOp sops[FIRST ? kMaxOps : 1];
-  __shared__ unsigned int whist[kSortWarps][kRadix];
-  __shared__ unsigned int tbase[kRadix];
-  __shared__ unsigned int gofs[kRadix];
   __shared__ unsigned int wsum[kSortWarps];
   __shared__ unsigned int tile_live;
   if (ctl->err) return;
@@ -213,7 +218,7 @@ __global__ void __launch_bounds__(kSortThreads)
   const unsigned int lt = (1u << lane) - 1u;
   const uint64_t n_dense = in.seg_cnt ? 0ull : *n_ptr;
   for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    for (int w = 0; w < kSortWarps; ++w) whist[w][threadIdx.x] = 0u;
+    for (uint32_t i = threadIdx.x; i < kSortWarps * R; i += blockDim.x) whist[i] = 0u;
     uint64_t base;
     uint32_t lim;
     tile_range(in, n_dense, tile, per_seg, base, lim);
@@ -231,28 +236,38 @@ __global__ void __launch_bounds__(kSortThreads)
         if (FIRST) live = apply_ops<KW, AT>(ops.n, sops, tab, k[r], a[r]);
       }
       // Dead lanes get a value no live lane has, so they match only themselves.
-      d[r] = live ? digit_of(k[r], t, shift, cm) : (uint32_t)kRadix + lane;
+      d[r] = live ? digit_of<RB>(k[r], t, shift, cm) : R + lane;
       const unsigned int peers = __match_any_sync(0xffffffffu, d[r]);
       unsigned int before = 0u;
-      if (live) before = whist[warp][d[r]];
+      if (live) before = whist[warp * R + d[r]];
       __syncwarp();
-      if (live && (peers & lt) == 0u) whist[warp][d[r]] = before + (unsigned int)__popc(peers);
+      if (live && (peers & lt) == 0u) whist[warp * R + d[r]] = before + (unsigned int)__popc(peers);
       __syncwarp();
       rk[r] = before + (unsigned int)__popc(peers & lt);
     }
     __syncthreads();
-    // Per digit: exclusive scan over warps, then the tile's digit totals.
+    // Per digit (each thread kDpt consecutive digits): exclusive scan over
+    // warps, then an exclusive scan of the digit totals across the block.
     {
-      const unsigned int dg = threadIdx.x;
-      unsigned int run = 0u;
-      for (int w = 0; w < kSortWarps; ++w) {
-        const unsigned int c = whist[w][dg];
-        whist[w][dg] = run;
-        run += c;
+      const uint32_t d0 = threadIdx.x * kDpt;
+      unsigned int dtot[kDpt];
+      unsigned int mine = 0u;
+#pragma unroll
+      for (uint32_t j = 0; j < kDpt; ++j) {
+        const uint32_t dg = d0 + j;
+        unsigned int run = 0u;
+        if (dg < R) {
+          for (int w = 0; w < kSortWarps; ++w) {
+            const unsigned int c = whist[w * R + dg];
+            whist[w * R + dg] = run;
+            run += c;
+          }
+          gofs[dg] = offs[(uint64_t)dg * n_tiles + tile];
+        }
+        dtot[j] = run;
+        mine += run;
       }
-      gofs[dg] = offs[(uint64_t)dg * n_tiles + tile];
-      // Exclusive scan of the digit totals across the block.
-      unsigned int incl = run;
+      unsigned int incl = mine;
       for (int o = 1; o < 32; o <<= 1) {
         const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= (unsigned int)o) incl += y;
@@ -261,17 +276,22 @@ __global__ void __launch_bounds__(kSortThreads)
       __syncthreads();
       unsigned int wb = 0u;
       for (unsigned int w = 0; w < warp; ++w) wb += wsum[w];
-      tbase[dg] = wb + incl - run;
-      if (dg == (unsigned int)kRadix - 1u) tile_live = wb + incl;
+      unsigned int pre = wb + incl - mine;
+#pragma unroll
+      for (uint32_t j = 0; j < kDpt; ++j) {
+        if (d0 + j < R) tbase[d0 + j] = pre;
+        pre += dtot[j];
+      }
+      if (threadIdx.x == blockDim.x - 1u) tile_live = wb + incl;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
-      if (d[r] < (uint32_t)kRadix) {
-        const uint32_t lp = tbase[d[r]] + whist[warp][d[r]] + rk[r];
+      if (d[r] < R) {
+        const uint32_t lp = tbase[d[r]] + whist[warp * R + d[r]] + rk[r];
         skey[lp] = k[r];
         samp[lp] = a[r];
-        sdig[lp] = (unsigned char)d[r];
+        sdig[lp] = (uint16_t)d[r];
       }
     }
     __syncthreads();
@@ -373,35 +393,36 @@ __global__ void __launch_bounds__(kStreamThreads)
   }
 }
 
-template <int KW, class AT>
+template <int KW, class AT, int RB>
 size_t scatter_smem() {
-  return (size_t)kSortTile * (sizeof(typename KT<KW>::T) + sizeof(AT) + 1);
+  return (size_t)kSortTile * (sizeof(typename KT<KW>::T) + sizeof(AT) + 2) +
+         (size_t)4 * ((size_t)kSortWarps + 2) * ((size_t)1 << RB);
 }
 
-template <int KW, class AT, bool FIRST>
+template <int KW, class AT, bool FIRST, int RB>
 cudaError_t pass_t(const Launch& L, Ctl* ctl, Arr in, const unsigned long long* n_ptr,
                    uint32_t per_seg, uint64_t n_tiles, const OpList& ops, uint32_t t,
                    uint32_t shift, unsigned int* hist, unsigned int* part,
                    unsigned long long* n_dev, Arr out, const uint64_t* cm) {
   const uint64_t cm0 = cm ? cm[0] : 0ull, cm1 = cm ? cm[1] : 0ull;
   const int grid = (int)std::min<uint64_t>(n_tiles, (uint64_t)L.sm_count * 8);
-  k_rsort_hist<KW, AT, FIRST><<<grid, kSortThreads, 0, L.stream>>>(
+  k_rsort_hist<KW, AT, FIRST, RB><<<grid, kSortThreads, 0, L.stream>>>(
       ctl, in, n_ptr, per_seg, ops, t, shift, n_tiles, hist, cm0, cm1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const uint64_t m = n_tiles * (uint64_t)kRadix;
+  const uint64_t m = n_tiles << RB;
   const uint64_t blocks = std::min<uint64_t>(kScanBlocks, (m + 4095) / 4096);
   const uint64_t chunk = (m + blocks - 1) / blocks;
   k_scan_reduce<<<(int)blocks, kScanThreads, 0, L.stream>>>(ctl, hist, m, chunk, part);
   k_scan_apply<<<(int)blocks, kScanThreads, 0, L.stream>>>(ctl, hist, m, chunk, part, n_dev);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = scatter_smem<KW, AT>();
+  const size_t smem = scatter_smem<KW, AT, RB>();
   static std::atomic<unsigned long long> configured{0};  // opt-in above 48 KB, per device
-  e = ensure_smem_optin((const void*)k_rsort_scatter<KW, AT, FIRST>, smem, configured);
+  e = ensure_smem_optin((const void*)k_rsort_scatter<KW, AT, FIRST, RB>, smem, configured);
   if (e != cudaSuccess) return e;
   const int sgrid = (int)std::min<uint64_t>(n_tiles, (uint64_t)L.sm_count * 4);
-  k_rsort_scatter<KW, AT, FIRST><<<sgrid, kSortThreads, smem, L.stream>>>(
+  k_rsort_scatter<KW, AT, FIRST, RB><<<sgrid, kSortThreads, smem, L.stream>>>(
       ctl, in, n_ptr, per_seg, ops, t, shift, n_tiles, hist, out, cm0, cm1);
   return cudaGetLastError();
 }
@@ -409,22 +430,25 @@ cudaError_t pass_t(const Launch& L, Ctl* ctl, Arr in, const unsigned long long* 
 }  // namespace
 
 int sort_tile() { return kSortTile; }
-int sort_radix_bits() { return kRadixBits; }
+int sort_radix_bits() { return kRadixBitsDefault; }
+int sort_radix_bits_max() { return kRadixBitsMax; }
+bool sort_radix_bits_ok(int rb) { return rb == 6 || rb == 8 || rb == 10 || rb == 11; }
 uint32_t sort_merge_chunk_log2() { return kMergeChunkLog2; }
 size_t sort_part_entries() { return kScanBlocks; }
 
 #define SQS_SORT_DISPATCH(kw, amp32, M) \
   ((kw) == 1 ? ((amp32) ? M(1, float2) : M(1, double2)) : ((amp32) ? M(2, float2) : M(2, double2)))
 
-cudaError_t launch_rsort_pass(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in,
-                              const unsigned long long* n_ptr, uint32_t per_seg,
-                              uint64_t n_tiles, const OpList* first_ops, uint32_t t,
-                              uint32_t shift, unsigned int* hist, unsigned int* part,
-                              unsigned long long* n_dev, Arr out, const uint64_t* clear_mask) {
-  if (n_tiles == 0) return cudaSuccess;
+template <int RB>
+static cudaError_t pass_rb(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in,
+                           const unsigned long long* n_ptr, uint32_t per_seg, uint64_t n_tiles,
+                           const OpList* first_ops, uint32_t t, uint32_t shift, unsigned int* hist,
+                           unsigned int* part, unsigned long long* n_dev, Arr out,
+                           const uint64_t* clear_mask) {
   if (first_ops) {
-#define SQS_P1(KW_, AT_) \
-  pass_t<KW_, AT_, true>(L, ctl, in, n_ptr, per_seg, n_tiles, *first_ops, t, shift, hist, part, n_dev, out, clear_mask)
+#define SQS_P1(KW_, AT_)                                                                  \
+  pass_t<KW_, AT_, true, RB>(L, ctl, in, n_ptr, per_seg, n_tiles, *first_ops, t, shift, hist, \
+                             part, n_dev, out, clear_mask)
     return SQS_SORT_DISPATCH(kw, amp32, SQS_P1);
 #undef SQS_P1
   }
@@ -433,10 +457,36 @@ cudaError_t launch_rsort_pass(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr
     std::memset(&o, 0, sizeof(o));
     return o;
   }();
-#define SQS_P2(KW_, AT_) \
-  pass_t<KW_, AT_, false>(L, ctl, in, n_ptr, per_seg, n_tiles, kNone, t, shift, hist, part, n_dev, out, clear_mask)
+#define SQS_P2(KW_, AT_)                                                                 \
+  pass_t<KW_, AT_, false, RB>(L, ctl, in, n_ptr, per_seg, n_tiles, kNone, t, shift, hist, \
+                              part, n_dev, out, clear_mask)
   return SQS_SORT_DISPATCH(kw, amp32, SQS_P2);
 #undef SQS_P2
+}
+
+cudaError_t launch_rsort_pass(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in,
+                              const unsigned long long* n_ptr, uint32_t per_seg,
+                              uint64_t n_tiles, const OpList* first_ops, uint32_t t,
+                              uint32_t shift, unsigned int* hist, unsigned int* part,
+                              unsigned long long* n_dev, Arr out, const uint64_t* clear_mask,
+                              int radix_bits) {
+  if (n_tiles == 0) return cudaSuccess;
+  switch (radix_bits) {
+    case 6:
+      return pass_rb<6>(L, kw, amp32, ctl, in, n_ptr, per_seg, n_tiles, first_ops, t, shift, hist,
+                        part, n_dev, out, clear_mask);
+    case 8:
+      return pass_rb<8>(L, kw, amp32, ctl, in, n_ptr, per_seg, n_tiles, first_ops, t, shift, hist,
+                        part, n_dev, out, clear_mask);
+    case 10:
+      return pass_rb<10>(L, kw, amp32, ctl, in, n_ptr, per_seg, n_tiles, first_ops, t, shift,
+                         hist, part, n_dev, out, clear_mask);
+    case 11:
+      return pass_rb<11>(L, kw, amp32, ctl, in, n_ptr, per_seg, n_tiles, first_ops, t, shift,
+                         hist, part, n_dev, out, clear_mask);
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_rsort_merge(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in,

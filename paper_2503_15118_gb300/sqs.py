@@ -20,6 +20,7 @@ AMP_FP64, AMP_FP32 = 0, 1
 SIZING_EXACT, SIZING_LEARNED = 0, 2
 MERGE_AUTO, MERGE_HASH, MERGE_SORT, MERGE_CLUSTER, MERGE_TUNED, MERGE_PLAIN = 0, 4, 8, 16, 32, 64
 FUSE_OFF, FUSE_ALWAYS = 128, 256
+AUTOTUNE = 512
 (PERM_X, PERM_ADD_REG, PERM_SUB_REG, PERM_ADD_CONST, PERM_SUB_CONST, PERM_SWAP, PERM_MUL_ADD,
  PERM_MUL_CONST, PERM_DIV_XOR) = range(9)
 MAX_CTRL = 8     # controls inline in one permutation operation
@@ -49,7 +50,8 @@ class Stats(ctypes.Structure):
                 ("bytes_peak", ctypes.c_uint64), ("steps_expand", ctypes.c_uint64),
                 ("steps_hash", ctypes.c_uint64), ("steps_sort", ctypes.c_uint64),
                 ("steps_cluster", ctypes.c_uint64), ("steps_fold", ctypes.c_uint64),
-                ("runs_fused", ctypes.c_uint64), ("steps_fused", ctypes.c_uint64)]
+                ("runs_fused", ctypes.c_uint64), ("steps_fused", ctypes.c_uint64),
+                ("ops_deferred", ctypes.c_uint64)]
 
 
 PRED_FEATURES, PRED_HIDDEN, PRED_PARAMS = 16, 32, 1633
@@ -108,6 +110,8 @@ SIGNATURES = {
     "sqs_probabilities_sparse": (_S, [_P, _u32, _UP, _DP, _u64, _UP, _DP]),
     "sqs_state_set_wait_test": (_S, [_P, _u32, ctypes.c_int32]),
     "sqs_set_fp32_cancel": (_S, [_P, ctypes.c_double]),
+    "sqs_tune_export": (_S, [_P, ctypes.c_char_p, _u64, _UP]),
+    "sqs_tune_import": (_S, [_P, ctypes.c_char_p]),
     "sqs_nnz": (_S, [_P, _UP]),
     "sqs_peak_nnz": (_S, [_P, _UP]),
     "sqs_export": (_S, [_P, _UP, _DP, _u64, _UP]),
@@ -242,6 +246,20 @@ class State:
     # --- operations -------------------------------------------------------
     def reset(self):
         self._chk(self.lib.sqs_state_reset(self.h))
+
+    def tune_export(self):
+        """The autotuner's choices (SQS_AUTOTUNE) as a parsed JSON object."""
+        import json
+        n = ctypes.c_uint64()
+        self.lib.sqs_tune_export(self.h, None, 0, ctypes.byref(n))
+        buf = ctypes.create_string_buffer(int(n.value) + 1)
+        self._chk(self.lib.sqs_tune_export(self.h, buf, int(n.value) + 1, ctypes.byref(n)))
+        return json.loads(buf.value.decode())
+
+    def tune_import(self, obj):
+        import json
+        text = obj if isinstance(obj, str) else json.dumps(obj)
+        self._chk(self.lib.sqs_tune_import(self.h, text.encode()))
 
     def set_fp32_cancel(self, rho):
         self._chk(self.lib.sqs_set_fp32_cancel(self.h, float(rho)))

@@ -534,15 +534,18 @@ def test_fold_takes_config2_cancellations(sqs):
     assert compare_states(df, o.to_dict()) >= 1 - 1e-12
 
 
+@pytest.mark.parametrize("with_ops", [False, True])
 @pytest.mark.parametrize("wide", [False, True])
 @pytest.mark.parametrize("amp32", [False, True])
 @pytest.mark.parametrize("segmented", [False, True])
-def test_uncontrolled_fold_over_many_chunks(sqs, wide, amp32, segmented):
-    """The uncontrolled copy-pair fold (k_fold: bit-1 members skipped, bit-0
-    members compacted) on a ragged state of about 10^5 branches spanning many
+def test_uncontrolled_fold_over_many_chunks(sqs, wide, amp32, segmented, with_ops):
+    """The uncontrolled copy-pair fold (bit-1 members skipped, bit-0 members
+    compacted) on a ragged state of about 10^5 branches spanning many
     4096-slot chunks, on a dense input (after an expansion) and a segmented
     one (after a bucket merge), one- and two-word keys: bit for bit the state
-    of the plain merge, and equal to the oracle."""
+    of the plain merge, and equal to the oracle.  Without operations fused
+    into it (they are deferred past the fold) the staged kernel runs; a queued
+    prune keeps them in front, so the register-fed kernel runs them."""
     widths = [16, 8, 40] + ([40] if wide else [])
     rng = np.random.default_rng(77)
     table = rng.integers(0, 256, size=1 << 16).astype(np.uint8)
@@ -554,15 +557,50 @@ def test_uncontrolled_fold_over_many_chunks(sqs, wide, amp32, segmented):
               ("phase", ((1, 1, 1),), 0.3), ("ry", 2, 9, 0.7, ())]
     if segmented:
         gates += [("h", 1, 3, ())]                # no partners: bucket merge, segmented out
-    gates += [("x", 2, 11, ((0, 2, 1),)), ("h", 0, 15, ())]   # the fold
+    gates += [("x", 2, 11, ((0, 2, 1),))]
+    if with_ops:
+        gates += [("prune", 1e-15)]               # nothing is that small; keeps the run in front
+    gates += [("h", 0, 15, ())]                   # the fold
     circ = {"widths": widths, "eps": 1e-14, "tables": [table], "gates": gates}
     fast, plain = _plain_and_fast(sqs, circ, amp32)
     names = [r[0] for r in fast.trace_read()[0]]
     assert names.count("k_fold") == 1
+    assert (fast.stats()["ops_deferred"] > 0) == (not with_ops)
     if segmented:
         assert fast.stats()["steps_hash"] >= 1
     df, dp = fast.to_dict(), plain.to_dict()
     assert len(df) > 60000 and len(df) % 2048 != 0
+    assert set(df) == set(dp) and all(df[k] == dp[k] for k in df)
+    o = oracle.run_circuit(circ).to_dict()
+    if amp32:
+        assert compare_states(df, o, atol=ATOL32, band=ATOL32) >= 1 - 1e-6
+    else:
+        assert set(df) == set(o)
+        assert compare_states(df, o) >= 1 - 1e-12
+
+
+@pytest.mark.parametrize("amp32", [False, True])
+def test_ops_deferred_past_copy_pair_steps(sqs, amp32):
+    """Operations queued before a step that can only merge (a copy-pair
+    target) stay queued past it when they commute with it: none writes a
+    control of the step and none prunes.  The plain merge path defers the
+    same way, so the two states agree bit for bit; both equal the oracle,
+    which applies every operation in issue order."""
+    widths = [8, 8, 8]
+    gates = [("h", 0, b, ()) for b in range(6)]
+    ops = [("x", 1, 0, ()), ("add", 2, 1, 0, ()), ("phase", ((1, 1, 1),), 0.4),
+           ("x", 2, 3, ((1, 0, 1),)), ("swap", 1, 2, ())]
+    gates += ops + [("h", 0, 5, ())]              # fold, the five operations deferred
+    gates += [("h", 0, 4, ())]                     # again deferred (still queued)
+    gates += [("x", 1, 6, ()), ("h", 0, 3, ((1, 6, 1),))]   # writes the control: applied first
+    gates += [("x", 2, 7, ()), ("prune", 1e-13), ("h", 0, 2, ())]  # a queued prune: applied first
+    gates += [("h", 0, 1, ()), ("phase", ((2, 7, 1),), 1.1)]
+    circ = {"widths": widths, "eps": 1e-14, "tables": [], "gates": gates}
+    fast, plain = _plain_and_fast(sqs, circ, amp32)
+    sf, sp = fast.stats(), plain.stats()
+    assert sf["ops_deferred"] == sp["ops_deferred"] >= 5 + 5
+    assert sf["steps_fold"] >= 3 and sp["steps_fold"] == 0
+    df, dp = fast.to_dict(), plain.to_dict()
     assert set(df) == set(dp) and all(df[k] == dp[k] for k in df)
     o = oracle.run_circuit(circ).to_dict()
     if amp32:
