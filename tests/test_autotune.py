@@ -36,17 +36,40 @@ def _same(x, y):
     return all(np.array_equal(p, q) for p, q in zip(x, y))
 
 
+def _merge_circuit(wide, n_gates, seed):
+    """A merge-heavy random circuit whose state stays at or below 2^16
+    branches: random gates over 16 qubits, or (wide) over 13 qubits plus a
+    64-bit register that takes three CNOT copies half way through, so the
+    keys need two words and the copied bits keep up to 8x more branches
+    apart."""
+    base = [5, 5, 3] if wide else [6, 6, 4]
+    c = W.random_circuit(base, n_gates, seed=seed, kinds=("x", "cx", "ccx", "ry", "phase", "h", "add"))
+    gates = list(c["gates"])
+    widths = list(base)
+    if wide:
+        widths.append(64)
+        half = len(gates) // 2
+        gates = gates[:half] + [("x", 3, 20 + 3 * i, ((i, i, 1),)) for i in range(3)] + gates[half:]
+    return {"widths": widths, "eps": 1e-14, "tables": [], "gates": gates}
+
+
+def _runs(wide, seed):
+    """Fused interference runs; about 0.3-3 million branches."""
+    return _run_circuit([40, 40, 6] if wide else [12, 12, 6], seed, n_runs=3, run_len=6, ry_reg=True)
+
+
 @pytest.mark.parametrize("mode", ["sort_merge", "fused_runs"])
-@pytest.mark.parametrize("widths", [[16, 16, 16, 16], [40, 40, 6]])
-def test_tuning_walks_every_candidate_bit_identically(sqs, mode, widths):
+@pytest.mark.parametrize("wide", [False, True])
+def test_tuning_walks_every_candidate_bit_identically(sqs, mode, wide):
     if mode == "sort_merge":
-        circ = W.random_circuit(widths, 120, seed=5, kinds=("x", "cx", "ccx", "ry", "phase", "h", "add"))
+        circ = _merge_circuit(wide, 120, seed=9)
         base = sqs.MERGE_SORT
     else:
-        circ = _run_circuit(widths, 3 + sum(widths), n_runs=3, run_len=6, ry_reg=True)
+        circ = _runs(wide, 3 + 86 * wide)
         base = sqs.FUSE_ALWAYS
     ref = sqs.run_circuit(circ, merge=base)
     want = _exact(ref)
+    assert ref.nnz() > 2048
     ref.close()
     st = sqs.State(circ["widths"], eps=circ["eps"], merge=base | sqs.AUTOTUNE)
     for rep in range(10):  # 4 candidates x 2 samples, then the choice
@@ -79,8 +102,8 @@ def test_tuning_walks_every_candidate_bit_identically(sqs, mode, widths):
 def test_cache_file_round_trip(sqs, tmp_path, monkeypatch):
     path = tmp_path / "tune.json"
     monkeypatch.setenv("SQS_TUNE_CACHE", str(path))
-    widths = [16, 16, 16, 16]
-    circ = W.random_circuit(widths, 80, seed=9, kinds=("x", "cx", "ry", "h", "phase"))
+    circ = _merge_circuit(False, 120, seed=9)
+    widths = circ["widths"]
     st = sqs.State(widths, eps=circ["eps"], merge=sqs.MERGE_SORT | sqs.AUTOTUNE)
     for _ in range(10):
         st.reset()
@@ -107,13 +130,13 @@ def test_cache_file_round_trip(sqs, tmp_path, monkeypatch):
 
 @pytest.mark.parametrize("bits", [6, 10, 11])
 @pytest.mark.parametrize("amp32", [False, True])
-@pytest.mark.parametrize("widths", [[16, 16, 16, 16], [40, 40, 6]])
-def test_every_digit_width_sorts_identically(sqs, monkeypatch, bits, amp32, widths):
+@pytest.mark.parametrize("wide", [False, True])
+def test_every_digit_width_sorts_identically(sqs, monkeypatch, bits, amp32, wide):
     """Each supported digit width, forced for every sort (SQS_SORT_BITS): the
     sort merge, fused runs and the sorted export give the state of 8-bit
     digits bit for bit."""
-    circ = W.random_circuit(widths, 150, seed=13 + bits, kinds=("x", "cx", "ccx", "ry", "phase", "h", "add"))
-    runs = _run_circuit(widths, 21 + bits, n_runs=3, run_len=6, ry_reg=True)
+    circ = _merge_circuit(wide, 150, seed=13 + bits)
+    runs = _runs(wide, 21 + bits)
     want = []
     for c, merge in ((circ, sqs.MERGE_SORT), (runs, sqs.FUSE_ALWAYS)):
         ref = sqs.run_circuit(c, amp32=amp32, merge=merge)
