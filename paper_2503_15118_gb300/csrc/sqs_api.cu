@@ -706,8 +706,9 @@ sqs_status run_binned(sqs_state* st, const Gate1& g, uint64_t B1, int64_t rec_id
 sqs_status run_hashed(sqs_state* st, const Gate1& g, double est_in, int64_t rec_idx) {
   sqs_status s;
   const OpList& L = st->ops_buf;
-  // A capture sized its buckets for the static bound at the larger fill.
-  const uint64_t target = st->capturing ? kBucketFillLarge : bucket_fill(st->ub);
+  // A capture sized its buckets for the static bound at the eager fill, so a
+  // replay partitions exactly as eager issue does.
+  const uint64_t target = bucket_fill(st->ub);
   uint64_t want =
       est_in < 0 ? st->ub : std::min<uint64_t>(st->ub, (uint64_t)(est_in * 1.2) + 1);
   // The per-CTA bucket merge is the default (measured faster at every size

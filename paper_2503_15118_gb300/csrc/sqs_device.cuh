@@ -76,6 +76,34 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 __device__ __forceinline__ uint64_t khash(uint64_t k) { return mix64(k); }
+
+// Visiting order of the parts of a segment.  Kernels hand out the parts of
+// segmented arrays round-robin (part u of the array is part u & (2^l - 1) of
+// segment u >> l); with that order and a grid that is a multiple of 2^l every
+// CTA would always take the same part of each segment, and segments that are
+// not full keep their live branches in their first parts, so the CTAs of the
+// last parts would idle.  spread(sg, l) is an l-bit multiplicative hash of
+// the segment index (Knuth's golden-ratio constant); XOR-ing it into the part
+// index permutes the parts of each segment, so each CTA meets every part
+// equally often.
+__device__ __forceinline__ uint64_t spread(uint64_t sg, uint32_t l) {
+  return l ? (sg * 0x9E3779B97F4A7C15ull) >> (64u - l) : 0ull;
+}
+
+// Part visited at round-robin position u (2^l parts per segment): a
+// permutation of the parts of each segment.
+__device__ __forceinline__ uint64_t spread_visit(uint64_t u, uint32_t l) {
+  if (!l) return u;
+  const uint64_t sg = u >> l;
+  return (sg << l) | ((u ^ spread(sg, l)) & ((1ull << l) - 1ull));
+}
+
+// log2 of the parts per segment when that is a power of two, else 0 (the
+// identity order: spread_visit permutes within aligned groups of 2^l parts,
+// which must tile the part range exactly).
+__device__ __forceinline__ uint32_t log2_pow2(uint32_t x) {
+  return (x == 0u || (x & (x - 1u))) ? 0u : 31u - (uint32_t)__clz(x);
+}
 __device__ __forceinline__ uint64_t khash(u128 k) {
   return mix64((uint64_t)k ^ mix64((uint64_t)(k >> 64) + 0x9e3779b97f4a7c15ull));
 }

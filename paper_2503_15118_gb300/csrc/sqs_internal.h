@@ -98,6 +98,7 @@ struct Ctl {
   unsigned long long items;      // fused run: branches of its input (after the queued run)
   unsigned long long stage[16];  // fused run: branches after each of its operations
   unsigned int buckets;          // bucket merge: buckets the partition filled
+  unsigned int pair_next;        // bucket merge: next bucket a pair CTA takes (the partition zeroes it)
 };
 
 constexpr unsigned int kErrCapacity = 1u;  // output array too small

@@ -47,6 +47,52 @@ __global__ void k_init(Ctl* ctl, Arr a, int slot) {
 
 // ---------------------------------------------------------------------------
 
+// Visits this CTA's units of `unit` slots of `in` -- slices of segments, or
+// of the dense array -- and calls body(base, lim) with every thread for each
+// unit holding live slots (lim > 0).  Units are handed out round-robin (unit
+// u to CTA u mod gridDim.x), in spread order over the parts of a segment.
+// For a segmented array the CTA checks blockDim.x of its candidate units at
+// once, one count load per thread, and lists the non-empty ones in shared
+// memory (list: blockDim.x entries): the count loads of empty units overlap
+// instead of forming a chain, which matters when the segment list is sized
+// for a bound far above the count (a graph's static bound).
+template <class F>
+__device__ __forceinline__ void for_units(const Arr& in, uint64_t n_dense, uint32_t unit,
+                                          uint16_t* list, unsigned int* n_list, F&& body) {
+  if (!in.seg_cnt) {
+    const uint64_t units = (n_dense + unit - 1) / unit;
+    for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
+      const uint64_t base = u * unit;
+      body(base, (uint32_t)(n_dense - base < unit ? n_dense - base : unit));
+    }
+    return;
+  }
+  const uint32_t per_seg = ((1u << in.seg_log2) + unit - 1) / unit;
+  const uint32_t l = log2_pow2(per_seg);
+  const uint64_t units = (uint64_t)in.n_seg * per_seg;
+  for (uint64_t k0 = 0; blockIdx.x + k0 * gridDim.x < units; k0 += blockDim.x) {
+    if (threadIdx.x == 0) *n_list = 0u;
+    __syncthreads();
+    const uint64_t u = blockIdx.x + (k0 + threadIdx.x) * gridDim.x;
+    if (u < units) {
+      const uint64_t v = spread_visit(u, l);
+      const uint32_t sg = (uint32_t)(v / per_seg);
+      const uint32_t off = (uint32_t)(v - (uint64_t)sg * per_seg) * unit;
+      if (off < in.seg_cnt[sg]) list[atomicAdd(n_list, 1u)] = (uint16_t)threadIdx.x;
+    }
+    __syncthreads();
+    const uint32_t n = *n_list;
+    for (uint32_t i = 0; i < n; ++i) {
+      const uint64_t v = spread_visit(blockIdx.x + (k0 + list[i]) * gridDim.x, l);
+      const uint32_t sg = (uint32_t)(v / per_seg);
+      const uint32_t off = (uint32_t)(v - (uint64_t)sg * per_seg) * unit;
+      const uint32_t cnt = in.seg_cnt[sg];
+      body(((uint64_t)sg << in.seg_log2) + off, cnt - off < unit ? cnt - off : unit);
+    }
+    __syncthreads();  // the list is rebuilt for the next candidates
+  }
+}
+
 // Op-major over kApplyILP branches per thread: each operation's descriptor
 // is read once for four branches (the interpreter's instruction count, not
 // memory, bounds a long run on a large state).
@@ -62,31 +108,11 @@ __global__ void __launch_bounds__(kStreamThreads)
   load_ops(ops, sops, tab);
   const uint64_t n_dense = ctl->cnt[slot];
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&ctl->peak, n_dense);
+  __shared__ uint16_t ulist[kStreamThreads];
+  __shared__ unsigned int n_ulist;
   // Units of kApplyILP * blockDim slots: a slice of a segment, or of the
   // dense array.
-  const uint32_t unit = kApplyILP * blockDim.x;
-  uint32_t per_seg = 1;
-  uint64_t units;
-  if (a.seg_cnt) {
-    per_seg = ((1u << a.seg_log2) + unit - 1) / unit;
-    units = (uint64_t)a.n_seg * per_seg;
-  } else {
-    units = (n_dense + unit - 1) / unit;
-  }
-  for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    uint64_t base;
-    uint32_t lim;
-    if (a.seg_cnt) {
-      const uint32_t sg = (uint32_t)(u / per_seg);
-      const uint32_t off = (uint32_t)(u - (uint64_t)sg * per_seg) * unit;
-      const uint32_t cnt = a.seg_cnt[sg];
-      if (off >= cnt) continue;
-      base = ((uint64_t)sg << a.seg_log2) + off;
-      lim = cnt - off < unit ? cnt - off : unit;
-    } else {
-      base = u * unit;
-      lim = (uint32_t)(n_dense - base < unit ? n_dense - base : unit);
-    }
+  for_units(a, n_dense, kApplyILP * blockDim.x, ulist, &n_ulist, [&](uint64_t base, uint32_t lim) {
     K k[kApplyILP];
     AT v[kApplyILP];
     bool live[kApplyILP];
@@ -110,7 +136,7 @@ __global__ void __launch_bounds__(kStreamThreads)
         if (TA) ((AT*)a.amp)[base + j] = v[q];
       }
     }
-  }
+  });
 }
 
 // Input segment (or dense chunk) c of 2^out.seg_log2 slots is compacted into
@@ -201,34 +227,15 @@ __global__ void __launch_bounds__(kStreamThreads)
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     atomicMax(&ctl->peak, n_dense);
     ctl->buckets = n_buckets;
+    ctl->pair_next = 0u;
   }
   const K bmask = bit_mask<KW>(g.t);
   const uint32_t C = 1u << bk.seg_log2;
+  __shared__ uint16_t ulist[kStreamThreads];
+  __shared__ unsigned int n_ulist;
   // Units of kPartILP * blockDim slots: a slice of a segment, or of the dense
   // array.
-  const uint32_t unit = kPartILP * blockDim.x;
-  uint32_t per_seg = 1;
-  uint64_t units;
-  if (in.seg_cnt) {
-    per_seg = ((1u << in.seg_log2) + unit - 1) / unit;
-    units = (uint64_t)in.n_seg * per_seg;
-  } else {
-    units = (n_dense + unit - 1) / unit;
-  }
-  for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    uint64_t base;
-    uint32_t lim;
-    if (in.seg_cnt) {
-      const uint32_t sg = (uint32_t)(u / per_seg);
-      const uint32_t off = (uint32_t)(u - (uint64_t)sg * per_seg) * unit;
-      const uint32_t cnt = in.seg_cnt[sg];
-      if (off >= cnt) continue;
-      base = ((uint64_t)sg << in.seg_log2) + off;
-      lim = cnt - off < unit ? cnt - off : unit;
-    } else {
-      base = u * unit;
-      lim = (uint32_t)(n_dense - base < unit ? n_dense - base : unit);
-    }
+  for_units(in, n_dense, kPartILP * blockDim.x, ulist, &n_ulist, [&](uint64_t base, uint32_t lim) {
     K k[kPartILP];
     AT v[kPartILP];
     bool live[kPartILP];
@@ -265,15 +272,18 @@ __global__ void __launch_bounds__(kStreamThreads)
         raise_err(ctl, kErrBucket, seq, (unsigned long long)pos[q] + 1);
       }
     }
-  }
+  });
 }
 
-// One CTA per bucket.  Shared memory: keys[C], amps[C] (storage type),
-// slots[2C] (0 = empty, else index + 1), partner[C].
-constexpr int kPairThreads = 256;
+// Persistent: a resident wave of CTAs takes the buckets the partition used
+// (ctl->buckets, from the device count) one by one, so the launch does not
+// grow with the host's bucket bound (a graph sizes it for a static bound).
+// Shared memory: keys[C], amps[C] (storage type), slots[2C] (0 = empty, else
+// index + 1), partner[C].
+constexpr int kPairThreads = 512;
 
 template <int KW, class AT>
-__global__ void __launch_bounds__(kPairThreads)
+__global__ void __launch_bounds__(kPairThreads, 3)
     k_pair(Ctl* ctl, Gate1 g, Arr bk, Arr out, int out_slot, uint32_t seq) {
   typedef typename KT<KW>::T K;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -286,129 +296,147 @@ __global__ void __launch_bounds__(kPairThreads)
   unsigned int* slot = (unsigned int*)(smem + (size_t)C * (sizeof(K) + sizeof(AT)));
   int* partner = (int*)(slot + S);
 
-  const uint32_t b = blockIdx.x;
-  if (b == 0 && threadIdx.x == 0) ctl->cnt[(out_slot + 1) & 3] = 0;
-  if (b >= ctl->buckets) {  // a bucket the partition did not use
-    if (threadIdx.x == 0) out.seg_cnt[b] = 0u;
-    return;
-  }
-  const uint32_t n = bk.seg_cnt[b];
-  if (n > C) return;  // overflow already flagged by the partition
-  const uint64_t base = (uint64_t)b << bk.seg_log2;
-#pragma unroll 4
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    skey[i] = ld_key<KW>(bk, base + i);
-    samp[i] = ((const AT*)bk.amp)[base + i];
-    partner[i] = -1;
-  }
-  for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) slot[i] = 0u;
-  if (threadIdx.x == 0) fill = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->cnt[(out_slot + 1) & 3] = 0;
+  // Buckets the partition did not use (it sized them from the device count)
+  // stay empty.
+  const uint32_t nb = ctl->buckets;
+  for (uint32_t b = nb + blockIdx.x * blockDim.x + threadIdx.x; b < bk.n_seg;
+       b += gridDim.x * blockDim.x)
+    out.seg_cnt[b] = 0u;
+  // Buckets are taken one at a time from a counter (ctl->pair_next), so a CTA
+  // that drew small buckets takes more of them; the next index is drawn while
+  // the current bucket is processed.
+  __shared__ uint32_t next_b;
+  if (threadIdx.x == 0) next_b = atomicAdd(&ctl->pair_next, 1u);
   __syncthreads();
-  if (threadIdx.x == 0) bk.seg_cnt[b] = 0u;  // bucket is clean for the next use
-
-  const K bmask = bit_mask<KW>(g.t);
-  const K cmask = mk<KW>(g.cmask[0], g.cmask[1]);
-  const K cval = mk<KW>(g.cval[0], g.cval[1]);
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const K k = skey[i];
-    if ((k & cmask) != cval) continue;  // passes through unchanged
-    const K p = k & ~bmask;
-    uint32_t h = (uint32_t)khash(p) & (S - 1u);
-    // At most C entries live in 2C slots, so a free slot or the partner is
-    // always found within S probes; the bound only guards against misuse.
-    uint32_t probe = 0;
-    for (; probe < S; ++probe) {
-      const unsigned int old = atomicCAS(&slot[h], 0u, i + 1u);
-      if (old == 0u) break;
-      const uint32_t j = old - 1u;
-      if ((skey[j] & ~bmask) == p) {
-        partner[i] = (int)j;
-        partner[j] = (int)i;
-        break;
-      }
-      h = (h + 1u) & (S - 1u);
+  for (uint32_t b = next_b; b < nb; b = next_b) {
+    uint32_t drawn = 0u;
+    if (threadIdx.x == 0) drawn = atomicAdd(&ctl->pair_next, 1u);
+    const uint32_t n = bk.seg_cnt[b];
+    if (n > C) {  // overflow already flagged by the partition
+      __syncthreads();  // every thread has read next_b
+      if (threadIdx.x == 0) next_b = drawn;
+      __syncthreads();
+      continue;
     }
-    if (probe == S) raise_err(ctl, kErrProbe, seq, 0);
-  }
-  __syncthreads();
+    const uint64_t base = (uint64_t)b << bk.seg_log2;
+  #pragma unroll 4
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      skey[i] = ld_key<KW>(bk, base + i);
+      samp[i] = ((const AT*)bk.amp)[base + i];
+      partner[i] = -1;
+    }
+    for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) slot[i] = 0u;
+    if (threadIdx.x == 0) fill = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) bk.seg_cnt[b] = 0u;  // bucket is clean for the next use
 
-  // Emitters: branches the controls leave alone, unpaired branches and the
-  // bit-0 member of each pair.  Listing them first (in the probe table, which
-  // is free now) keeps every lane of the arithmetic below busy.
-  unsigned int* emit = slot;
-  const uint32_t lane = threadIdx.x & 31u;
-  const unsigned int lt = (1u << lane) - 1u;
-  if (threadIdx.x == 0) fill = 0;
-  __shared__ unsigned int n_emit;
-  if (threadIdx.x == 0) n_emit = 0;
-  __syncthreads();
-  const uint32_t rounds_in = (n + blockDim.x - 1u) / blockDim.x;
-  for (uint32_t r = 0; r < rounds_in; ++r) {
-    const uint32_t i = r * blockDim.x + threadIdx.x;
-    bool e = false;
-    if (i < n) {
+    const K bmask = bit_mask<KW>(g.t);
+    const K cmask = mk<KW>(g.cmask[0], g.cmask[1]);
+    const K cval = mk<KW>(g.cval[0], g.cval[1]);
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
       const K k = skey[i];
-      e = (k & cmask) != cval || !((k & bmask) != (K)0 && partner[i] >= 0);
+      if ((k & cmask) != cval) continue;  // passes through unchanged
+      const K p = k & ~bmask;
+      uint32_t h = (uint32_t)khash(p) & (S - 1u);
+      // At most C entries live in 2C slots, so a free slot or the partner is
+      // always found within S probes; the bound only guards against misuse.
+      uint32_t probe = 0;
+      for (; probe < S; ++probe) {
+        const unsigned int old = atomicCAS(&slot[h], 0u, i + 1u);
+        if (old == 0u) break;
+        const uint32_t j = old - 1u;
+        if ((skey[j] & ~bmask) == p) {
+          partner[i] = (int)j;
+          partner[j] = (int)i;
+          break;
+        }
+        h = (h + 1u) & (S - 1u);
+      }
+      if (probe == S) raise_err(ctl, kErrProbe, seq, 0);
     }
-    const unsigned int ball = __ballot_sync(0xffffffffu, e);
-    unsigned int wb = 0;
-    if (lane == 0 && ball) wb = atomicAdd(&n_emit, (unsigned int)__popc(ball));
-    wb = __shfl_sync(0xffffffffu, wb, 0);
-    if (e) emit[wb + __popc(ball & lt)] = i;
-  }
-  __syncthreads();
-  const uint32_t ne = n_emit;
+    __syncthreads();
 
-  const uint64_t obase = (uint64_t)b << out.seg_log2;
-  const uint32_t rounds = (ne + blockDim.x - 1u) / blockDim.x;
-  for (uint32_t r = 0; r < rounds; ++r) {
-    const uint32_t q = r * blockDim.x + threadIdx.x;
-    bool keep0 = false, keep1 = false;
-    K k0 = 0, k1 = 0;
-    AT o0, o1;
-    if (q < ne) {
-      const uint32_t i = emit[q];
-      const K k = skey[i];
-      const AT ai = samp[i];
-      if ((k & cmask) != cval) {
-        keep0 = true;  // controls not met: the branch is unchanged
-        k0 = k;
-        o0 = ai;
-      } else {
-        const bool kt = (k & bmask) != (K)0;
-        const int j = partner[i];
-        k0 = k & ~bmask;
-        k1 = k | bmask;
-        const uint64_t av = g.mode == 1 ? get_field(k0, g.ang_off, g.ang_w) : 0ull;
-        if (!kt)
-          children<AT>(g, av, true, ai, j >= 0, j >= 0 ? samp[j] : ai, o0, o1);
-        else
-          children<AT>(g, av, false, ai, true, ai, o0, o1);
-        keep0 = keep_amp(o0, g.eps, g.epsf, g.eps2);
-        keep1 = keep_amp(o1, g.eps, g.epsf, g.eps2);
+    // Emitters: branches the controls leave alone, unpaired branches and the
+    // bit-0 member of each pair.  Listing them first (in the probe table, which
+    // is free now) keeps every lane of the arithmetic below busy.
+    unsigned int* emit = slot;
+    const uint32_t lane = threadIdx.x & 31u;
+    const unsigned int lt = (1u << lane) - 1u;
+    if (threadIdx.x == 0) fill = 0;
+    __shared__ unsigned int n_emit;
+    if (threadIdx.x == 0) n_emit = 0;
+    __syncthreads();
+    const uint32_t rounds_in = (n + blockDim.x - 1u) / blockDim.x;
+    for (uint32_t r = 0; r < rounds_in; ++r) {
+      const uint32_t i = r * blockDim.x + threadIdx.x;
+      bool e = false;
+      if (i < n) {
+        const K k = skey[i];
+        e = (k & cmask) != cval || !((k & bmask) != (K)0 && partner[i] >= 0);
+      }
+      const unsigned int ball = __ballot_sync(0xffffffffu, e);
+      unsigned int wb = 0;
+      if (lane == 0 && ball) wb = atomicAdd(&n_emit, (unsigned int)__popc(ball));
+      wb = __shfl_sync(0xffffffffu, wb, 0);
+      if (e) emit[wb + __popc(ball & lt)] = i;
+    }
+    __syncthreads();
+    const uint32_t ne = n_emit;
+
+    const uint64_t obase = (uint64_t)b << out.seg_log2;
+    const uint32_t rounds = (ne + blockDim.x - 1u) / blockDim.x;
+    for (uint32_t r = 0; r < rounds; ++r) {
+      const uint32_t q = r * blockDim.x + threadIdx.x;
+      bool keep0 = false, keep1 = false;
+      K k0 = 0, k1 = 0;
+      AT o0, o1;
+      if (q < ne) {
+        const uint32_t i = emit[q];
+        const K k = skey[i];
+        const AT ai = samp[i];
+        if ((k & cmask) != cval) {
+          keep0 = true;  // controls not met: the branch is unchanged
+          k0 = k;
+          o0 = ai;
+        } else {
+          const bool kt = (k & bmask) != (K)0;
+          const int j = partner[i];
+          k0 = k & ~bmask;
+          k1 = k | bmask;
+          const uint64_t av = g.mode == 1 ? get_field(k0, g.ang_off, g.ang_w) : 0ull;
+          if (!kt)
+            children<AT>(g, av, true, ai, j >= 0, j >= 0 ? samp[j] : ai, o0, o1);
+          else
+            children<AT>(g, av, false, ai, true, ai, o0, o1);
+          keep0 = keep_amp(o0, g.eps, g.epsf, g.eps2);
+          keep1 = keep_amp(o1, g.eps, g.epsf, g.eps2);
+        }
+      }
+      const unsigned int b0 = __ballot_sync(0xffffffffu, keep0);
+      const unsigned int b1 = __ballot_sync(0xffffffffu, keep1);
+      const unsigned int tot = __popc(b0) + __popc(b1);
+      unsigned int wbase = 0;
+      if (lane == 0 && tot) wbase = atomicAdd(&fill, tot);
+      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      if (keep0) {
+        const uint64_t pos = obase + wbase + __popc(b0 & lt);
+        st_key<KW>(out, pos, k0);
+        ((AT*)out.amp)[pos] = o0;
+      }
+      if (keep1) {
+        const uint64_t pos = obase + wbase + __popc(b0) + __popc(b1 & lt);
+        st_key<KW>(out, pos, k1);
+        ((AT*)out.amp)[pos] = o1;
       }
     }
-    const unsigned int b0 = __ballot_sync(0xffffffffu, keep0);
-    const unsigned int b1 = __ballot_sync(0xffffffffu, keep1);
-    const unsigned int tot = __popc(b0) + __popc(b1);
-    unsigned int wbase = 0;
-    if (lane == 0 && tot) wbase = atomicAdd(&fill, tot);
-    wbase = __shfl_sync(0xffffffffu, wbase, 0);
-    if (keep0) {
-      const uint64_t pos = obase + wbase + __popc(b0 & lt);
-      st_key<KW>(out, pos, k0);
-      ((AT*)out.amp)[pos] = o0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      out.seg_cnt[b] = fill;
+      if (fill) atomicAdd(&ctl->cnt[out_slot], (unsigned long long)fill);
+      next_b = drawn;
     }
-    if (keep1) {
-      const uint64_t pos = obase + wbase + __popc(b0) + __popc(b1 & lt);
-      st_key<KW>(out, pos, k1);
-      ((AT*)out.amp)[pos] = o1;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    out.seg_cnt[b] = fill;
-    if (fill) atomicAdd(&ctl->cnt[out_slot], (unsigned long long)fill);
+    __syncthreads();  // fill, next_b and the tables are reused by the next bucket
   }
 }
 
@@ -464,7 +492,8 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     uint64_t ibase, cnt;
     if (in.seg_cnt) {
       const uint64_t sg = c >> cps_log2;
-      const uint64_t off = (c & ((1ull << cps_log2) - 1ull)) << kExpandChunkLog2;
+      const uint64_t off = ((c ^ spread(sg, cps_log2)) & ((1ull << cps_log2) - 1ull))
+                           << kExpandChunkLog2;
       const uint64_t n_sg = sg < in.n_seg ? in.seg_cnt[sg] : 0;
       ibase = (sg << in.seg_log2) + off;
       cnt = n_sg > off ? (n_sg - off < chunk ? n_sg - off : chunk) : 0;
@@ -638,7 +667,8 @@ __global__ void __launch_bounds__(kStreamThreads, 3)
     uint64_t ibase, cnt;
     if (in.seg_cnt) {
       const uint64_t sg = c >> cps_log2;
-      const uint64_t off = (c & ((1ull << cps_log2) - 1ull)) << kExpandChunkLog2;
+      const uint64_t off = ((c ^ spread(sg, cps_log2)) & ((1ull << cps_log2) - 1ull))
+                           << kExpandChunkLog2;
       const uint64_t n_sg = sg < in.n_seg ? in.seg_cnt[sg] : 0;
       ibase = (sg << in.seg_log2) + off;
       cnt = n_sg > off ? (n_sg - off < chunk ? n_sg - off : chunk) : 0;
@@ -788,8 +818,9 @@ __global__ void __launch_bounds__(kStreamThreads, 3)
 
 // ---------------------------------------------------------------------------
 // Staged input stream (TMA bulk copies, double-buffered).  The input is
-// walked in units of kUnit slots: slice (G & 3) of chunk (G >> 2) of
-// 2^kExpandChunkLog2 slots (a dense range, or a slice of one segment).  A
+// walked in units of kUnit slots: slice (G ^ spread(G >> 2, 2)) & 3 of chunk
+// G >> 2 of 2^kExpandChunkLog2 slots (a dense range, or a slice of one
+// segment).  A
 // CTA takes units G = blockIdx.x, + gridDim.x, ...; one elected thread copies
 // unit i + 2 into the stage buffer unit i has just released, with
 // cp.async.bulk on that buffer's mbarrier, while every thread computes on
@@ -812,7 +843,8 @@ __device__ __forceinline__ UnitRange unit_range(const Arr& in, uint64_t n_dense,
   uint64_t ibase, cnt;
   if (in.seg_cnt) {
     const uint64_t sg = c >> cps_log2;
-    const uint64_t off = (c & ((1ull << cps_log2) - 1ull)) << kExpandChunkLog2;
+    const uint64_t off = ((c ^ spread(sg, cps_log2)) & ((1ull << cps_log2) - 1ull))
+                         << kExpandChunkLog2;
     const uint64_t n_sg = sg < in.n_seg ? in.seg_cnt[sg] : 0;
     ibase = (sg << in.seg_log2) + off;
     cnt = n_sg > off ? (n_sg - off < chunk ? n_sg - off : chunk) : 0;
@@ -820,7 +852,8 @@ __device__ __forceinline__ UnitRange unit_range(const Arr& in, uint64_t n_dense,
     ibase = c << kExpandChunkLog2;
     cnt = ibase >= n_dense ? 0 : (n_dense - ibase < chunk ? n_dense - ibase : chunk);
   }
-  const uint64_t off = (G & ((1ull << kUnitsPerChunkLog2) - 1ull)) << kUnitLog2;
+  const uint64_t off = ((G ^ spread(c, kUnitsPerChunkLog2)) & ((1ull << kUnitsPerChunkLog2) - 1ull))
+                       << kUnitLog2;
   UnitRange r;
   r.base = ibase + off;
   r.cnt = (uint32_t)(cnt > off ? (cnt - off < kUnit ? cnt - off : kUnit) : 0);
@@ -889,9 +922,11 @@ __device__ __forceinline__ bool staged_stream(Ctl* ctl, const Arr& in, uint64_t 
   const uint32_t cps_log2 = in.seg_cnt ? in.seg_log2 - kExpandChunkLog2 : 0u;
   // A dense input covers only the units its device count reaches (the host
   // sized n_chunks from a bound, which may be far above it, as in a graph).
+  // Whole chunks: the slices of the last chunk are visited in spread order.
   uint64_t n_units = n_chunks << kUnitsPerChunkLog2;
   if (!in.seg_cnt) {
-    const uint64_t need = (n_dense + kUnit - 1) >> kUnitLog2;
+    const uint64_t need = ((n_dense + (1ull << kExpandChunkLog2) - 1) >> kExpandChunkLog2)
+                          << kUnitsPerChunkLog2;
     if (need < n_units) n_units = need;
   }
   // Units with no live slot (the tails of segments that are not full) are
@@ -967,6 +1002,8 @@ static cudaError_t resident_per_sm(Kern kern, size_t smem, int* per_sm_cache, in
 // operation (measured faster there: the input arrives by bulk copy while the
 // previous unit computes; with a long fused run the per-unit barriers cost
 // more than the loads they hide, and the register-fed kernels above win).
+// They carry no operation interpreter: without its tables and registers more
+// CTAs fit an SM.
 // Constant target bit: no branch has a partner, so each controlled branch
 // expands into its two children directly (no partition, no pairing).
 // Copy-pair fold with controls (g.fold_sign != 0): every controlled branch has
@@ -976,18 +1013,15 @@ static cudaError_t resident_per_sm(Kern kern, size_t smem, int* per_sm_cache, in
 // stream; the output is dense: each block reserves every round's outputs with
 // one atomic.
 template <int KW, class AT>
-__global__ void __launch_bounds__(kStreamThreads, 3)
+__global__ void __launch_bounds__(kStreamThreads, 4)
     k_expand_staged(Ctl* ctl, Arr in, int in_slot, uint64_t n_chunks, Arr out, int out_slot,
-             const __grid_constant__ OpList ops, Gate1 g, uint32_t seq) {
+                    Gate1 g, uint32_t seq) {
   typedef typename KT<KW>::T K;
-  __shared__ AT tab[kTabEntries];
-  __shared__ DevOp sops[kMaxOps];
   __shared__ unsigned int wtot[kStreamThreads / 32];
   __shared__ unsigned long long round_base;
   __shared__ unsigned int abort_flag;
   extern __shared__ __align__(128) unsigned char exp_smem[];
   if (ctl->err) return;
-  load_ops(ops, sops, tab);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->cnt[(out_slot + 1) & 3] = 0;
     atomicMax(&ctl->peak, ctl->cnt[in_slot]);
@@ -1020,7 +1054,6 @@ __global__ void __launch_bounds__(kStreamThreads, 3)
           v[q] = sb.amp[j];
         }
       }
-      if (__any_sync(0xffffffffu, live[0])) apply_ops_n<KW, AT, kExpandILP>(ops.n, sops, tab, k, v, live);
       K k0[kExpandILP], k1[kExpandILP];
       AT o0[kExpandILP], o1[kExpandILP];
       unsigned int b0[kExpandILP], b1[kExpandILP];
@@ -1136,19 +1169,16 @@ constexpr size_t fold_staged_smem_bytes() {
 }
 
 template <int KW, class AT>
-__global__ void __launch_bounds__(kStreamThreads, 3)
+__global__ void __launch_bounds__(kStreamThreads, 4)
     k_fold_staged(Ctl* ctl, Arr in, int in_slot, uint64_t n_chunks, Arr out, int out_slot,
-           const __grid_constant__ OpList ops, Gate1 g, uint32_t seq) {
+                  Gate1 g, uint32_t seq) {
   typedef typename KT<KW>::T K;
-  __shared__ AT tab[kTabEntries];
-  __shared__ DevOp sops[kMaxOps];
   __shared__ unsigned int wtot[kStreamThreads / 32];
   __shared__ unsigned long long round_base;
   __shared__ unsigned int n_act, abort_flag;
   extern __shared__ __align__(128) unsigned char fold_smem[];
   uint16_t* list = (uint16_t*)(fold_smem + stream_smem_bytes<KW, AT>());
   if (ctl->err) return;
-  load_ops(ops, sops, tab);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->cnt[(out_slot + 1) & 3] = 0;
     atomicMax(&ctl->peak, ctl->cnt[in_slot]);
@@ -1217,9 +1247,6 @@ __global__ void __launch_bounds__(kStreamThreads, 3)
       AT o0[kFoldILP], o1[kFoldILP];
       unsigned int b0[kFoldILP], b1[kFoldILP];
       unsigned int wsum = 0;
-      // A warp with no member this round skips the arithmetic (it still takes
-      // part in the round's barriers).
-      if (__any_sync(0xffffffffu, live[0])) apply_ops_n<KW, AT, kFoldILP>(ops.n, sops, tab, k, v, live);
 #pragma unroll
       for (int q = 0; q < kFoldILP; ++q) {
         bool keep0 = false, keep1 = false;
@@ -1429,8 +1456,9 @@ __global__ void __launch_bounds__(kBinThreads)
     uint64_t base;
     uint32_t lim;
     if (in.seg_cnt) {
-      const uint32_t sg = (uint32_t)(u / per_seg);
-      const uint32_t o = (uint32_t)(u - (uint64_t)sg * per_seg) * kBinTile;
+      const uint64_t v = spread_visit(u, log2_pow2(per_seg));
+      const uint32_t sg = (uint32_t)(v / per_seg);
+      const uint32_t o = (uint32_t)(v - (uint64_t)sg * per_seg) * kBinTile;
       const uint32_t cnt = in.seg_cnt[sg];
       lim = o >= cnt ? 0u : (cnt - o < (uint32_t)kBinTile ? cnt - o : (uint32_t)kBinTile);
       base = ((uint64_t)sg << in.seg_log2) + o;
@@ -1840,7 +1868,7 @@ cudaError_t launch_angle_table(cudaStream_t s, double2* tab, uint32_t digits, do
 // The staged variants: one wave of resident CTAs, each streaming its units.
 template <int KW, class AT>
 static cudaError_t expand_staged_t(const Launch& L, Ctl* ctl, Arr in, int in_slot,
-                                   uint64_t n_chunks, const OpList& ops, const Gate1& g, Arr out,
+                                   uint64_t n_chunks, const Gate1& g, Arr out,
                                    int out_slot) {
   const size_t smem = stream_smem_bytes<KW, AT>();
   static std::atomic<unsigned long long> configured{0};
@@ -1855,13 +1883,13 @@ static cudaError_t expand_staged_t(const Launch& L, Ctl* ctl, Arr in, int in_slo
   if (grid > units) grid = units;
   if (grid < 1) grid = 1;
   k_expand_staged<KW, AT><<<(int)grid, kStreamThreads, smem, L.stream>>>(
-      ctl, in, in_slot, n_chunks, out, out_slot, ops, g, L.seq);
+      ctl, in, in_slot, n_chunks, out, out_slot, g, L.seq);
   return cudaGetLastError();
 }
 
 template <int KW, class AT>
 static cudaError_t fold_staged_t(const Launch& L, Ctl* ctl, Arr in, int in_slot,
-                                 uint64_t n_chunks, const OpList& ops, const Gate1& g, Arr out,
+                                 uint64_t n_chunks, const Gate1& g, Arr out,
                                  int out_slot) {
   const size_t smem = fold_staged_smem_bytes<KW, AT>();
   static std::atomic<unsigned long long> configured{0};
@@ -1876,7 +1904,7 @@ static cudaError_t fold_staged_t(const Launch& L, Ctl* ctl, Arr in, int in_slot,
   if (grid > units) grid = units;
   if (grid < 1) grid = 1;
   k_fold_staged<KW, AT><<<(int)grid, kStreamThreads, smem, L.stream>>>(
-      ctl, in, in_slot, n_chunks, out, out_slot, ops, g, L.seq);
+      ctl, in, in_slot, n_chunks, out, out_slot, g, L.seq);
   return cudaGetLastError();
 }
 
@@ -1885,10 +1913,10 @@ cudaError_t launch_expand(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in,
                           int out_slot) {
   if (ops.n == 0) {
     if (kw == 1)
-      return amp32 ? expand_staged_t<1, float2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot)
-                   : expand_staged_t<1, double2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot);
-    return amp32 ? expand_staged_t<2, float2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot)
-                 : expand_staged_t<2, double2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot);
+      return amp32 ? expand_staged_t<1, float2>(L, ctl, in, in_slot, n_chunks, g, out, out_slot)
+                   : expand_staged_t<1, double2>(L, ctl, in, in_slot, n_chunks, g, out, out_slot);
+    return amp32 ? expand_staged_t<2, float2>(L, ctl, in, in_slot, n_chunks, g, out, out_slot)
+                 : expand_staged_t<2, double2>(L, ctl, in, in_slot, n_chunks, g, out, out_slot);
   }
   uint64_t grid = n_chunks < 1 ? 1 : n_chunks;
   if (grid > (uint64_t)L.sm_count * 8) grid = (uint64_t)L.sm_count * 8;
@@ -1920,10 +1948,10 @@ cudaError_t launch_fold(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in, i
   if (g.fold_sign == 0 || g.cmask[0] != 0 || g.cmask[1] != 0) return cudaErrorInvalidValue;
   if (ops.n == 0) {
     if (kw == 1)
-      return amp32 ? fold_staged_t<1, float2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot)
-                   : fold_staged_t<1, double2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot);
-    return amp32 ? fold_staged_t<2, float2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot)
-                 : fold_staged_t<2, double2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot);
+      return amp32 ? fold_staged_t<1, float2>(L, ctl, in, in_slot, n_chunks, g, out, out_slot)
+                   : fold_staged_t<1, double2>(L, ctl, in, in_slot, n_chunks, g, out, out_slot);
+    return amp32 ? fold_staged_t<2, float2>(L, ctl, in, in_slot, n_chunks, g, out, out_slot)
+                 : fold_staged_t<2, double2>(L, ctl, in, in_slot, n_chunks, g, out, out_slot);
   }
   if (kw == 1)
     return amp32 ? fold_t<1, float2>(L, ctl, in, in_slot, n_chunks, ops, g, out, out_slot)
@@ -1962,7 +1990,22 @@ static cudaError_t pair_t(const Launch& L, Ctl* ctl, const Gate1& g, Arr bk, Arr
   static std::atomic<unsigned long long> configured{0};
   cudaError_t e = ensure_smem_optin((const void*)k_pair<KW, AT>, smem, configured);
   if (e != cudaSuccess) return e;
-  k_pair<KW, AT><<<bk.n_seg, kPairThreads, smem, L.stream>>>(ctl, g, bk, out, out_slot, L.seq);
+  // One resident wave (the kernel loops over the buckets).
+  static int per_sm[64] = {0};
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int occ = dev < 64 ? per_sm[dev] : 0;
+  if (occ == 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair<KW, AT>, kPairThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    if (dev < 64) per_sm[dev] = occ;
+  }
+  uint64_t grid = (uint64_t)L.sm_count * (uint64_t)occ;
+  if (grid > bk.n_seg) grid = bk.n_seg;
+  if (grid < 1) grid = 1;
+  k_pair<KW, AT><<<(int)grid, kPairThreads, smem, L.stream>>>(ctl, g, bk, out, out_slot, L.seq);
   return cudaGetLastError();
 }
 

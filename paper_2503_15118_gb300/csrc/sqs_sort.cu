@@ -58,6 +58,13 @@ __device__ __forceinline__ uint32_t digit_of(K k, uint32_t t, uint32_t shift, K 
 }
 
 // Tile `tile` of the input: a slice of one segment, or of the dense array.
+// CTAs visit the tiles of segmented inputs in spread order (a permutation of
+// the tiles of each segment); every tile keeps its index, so the scan over
+// tile indices still ranks the input in storage order.
+__device__ __forceinline__ uint64_t tile_visit(const Arr& in, uint64_t u, uint32_t per_seg) {
+  return in.seg_cnt ? spread_visit(u, log2_pow2(per_seg)) : u;
+}
+
 __device__ __forceinline__ void tile_range(const Arr& in, uint64_t n_dense, uint64_t tile,
                                            uint32_t per_seg, uint64_t& base, uint32_t& lim) {
   if (in.seg_cnt) {
@@ -94,7 +101,8 @@ __global__ void __launch_bounds__(kSortThreads)
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, kErrCapacity);
     return;
   }
-  for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  for (uint64_t u = blockIdx.x; u < n_tiles; u += gridDim.x) {
+    const uint64_t tile = tile_visit(in, u, per_seg);
     for (uint32_t d = threadIdx.x; d < R; d += blockDim.x) h[d] = 0u;
     uint64_t base;
     uint32_t lim;
@@ -217,7 +225,8 @@ __global__ void __launch_bounds__(kSortThreads)
   const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned int lt = (1u << lane) - 1u;
   const uint64_t n_dense = in.seg_cnt ? 0ull : *n_ptr;
-  for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  for (uint64_t u = blockIdx.x; u < n_tiles; u += gridDim.x) {
+    const uint64_t tile = tile_visit(in, u, per_seg);
     for (uint32_t i = threadIdx.x; i < kSortWarps * R; i += blockDim.x) whist[i] = 0u;
     uint64_t base;
     uint32_t lim;
