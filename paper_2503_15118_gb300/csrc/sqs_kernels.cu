@@ -982,16 +982,17 @@ constexpr size_t stream_smem_bytes() {
 
 // Resident CTAs per SM of a staged-stream kernel (cached per device).
 template <class Kern>
-static cudaError_t resident_per_sm(Kern kern, size_t smem, int* per_sm_cache, int& occ) {
+static cudaError_t resident_per_sm(Kern kern, size_t smem, std::atomic<int>* per_sm_cache,
+                                   int& occ) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  occ = dev < 64 ? per_sm_cache[dev] : 0;
+  occ = dev < 64 ? per_sm_cache[dev].load(std::memory_order_relaxed) : 0;
   if (occ == 0) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kStreamThreads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
-    if (dev < 64) per_sm_cache[dev] = occ;
+    if (dev < 64) per_sm_cache[dev].store(occ, std::memory_order_relaxed);
   }
   return cudaSuccess;
 }
@@ -1874,7 +1875,7 @@ static cudaError_t expand_staged_t(const Launch& L, Ctl* ctl, Arr in, int in_slo
   static std::atomic<unsigned long long> configured{0};
   cudaError_t e = ensure_smem_optin((const void*)k_expand_staged<KW, AT>, smem, configured);
   if (e != cudaSuccess) return e;
-  static int per_sm[64] = {0};
+  static std::atomic<int> per_sm[64];
   int occ = 1;
   e = resident_per_sm(k_expand_staged<KW, AT>, smem, per_sm, occ);
   if (e != cudaSuccess) return e;
@@ -1895,7 +1896,7 @@ static cudaError_t fold_staged_t(const Launch& L, Ctl* ctl, Arr in, int in_slot,
   static std::atomic<unsigned long long> configured{0};
   cudaError_t e = ensure_smem_optin((const void*)k_fold_staged<KW, AT>, smem, configured);
   if (e != cudaSuccess) return e;
-  static int per_sm[64] = {0};
+  static std::atomic<int> per_sm[64];
   int occ = 1;
   e = resident_per_sm(k_fold_staged<KW, AT>, smem, per_sm, occ);
   if (e != cudaSuccess) return e;
@@ -1991,16 +1992,16 @@ static cudaError_t pair_t(const Launch& L, Ctl* ctl, const Gate1& g, Arr bk, Arr
   cudaError_t e = ensure_smem_optin((const void*)k_pair<KW, AT>, smem, configured);
   if (e != cudaSuccess) return e;
   // One resident wave (the kernel loops over the buckets).
-  static int per_sm[64] = {0};
+  static std::atomic<int> per_sm[64];
   int dev = 0;
   e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  int occ = dev < 64 ? per_sm[dev] : 0;
+  int occ = dev < 64 ? per_sm[dev].load(std::memory_order_relaxed) : 0;
   if (occ == 0) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair<KW, AT>, kPairThreads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
-    if (dev < 64) per_sm[dev] = occ;
+    if (dev < 64) per_sm[dev].store(occ, std::memory_order_relaxed);
   }
   uint64_t grid = (uint64_t)L.sm_count * (uint64_t)occ;
   if (grid > bk.n_seg) grid = bk.n_seg;
