@@ -377,15 +377,30 @@ __device__ __forceinline__ void apply_ops_n(uint32_t n_ops, const DevOp* ops, co
           k[q] ^= xm;
         }
       }
-    } else if (kind == OP_ADD_REG || kind == OP_SUB_REG || kind == OP_ADD_CONST) {
-      const uint32_t doff = op.dst_off, dw = op.dst_w, soff = op.src_off, sw = op.src_w;
-      const uint64_t c = op.constant;
+    } else if (kind == OP_ADD_CONST) {
+      // In place: the field's bits are added with the constant shifted to the
+      // field; carries out of the field are masked off (mod 2^w).
+      const K D = ((K)wmask(op.dst_w)) << op.dst_off;
+      const K C = ((K)(op.constant & wmask(op.dst_w))) << op.dst_off;
+#pragma unroll
+      for (int q = 0; q < NI; ++q)
+        if ((k[q] & pm) == pv) k[q] = (k[q] & ~D) | (((k[q] & D) + C) & D);
+    } else if (kind == OP_ADD_REG || kind == OP_SUB_REG) {
+      // The source field moved onto the destination's position (one shift),
+      // then added or subtracted in place: ((d +- s) mod 2^w) << doff, as
+      // get_field / set_field give.
+      const uint32_t doff = op.dst_off, soff = op.src_off;
+      const K D = ((K)wmask(op.dst_w)) << doff;
+      const K S = ((K)wmask(op.src_w)) << soff;
+      const bool left = doff >= soff;
+      const uint32_t sh = left ? doff - soff : soff - doff;
+      const bool sub = kind == OP_SUB_REG;
 #pragma unroll
       for (int q = 0; q < NI; ++q) {
         if ((k[q] & pm) == pv) {
-          const uint64_t d = get_field(k[q], doff, dw);
-          const uint64_t sv = kind == OP_ADD_CONST ? c : get_field(k[q], soff, sw);
-          k[q] = set_field<K>(k[q], doff, dw, kind == OP_SUB_REG ? d - sv : d + sv);
+          const K t = left ? (k[q] & S) << sh : (k[q] & S) >> sh;
+          const K kd = k[q] & D;
+          k[q] = (k[q] & ~D) | ((sub ? kd - t : kd + t) & D);
         }
       }
     } else if (kind == OP_TABLE) {
