@@ -171,6 +171,20 @@ __device__ __forceinline__ double neg_bits(double x) {
   asm("xor.b64 %0, %0, 0x8000000000000000;" : "+l"(u));
   return __longlong_as_double((long long)u);
 }
+// Magnitude and sign bits of an FP64 value, as integer ANDs in PTX.  Written
+// as C++ masks of the value's bits, the compiler recognises the magnitude as
+// an absolute value and evaluates it on the FP64 pipe (a counted DADD per
+// component), this GPU's scarcest unit.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  asm("and.b64 %0, %0, 0x7fffffffffffffff;" : "+l"(u));
+  return u;
+}
+__device__ __forceinline__ unsigned long long sign_bits(double x) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  asm("and.b64 %0, %0, 0x8000000000000000;" : "+l"(u));
+  return u;
+}
 __device__ __forceinline__ double2 cneg(double2 a) {
   return make_double2(neg_bits(a.x), neg_bits(a.y));
 }
@@ -190,10 +204,8 @@ __device__ __forceinline__ double norm2(float2 a) {
 // integer order); otherwise |a|^2 is compared with eps^2 in FP64.
 __device__ __forceinline__ bool keep_amp(double2 a, double eps, float, double eps2) {
   const unsigned long long e = (unsigned long long)__double_as_longlong(eps);
-  const unsigned long long ax =
-      (unsigned long long)__double_as_longlong(a.x) & 0x7fffffffffffffffull;
-  const unsigned long long ay =
-      (unsigned long long)__double_as_longlong(a.y) & 0x7fffffffffffffffull;
+  const unsigned long long ax = abs_bits(a.x);
+  const unsigned long long ay = abs_bits(a.y);
   if (ax >= e || ay >= e) return true;
   if ((ax | ay) == 0ull) return e == 0ull;  // exact zero: kept only when eps = 0
   // Both components below eps/2 (the exponent of a normal eps minus one):
@@ -671,12 +683,15 @@ __device__ __forceinline__ void children<double2>(const Gate1& g, uint64_t angle
         o1 = neg1 ? rfms(u10, a0, p01) : rfma(u10, a0, p01);
       else
         o1 = rfma(u10, a0, rmul(u11, a1));
-    } else if (has0) {
-      o0 = rmul(u00, a0);
-      o1 = same0 ? (neg0 ? cneg(o0) : o0) : rmul(u10, a0);
     } else {
-      o0 = rmul(u01, a1);
-      o1 = same1 ? (neg1 ? cneg(o0) : o0) : rmul(u11, a1);
+      // One member: the column of U it multiplies is selected, not branched
+      // on, so lanes holding a bit-0 and a bit-1 member issue one sequence.
+      const bool c1 = !has0;
+      const S ua = c1 ? u01 : u00, ub = c1 ? u11 : u10;
+      const bool same = c1 ? same1 : same0, neg = c1 ? neg1 : neg0;
+      const AT a = c1 ? a1 : a0;
+      o0 = rmul(ua, a);
+      o1 = same ? (neg ? cneg(o0) : o0) : rmul(ub, a);
     }
   } else {
     const AT U00 = Coef<AT>::c(g, 0), U01 = Coef<AT>::c(g, 1);
@@ -686,12 +701,13 @@ __device__ __forceinline__ void children<double2>(const Gate1& g, uint64_t angle
       const AT p11 = same1 ? (neg1 ? cneg(p01) : p01) : cmul(U11, a1);
       o0 = cfma(U00, a0, p01);
       o1 = cfma(U10, a0, p11);
-    } else if (has0) {
-      o0 = cmul(U00, a0);
-      o1 = same0 ? (neg0 ? cneg(o0) : o0) : cmul(U10, a0);
     } else {
-      o0 = cmul(U01, a1);
-      o1 = same1 ? (neg1 ? cneg(o0) : o0) : cmul(U11, a1);
+      const bool c1 = !has0;  // one member, its column selected as above
+      const AT Ua = c1 ? U01 : U00, Ub = c1 ? U11 : U10;
+      const bool same = c1 ? same1 : same0, neg = c1 ? neg1 : neg0;
+      const AT a = c1 ? a1 : a0;
+      o0 = cmul(Ua, a);
+      o1 = same ? (neg ? cneg(o0) : o0) : cmul(Ub, a);
     }
   }
 }
@@ -770,8 +786,8 @@ __device__ __forceinline__ float2 child_real<float2>(const Gate1& g, int r, floa
 // doubling out of the largest binade.
 __device__ __forceinline__ double twice(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned long long sign = b & 0x8000000000000000ull;
-  const unsigned long long mag = b & 0x7fffffffffffffffull;
+  const unsigned long long sign = sign_bits(x);
+  const unsigned long long mag = abs_bits(x);
   const unsigned long long e = mag >> 52;
   const unsigned long long r = e == 0ull    ? (sign | (mag << 1))
                                : e < 2046ull ? b + (1ull << 52)
@@ -801,8 +817,7 @@ __device__ __forceinline__ double2 fold_child<double2>(const Gate1& g, int r, do
 // FP32 storage the cancelling child of a fold is u a + (-u) a evaluated
 // compensated, which is exactly zero, so the test passes.
 __device__ __forceinline__ bool below_bits(double2 a, uint64_t t) {
-  return ((unsigned long long)__double_as_longlong(a.x) & 0x7fffffffffffffffull) < t &&
-         ((unsigned long long)__double_as_longlong(a.y) & 0x7fffffffffffffffull) < t;
+  return abs_bits(a.x) < t && abs_bits(a.y) < t;
 }
 __device__ __forceinline__ bool below_bits(float2, uint64_t) { return true; }
 

@@ -359,30 +359,44 @@ __global__ void __launch_bounds__(kPairThreads, 3)
 
     // Emitters: branches the controls leave alone, unpaired branches and the
     // bit-0 member of each pair.  Listing them first (in the probe table, which
-    // is free now) keeps every lane of the arithmetic below busy.
+    // is free now) keeps every lane of the arithmetic below busy.  The pairs
+    // are listed apart from the rest ([0, C) and [C, 2C) of the table), so a
+    // warp evaluates one form of the 2x2 (two members, or one): mixed, it
+    // would issue both FP64 sequences, each with part of its lanes.
     unsigned int* emit = slot;
     const uint32_t lane = threadIdx.x & 31u;
     const unsigned int lt = (1u << lane) - 1u;
     if (threadIdx.x == 0) fill = 0;
-    __shared__ unsigned int n_emit;
-    if (threadIdx.x == 0) n_emit = 0;
+    __shared__ unsigned int n_pairs, n_rest;
+    if (threadIdx.x == 0) n_pairs = n_rest = 0;
     __syncthreads();
     const uint32_t rounds_in = (n + blockDim.x - 1u) / blockDim.x;
     for (uint32_t r = 0; r < rounds_in; ++r) {
       const uint32_t i = r * blockDim.x + threadIdx.x;
-      bool e = false;
+      bool ep = false, er = false;
       if (i < n) {
         const K k = skey[i];
-        e = (k & cmask) != cval || !((k & bmask) != (K)0 && partner[i] >= 0);
+        const bool met = (k & cmask) == cval;
+        const bool kt = (k & bmask) != (K)0;
+        const bool paired = partner[i] >= 0;
+        ep = met && !kt && paired;
+        er = !met || !paired;
       }
-      const unsigned int ball = __ballot_sync(0xffffffffu, e);
-      unsigned int wb = 0;
-      if (lane == 0 && ball) wb = atomicAdd(&n_emit, (unsigned int)__popc(ball));
-      wb = __shfl_sync(0xffffffffu, wb, 0);
-      if (e) emit[wb + __popc(ball & lt)] = i;
+      const unsigned int bp = __ballot_sync(0xffffffffu, ep);
+      const unsigned int br = __ballot_sync(0xffffffffu, er);
+      unsigned int wp = 0, wr = 0;
+      if (lane == 0) {
+        if (bp) wp = atomicAdd(&n_pairs, (unsigned int)__popc(bp));
+        if (br) wr = atomicAdd(&n_rest, (unsigned int)__popc(br));
+      }
+      wp = __shfl_sync(0xffffffffu, wp, 0);
+      wr = __shfl_sync(0xffffffffu, wr, 0);
+      if (ep) emit[wp + __popc(bp & lt)] = i;
+      if (er) emit[C + wr + __popc(br & lt)] = i;
     }
     __syncthreads();
-    const uint32_t ne = n_emit;
+    const uint32_t np = n_pairs;
+    const uint32_t ne = np + n_rest;
 
     const uint64_t obase = (uint64_t)b << out.seg_log2;
     const uint32_t rounds = (ne + blockDim.x - 1u) / blockDim.x;
@@ -392,7 +406,7 @@ __global__ void __launch_bounds__(kPairThreads, 3)
       K k0 = 0, k1 = 0;
       AT o0, o1;
       if (q < ne) {
-        const uint32_t i = emit[q];
+        const uint32_t i = q < np ? emit[q] : emit[C + (q - np)];
         const K k = skey[i];
         const AT ai = samp[i];
         if ((k & cmask) != cval) {
