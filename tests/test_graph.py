@@ -136,3 +136,28 @@ def test_replay_is_faster_than_eager_for_small_states(sqs, cfg1):
     t_graph = (time.perf_counter() - t0) / reps
     print(f"\nconfig 1 per circuit: eager {t_eager * 1e3:.3f} ms, graph {t_graph * 1e3:.3f} ms")
     assert t_graph < t_eager
+
+
+@pytest.mark.parametrize("factor", [2, 32])
+def test_replay_with_a_loose_static_bound(sqs, factor):
+    """A static bound far above the peak sizes every segment list of the
+    replay mostly empty: the partition and in-place passes search it for
+    non-empty units in batches and the pair kernel draws only the buckets
+    the device count asks for.  The replay stays bit-identical to eager
+    issue and equal to the oracle."""
+    from paper_2503_15118_gb300 import workloads as W
+    circ = W.random_circuit([8, 8, 8], 80, seed=31,
+                            kinds=("x", "cx", "ccx", "ry", "phase", "h", "add"))
+    eager = _eager(sqs, circ).to_dict()
+    st = _state(sqs, circ["widths"])
+    st.run(circ)
+    peak = st.peak_nnz()
+    g = st.capture(circ, static_bound=factor * peak)
+    for _ in range(2):
+        g.launch()
+        got = st.to_dict()
+        assert set(got) == set(eager) and all(got[k] == eager[k] for k in got)
+    assert st.stats()["steps_hash"] > 0
+    o = oracle.run_circuit(circ)
+    assert compare_states(got, o.to_dict()) >= 1 - 1e-10
+    g.close()
