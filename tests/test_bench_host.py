@@ -150,3 +150,21 @@ def test_fp32_error_report():
     assert not r["keys_equal"] and r["only_f64"] == 1 and r["only_f32"] == 1
     assert abs(r["only_max_abs"] - max(abs(a[7]), 0.5)) < 1e-15
     assert r["max_abs_diff"] == 0.0
+
+
+def test_cpu_baseline_repeats_its_prefix():
+    """The CPU baseline times the oracle on the gate prefix whose inputs stay
+    within the budget, repeating the prefix from a fresh state until at least
+    min_seconds are timed; its rate counts every repetition's updates."""
+    from paper_2503_15118_gb300 import workloads as W
+    circ = W.random_circuit([4, 4, 4], 40, seed=3, kinds=("x", "cx", "h", "ry", "phase"))
+    cb1, dt1 = bench.cpu_baseline(circ, budget_nnz=64)
+    assert cb1["kind"] == "oracle" and cb1["cores"] == 1 and "1 pass(es)" in cb1["sample"]
+    cb2, dt2 = bench.cpu_baseline(circ, budget_nnz=64, min_seconds=0.05)
+    assert dt2 >= 0.05
+    passes = int(cb2["sample"].split(" pass(es)")[0].split()[-1])
+    assert passes >= 1
+    upd1 = int(cb1["sample"].split(" updates in")[0].split()[-1])
+    upd2 = int(cb2["sample"].split(" updates in")[0].split()[-1])
+    assert upd2 == passes * upd1
+    assert cb2["value"] == pytest.approx(upd2 / dt2)
