@@ -220,9 +220,10 @@ cudaError_t launch_rsort_pass(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr
 cudaError_t launch_rsort_merge(const Launch& L, int kw, bool amp32, Ctl* ctl, Arr in,
                                const unsigned long long* n_ptr, const Gate1& g, Arr out,
                                int out_slot);
-// One CTA per bucket: pair, apply the 2x2, prune; bucket b's survivors become
-// segment b of `out` (segment capacity 2 x bucket capacity).  Resets the
-// bucket counters.
+// Per bucket: pair, apply the 2x2, prune; bucket b's survivors become
+// segment b of `out` (segment capacity 2 x bucket capacity).  One resident
+// wave of CTAs draws the buckets the partition used (ctl->buckets) from a
+// counter the partition zeroed (ctl->pair_next).  Resets the bucket counters.
 cudaError_t launch_pair(const Launch& L, int kw, bool amp32, Ctl* ctl, const Gate1& g, Arr bk,
                         Arr out, int out_slot);
 // Interference step whose target bit is constant over the state (no pair can
